@@ -1,0 +1,127 @@
+/*
+ * tnrd.h -- C ABI of the GB300 (sm_103a) TRDMD despeckling library, libtnrd.so.
+ *
+ * The method (Feng & Chen, "Speckle Reduction with Trained Nonlinear Diffusion
+ * Filtering", Sec. 3.1, Eq. diffusionprocessfinal) runs T stages from u_0 = f:
+ *
+ *     u~_t = u_{t-1} - sum_{i<N_k} K_i^T phi_i^t(K_i^t u_{t-1})
+ *     u_t  = (u~_t + sqrt(u~_t^2 + 8 (1+2 lam_t) lam_t f^2)) / (2 (1+2 lam_t))
+ *
+ * K_i is true 2-D convolution with the ksize x ksize filter k_i over the
+ * half-sample symmetric padded image (edge pixel repeated), K_i^T its exact
+ * transpose (the rotated-kernel convolution of Eq. diffusion, with the border
+ * folded back), and phi_i(z) = sum_j w_ij exp(-(z - mu_j)^2 / (2 gamma^2)) with
+ * mu_j = rbf_mu0 + j * rbf_delta.  The prox is Eq. subproblemGIdiv.
+ *
+ * Conventions for every entry point:
+ *  - All array pointers are DEVICE pointers unless stated; the caller owns all
+ *    memory.  Images are float32, row-major, `pitch` floats between rows
+ *    (pitch >= W, pitch % 4 == 0, base pointers 16-byte aligned); a batch of N
+ *    images of one size is contiguous with stride H * pitch floats.
+ *  - Every call is asynchronous on `stream`, never synchronises the host, and
+ *    launches nothing when it returns an error status.  Calls made from one
+ *    host thread that fail leave a message for tnrd_last_error().
+ *  - `workspace` is caller-allocated device scratch of at least the size that
+ *    tnrd_workspace_size() returns for the same arguments; it may be reused
+ *    between calls on the same stream.
+ *  - Supported models: (ksize, nfilt) in {(3,4), (5,24), (7,48)}, nrbf <= 128,
+ *    rbf_delta >= rbf_gamma > 0 (the RBF sum is evaluated over the 13 centres
+ *    nearest to z; the dropped terms are below 1.4e-9 * max|w|).  Images need
+ *    H >= ksize and W >= ksize; N == 0 is a no-op.
+ */
+#ifndef TNRD_H
+#define TNRD_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define TNRD_API __attribute__((visibility("default")))
+#else
+#define TNRD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TNRD_OK = 0,
+    TNRD_ERR_INVALID_ARG = 1,   /* null pointer, bad size, pitch or alignment      */
+    TNRD_ERR_UNSUPPORTED = 2,   /* (ksize, nfilt, nrbf, rbf spacing) not built      */
+    TNRD_ERR_CUDA = 3,          /* a CUDA runtime call failed; see tnrd_last_error */
+    TNRD_ERR_TIMEOUT = 4,       /* a bounded device-side wait expired              */
+    TNRD_ERR_WORKSPACE = 5      /* workspace null or smaller than required          */
+} tnrd_status;
+
+/* How the stage is computed.  All give the same result within the stated
+ * tolerances; FUSED and UNFUSED compute in FP32, the tensor-core variants run
+ * the filter bank and its adjoint with TF32 / BF16 operands and FP32
+ * accumulation, phi and the prox in FP32. */
+typedef enum {
+    TNRD_ALGO_FUSED = 0,      /* one kernel per stage, responses kept on chip      */
+    TNRD_ALGO_UNFUSED = 1,    /* three kernels per stage, N_k response planes in HBM */
+    TNRD_ALGO_TC_TF32 = 2,
+    TNRD_ALGO_TC_BF16 = 3
+} tnrd_algo;
+
+/* Parameters of a T-stage model (Sec. 3.2: Theta_t = {lam_t, phi_i^t, k_i^t}). */
+typedef struct {
+    int T;                  /* number of stages, >= 1                              */
+    int ksize;              /* filter side k (odd)                                 */
+    int nfilt;              /* N_k filters per stage                               */
+    int nrbf;               /* Gaussian RBFs per influence function                */
+    float rbf_mu0;          /* centre of the first RBF                             */
+    float rbf_delta;        /* spacing of the centres                              */
+    float rbf_gamma;        /* RBF width gamma                                     */
+    const float* filters;   /* device [T][nfilt][ksize][ksize], k[a][b] row-major  */
+    const float* rbf_w;     /* device [T][nfilt][nrbf]                             */
+    const float* lambda;    /* device [T], lam_t >= 0 (> 0 for tnrd_backward)      */
+} tnrd_params;
+
+typedef enum { TNRD_OP_FORWARD = 0, TNRD_OP_BACKWARD = 1 } tnrd_op;
+
+/* Bytes of device workspace that `op` needs for N images of H x W (pitch in
+ * floats).  `keep_stages` as in tnrd_forward.  Returns 0 on invalid arguments. */
+TNRD_API size_t tnrd_workspace_size(tnrd_op op, const tnrd_params* params, int N, int H, int W,
+                           int pitch, int keep_stages, tnrd_algo algo);
+
+/* Forward cascade, Eq. diffusion with the stage of Eq. diffusionprocessfinal.
+ *   f      [N][H][pitch]  noisy input (also u_0 and the data term's f)
+ *   u      keep_stages != 0: [T+1][N][H][pitch] receives u_0 = f, u_1 .. u_T
+ *                            (the checkpoints tnrd_backward needs);
+ *          keep_stages == 0: [N][H][pitch] receives u_T only.
+ * u must not overlap f.  Padding columns (W..pitch) are not written. */
+TNRD_API tnrd_status tnrd_forward(const tnrd_params* params, int N, int H, int W, int pitch,
+                         const float* f, float* u, int keep_stages, tnrd_algo algo,
+                         void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* Gradients of a loss L through the cascade (Sec. 3.2, Eq. iterstep), for the
+ * images of a batch summed (the loss of Eq. learning sums over samples).
+ *   u_stages  [T+1][N][H][pitch] from tnrd_forward(keep_stages = 1)
+ *   grad_uT   [N][H][pitch] dL/du_T (u_T - u_gt for the loss of Eq. learning)
+ * Outputs (overwritten, not accumulated):
+ *   grad_u0      [N][H][pitch] dL/du_0 along the state path, f held fixed
+ *                in the data term (nullable: not computed)
+ *   grad_filters [T][nfilt][ksize][ksize]  dL/dk (raw coefficients)
+ *   grad_rbf_w   [T][nfilt][nrbf]           dL/dw
+ *   grad_lambda  [T]                         dL/dlam (dL/dbeta = lam dL/dlam
+ *                for lam = e^beta, Eq. derv5)
+ * Requires lam_t > 0.  algo must be TNRD_ALGO_FUSED.  The parameter gradients
+ * are reduced in a fixed order: repeated calls give identical bits. */
+TNRD_API tnrd_status tnrd_backward(const tnrd_params* params, int N, int H, int W, int pitch,
+                          const float* f, const float* u_stages, const float* grad_uT,
+                          float* grad_u0, float* grad_filters, float* grad_rbf_w,
+                          float* grad_lambda, tnrd_algo algo,
+                          void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* Message describing the last error status returned on this host thread. */
+TNRD_API const char* tnrd_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+TNRD_API int tnrd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNRD_H */

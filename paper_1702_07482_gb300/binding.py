@@ -1,0 +1,120 @@
+"""ctypes binding of libtnrd.so (include/tnrd.h) -- argument marshalling only.
+
+Every step of the stage runs in the library's CUDA kernels; this module turns
+torch CUDA tensors into the pointers, sizes and stream handle of the C calls
+and raises on a non-OK status.  It never computes anything itself and has no
+CPU fallback: if the shared library is missing it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libtnrd.so")
+
+TNRD_OK = 0
+STATUS_NAMES = {0: "TNRD_OK", 1: "TNRD_ERR_INVALID_ARG", 2: "TNRD_ERR_UNSUPPORTED",
+                3: "TNRD_ERR_CUDA", 4: "TNRD_ERR_TIMEOUT", 5: "TNRD_ERR_WORKSPACE"}
+
+ALGO = {"fused": 0, "unfused": 1, "tf32": 2, "bf16": 3}
+OP_FORWARD, OP_BACKWARD = 0, 1
+
+# Every symbol include/tnrd.h declares (checked by the tests).
+EXPORTS = ["tnrd_workspace_size", "tnrd_forward", "tnrd_backward",
+           "tnrd_last_error", "tnrd_version"]
+
+
+class TnrdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class tnrd_params(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("ksize", ctypes.c_int), ("nfilt", ctypes.c_int),
+                ("nrbf", ctypes.c_int), ("rbf_mu0", ctypes.c_float),
+                ("rbf_delta", ctypes.c_float), ("rbf_gamma", ctypes.c_float),
+                ("filters", ctypes.c_void_p), ("rbf_w", ctypes.c_void_p),
+                ("lambda_", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libtnrd.so and declare the C signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtnrd.so not found at {path}: the CUDA library must be "
+                               "built first (paper_1702_07482_gb300.build.build())")
+        L = ctypes.CDLL(path)
+        P, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        pp = ctypes.POINTER(tnrd_params)
+        L.tnrd_workspace_size.restype = sz
+        L.tnrd_workspace_size.argtypes = [i, pp, i, i, i, i, i, i]
+        L.tnrd_forward.restype = i
+        L.tnrd_forward.argtypes = [pp, i, i, i, i, P, P, i, i, P, sz, P]
+        L.tnrd_backward.restype = i
+        L.tnrd_backward.argtypes = [pp, i, i, i, i, P, P, P, P, P, P, P, i, P, sz, P]
+        L.tnrd_last_error.restype = ctypes.c_char_p
+        L.tnrd_last_error.argtypes = []
+        L.tnrd_version.restype = i
+        L.tnrd_version.argtypes = []
+        _lib = L
+        return _lib
+
+
+def last_error() -> str:
+    return load().tnrd_last_error().decode()
+
+
+def check(status: int) -> None:
+    if status != TNRD_OK:
+        raise TnrdError(status, last_error())
+
+
+def version() -> int:
+    return load().tnrd_version()
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def make_params(model) -> tnrd_params:
+    """tnrd_params from a model holding device float32 tensors (see ops.Model)."""
+    p = tnrd_params()
+    p.T, p.ksize, p.nfilt, p.nrbf = model.T, model.ksize, model.nfilt, model.nrbf
+    p.rbf_mu0, p.rbf_delta, p.rbf_gamma = model.mu0, model.delta, model.gamma
+    p.filters = model.filters.data_ptr()
+    p.rbf_w = model.rbf_w.data_ptr()
+    p.lambda_ = model.lam.data_ptr()
+    return p
+
+
+def tnrd_workspace_size(op: int, params: tnrd_params, N: int, H: int, W: int, pitch: int,
+                        keep_stages: int, algo: int) -> int:
+    return load().tnrd_workspace_size(op, ctypes.byref(params), N, H, W, pitch,
+                                      keep_stages, algo)
+
+
+def tnrd_forward(params: tnrd_params, N, H, W, pitch, f, u, keep_stages, algo,
+                 workspace, workspace_bytes, stream) -> None:
+    check(load().tnrd_forward(ctypes.byref(params), N, H, W, pitch, _ptr(f), _ptr(u),
+                              int(keep_stages), int(algo), _ptr(workspace),
+                              int(workspace_bytes), ctypes.c_void_p(stream)))
+
+
+def tnrd_backward(params: tnrd_params, N, H, W, pitch, f, u_stages, grad_uT, grad_u0,
+                  grad_filters, grad_rbf_w, grad_lambda, algo, workspace,
+                  workspace_bytes, stream) -> None:
+    check(load().tnrd_backward(ctypes.byref(params), N, H, W, pitch, _ptr(f), _ptr(u_stages),
+                               _ptr(grad_uT), _ptr(grad_u0), _ptr(grad_filters),
+                               _ptr(grad_rbf_w), _ptr(grad_lambda), int(algo),
+                               _ptr(workspace), int(workspace_bytes), ctypes.c_void_p(stream)))

@@ -1,0 +1,258 @@
+// C ABI of libtnrd.so (declared in include/tnrd.h): argument validation,
+// workspace layout, stage scheduling and kernel selection.  No allocation and
+// no host synchronisation happens here.
+#include "tnrd.h"
+#include "launch.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+namespace {
+
+thread_local std::string g_err;
+
+tnrd_status fail(tnrd_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+tnrd_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(TNRD_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool supported_model(int ks, int nk)
+{
+    return (ks == 3 && nk == 4) || (ks == 5 && nk == 24) || (ks == 7 && nk == 48);
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+tnrd_status check_params(const tnrd_params* p)
+{
+    if (!p) return fail(TNRD_ERR_INVALID_ARG, "params is null");
+    if (p->T < 1) return fail(TNRD_ERR_INVALID_ARG, "T = %d < 1", p->T);
+    if (!supported_model(p->ksize, p->nfilt))
+        return fail(TNRD_ERR_UNSUPPORTED, "(ksize, nfilt) = (%d, %d) not built; "
+                    "supported: (3,4), (5,24), (7,48)", p->ksize, p->nfilt);
+    if (p->nrbf < 1 || p->nrbf > tnrd::MAX_NRBF)
+        return fail(TNRD_ERR_UNSUPPORTED, "nrbf = %d outside [1, %d]", p->nrbf, tnrd::MAX_NRBF);
+    if (!(p->rbf_gamma > 0.0f) || !(p->rbf_delta >= p->rbf_gamma) || !std::isfinite(p->rbf_mu0))
+        return fail(TNRD_ERR_UNSUPPORTED, "RBF spacing must satisfy delta >= gamma > 0 "
+                    "(delta = %g, gamma = %g)", p->rbf_delta, p->rbf_gamma);
+    if (!p->filters || !p->rbf_w || !p->lambda)
+        return fail(TNRD_ERR_INVALID_ARG, "null parameter array");
+    return TNRD_OK;
+}
+
+tnrd_status check_images(int N, int H, int W, int pitch, int ks)
+{
+    if (N < 0) return fail(TNRD_ERR_INVALID_ARG, "N = %d < 0", N);
+    if (H < ks || W < ks)
+        return fail(TNRD_ERR_INVALID_ARG, "image %d x %d smaller than the %d x %d filter", H, W, ks, ks);
+    if (pitch < W || pitch % 4 != 0)
+        return fail(TNRD_ERR_INVALID_ARG, "pitch %d must be >= W = %d and a multiple of 4", pitch, W);
+    if ((long long)H * (long long)pitch >= (1LL << 31))
+        return fail(TNRD_ERR_INVALID_ARG, "image of %d x %d (pitch %d) too large", H, W, pitch);
+    if (N > 65535) return fail(TNRD_ERR_INVALID_ARG, "N = %d > 65535", N);
+    return TNRD_OK;
+}
+
+tnrd::RbfConst make_rbf(const tnrd_params* p)
+{
+    tnrd::RbfConst rc{};
+    const double mu0 = p->rbf_mu0, d = p->rbf_delta, g = p->rbf_gamma;
+    const int W = tnrd::RBF_WIN;
+    rc.mu0 = (float)mu0;
+    rc.delta = (float)d;
+    rc.inv_delta = (float)(1.0 / d);
+    rc.zlo = (float)(mu0 - (W + 0.5) * d);
+    rc.zhi = (float)(mu0 + (p->nrbf - 1 + W + 0.5) * d);
+    rc.cq = (float)(d / (g * g));
+    rc.half_inv_g2 = (float)(1.0 / (2.0 * g * g));
+    rc.inv_g2 = (float)(1.0 / (g * g));
+    rc.jmax = p->nrbf - 1 + W;
+    for (int m = 0; m <= W; ++m) rc.E[m] = (float)std::exp(-(double)m * m * d * d / (2.0 * g * g));
+    return rc;
+}
+
+// Pick the fused tile height minimising (max tiles per SM) x (work per tile).
+int pick_fused_th(int ks, int nk, int N, int H, int W)
+{
+    int nsm = 148;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int R = ks / 2;
+    double best = 1e300;
+    int best_th = 32;
+    for (int i = 0; i < tnrd::kNumFusedTH; ++i) {
+        const int th = tnrd::kFusedTH[i];
+        const long long tiles = (long long)N * ((H + th - 1) / th) * ((W + 31) / 32);
+        const long long per_sm = (tiles + nsm - 1) / nsm;
+        const double work = (double)(th + 2 * R) * (32 + 2 * R) * 2.0 + (double)th * 32;
+        const double cost = per_sm * work;
+        if (cost < best * 0.999) {
+            best = cost;
+            best_th = th;
+        }
+    }
+    return best_th;
+}
+
+struct FwdLayout {
+    size_t pingpong = 0;   // offset of the ping-pong image batch
+    size_t v = 0, g = 0;   // unfused response planes and adjoint plane
+    size_t total = 0;
+};
+
+FwdLayout fwd_layout(const tnrd_params* p, int N, int H, int pitch, int keep, tnrd_algo algo)
+{
+    FwdLayout L;
+    const size_t batch = sizeof(float) * (size_t)N * H * pitch;
+    size_t off = 0;
+    if (!keep && p->T >= 2) {
+        L.pingpong = off;
+        off = align_up(off + batch, 256);
+    }
+    if (algo == TNRD_ALGO_UNFUSED) {
+        L.v = off;
+        off = align_up(off + batch * (size_t)p->nfilt, 256);
+        L.g = off;
+        off = align_up(off + batch, 256);
+    }
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tnrd_last_error(void) { return g_err.c_str(); }
+
+int tnrd_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+size_t tnrd_workspace_size(tnrd_op op, const tnrd_params* params, int N, int H, int W,
+                           int pitch, int keep_stages, tnrd_algo algo)
+{
+    if (check_params(params) != TNRD_OK) return 0;
+    if (check_images(N, H, W, pitch, params->ksize) != TNRD_OK) return 0;
+    if (op == TNRD_OP_FORWARD) return fwd_layout(params, N, H, pitch, keep_stages, algo).total;
+    return 0;
+}
+
+tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
+                         const float* f, float* u, int keep_stages, tnrd_algo algo,
+                         void* workspace, size_t workspace_bytes, cudaStream_t stream)
+{
+    tnrd_status st = check_params(p);
+    if (st != TNRD_OK) return st;
+    st = check_images(N, H, W, pitch, p->ksize);
+    if (st != TNRD_OK) return st;
+    if (algo != TNRD_ALGO_FUSED && algo != TNRD_ALGO_UNFUSED)
+        return fail(TNRD_ERR_UNSUPPORTED, "algo %d not available in tnrd_forward", (int)algo);
+    if (N == 0) return TNRD_OK;
+    if (!f || !u) return fail(TNRD_ERR_INVALID_ARG, "null image pointer");
+    if (!aligned16(f) || !aligned16(u)) return fail(TNRD_ERR_INVALID_ARG, "f and u must be 16-byte aligned");
+    const size_t plane = (size_t)H * pitch;
+    const size_t batch = plane * (size_t)N;
+    const size_t u_len = keep_stages ? batch * (size_t)(p->T + 1) : batch;
+    if ((const float*)u < f + batch && f < (const float*)u + u_len)
+        return fail(TNRD_ERR_INVALID_ARG, "u overlaps f");
+    const FwdLayout L = fwd_layout(p, N, H, pitch, keep_stages, algo);
+    if (L.total > 0 && (!workspace || workspace_bytes < L.total))
+        return fail(TNRD_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", L.total,
+                    workspace ? workspace_bytes : (size_t)0);
+    char* ws = (char*)workspace;
+    float* pp = L.total ? (float*)(ws + L.pingpong) : nullptr;
+
+    if (keep_stages) {
+        cudaError_t e = cudaMemcpyAsync(u, f, sizeof(float) * batch, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy of u_0");
+    }
+    const tnrd::RbfConst rc = make_rbf(p);
+    const int ks = p->ksize, nk = p->nfilt;
+    const int th = (algo == TNRD_ALGO_FUSED) ? pick_fused_th(ks, nk, N, H, W) : 0;
+
+    for (int t = 0; t < p->T; ++t) {
+        const float* in;
+        float* out;
+        if (keep_stages) {
+            in = (t == 0) ? f : u + (size_t)t * batch;
+            out = u + (size_t)(t + 1) * batch;
+        } else {
+            // stage t writes u when (T-1-t) is even, so the last stage lands in u
+            float* cur = ((p->T - 1 - t) % 2 == 0) ? u : pp;
+            float* prev = ((p->T - t) % 2 == 0) ? u : pp;
+            in = (t == 0) ? f : prev;
+            out = cur;
+        }
+        const float* kt = p->filters + (size_t)t * nk * ks * ks;
+        const float* wt = p->rbf_w + (size_t)t * nk * p->nrbf;
+        cudaError_t e;
+        if (algo == TNRD_ALGO_FUSED) {
+            tnrd::StageArgs a{};
+            a.u_in = in;
+            a.u_out = out;
+            a.f = f;
+            a.img_stride = (long long)plane;
+            a.H = H;
+            a.W = W;
+            a.pitch = pitch;
+            a.tiles_x = (W + 31) / 32;
+            a.tiles_y = (H + th - 1) / th;
+            a.k = kt;
+            a.w = wt;
+            a.lam = p->lambda + t;
+            a.nrbf = p->nrbf;
+            a.rc = rc;
+            e = tnrd::launch_fused_fwd(ks, nk, th, a, N, stream);
+        } else {
+            tnrd::UnfArgs a{};
+            a.u_in = in;
+            a.u_out = out;
+            a.f = f;
+            a.v = (float*)(ws + L.v);
+            a.g = (float*)(ws + L.g);
+            a.img_stride = (long long)plane;
+            a.H = H;
+            a.W = W;
+            a.pitch = pitch;
+            a.nfilt = nk;
+            a.k = kt;
+            a.w = wt;
+            a.lam = p->lambda + t;
+            a.nrbf = p->nrbf;
+            a.rc = rc;
+            e = tnrd::launch_unfused_fwd(ks, a, N, stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "stage launch");
+    }
+    return TNRD_OK;
+}
+
+tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
+                          const float* f, const float* u_stages, const float* grad_uT,
+                          float* grad_u0, float* grad_filters, float* grad_rbf_w,
+                          float* grad_lambda, tnrd_algo algo,
+                          void* workspace, size_t workspace_bytes, cudaStream_t stream)
+{
+    (void)p; (void)N; (void)H; (void)W; (void)pitch; (void)f; (void)u_stages; (void)grad_uT;
+    (void)grad_u0; (void)grad_filters; (void)grad_rbf_w; (void)grad_lambda; (void)algo;
+    (void)workspace; (void)workspace_bytes; (void)stream;
+    return fail(TNRD_ERR_UNSUPPORTED, "tnrd_backward is not built yet");
+}
+
+}  // extern "C"

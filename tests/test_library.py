@@ -1,0 +1,92 @@
+"""Host-side checks of libtnrd.so that need no GPU: it builds, loads, exports
+every symbol include/tnrd.h declares, and rejects bad arguments before it
+touches the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1702_07482_gb300 import binding as B
+from paper_1702_07482_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return B.load()
+
+
+def _declared_symbols():
+    syms = set()
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if name.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", name)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            syms |= set(re.findall(r"\b(tnrd_[a-z0-9_]+)\s*\(", txt))
+    return syms
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_symbols()
+    assert "tnrd_forward" in declared and "tnrd_backward" in declared
+    for s in declared:
+        assert hasattr(lib, s), f"{s} declared in include/ but not exported"
+    assert set(B.EXPORTS) <= declared
+
+
+def test_version(lib):
+    assert B.version() >= 10000
+
+
+def _params(T=2, ks=7, nk=48, nrbf=63, fake=0x1000):
+    p = B.tnrd_params()
+    p.T, p.ksize, p.nfilt, p.nrbf = T, ks, nk, nrbf
+    p.rbf_mu0, p.rbf_delta, p.rbf_gamma = -310.0, 10.0, 10.0
+    p.filters = p.rbf_w = p.lambda_ = fake
+    return p
+
+
+def _fwd(lib, p, N=1, H=64, W=64, pitch=64, f=0x10000, u=0x200000, keep=0, algo=0,
+         ws=None, wsb=0):
+    return lib.tnrd_forward(ctypes.byref(p) if p is not None else None, N, H, W, pitch,
+                            ctypes.c_void_p(f), ctypes.c_void_p(u), keep, algo,
+                            ctypes.c_void_p(ws) if ws else None, wsb, None)
+
+
+def test_argument_errors_launch_nothing(lib):
+    assert _fwd(lib, None) == 1
+    assert _fwd(lib, _params(ks=9, nk=80)) == 2
+    assert _fwd(lib, _params(nrbf=0)) == 2
+    p = _params()
+    p.rbf_delta = 5.0  # centres closer than the width: window bound does not hold
+    assert _fwd(lib, p) == 2
+    assert _fwd(lib, _params(T=0)) == 1
+    assert _fwd(lib, _params(), H=6) == 1          # smaller than the filter
+    assert _fwd(lib, _params(), W=65, pitch=65) == 1   # pitch not a multiple of 4
+    assert _fwd(lib, _params(), pitch=60) == 1     # pitch < W
+    assert _fwd(lib, _params(), f=0x10004) == 1    # misaligned
+    assert _fwd(lib, _params(), f=0, u=0) == 1     # null images
+    assert _fwd(lib, _params(), u=0x10000 + 64) == 1   # u overlaps f
+    assert _fwd(lib, _params(), algo=7) == 2
+    # T >= 2 without keep_stages needs a ping-pong workspace
+    assert _fwd(lib, _params(T=3), ws=None) == 5
+    assert "workspace" in B.last_error()
+    assert _fwd(lib, _params(), N=-1) == 1
+
+
+def test_empty_batch_is_a_noop(lib):
+    assert _fwd(lib, _params(), N=0, f=0, u=0) == 0
+
+
+def test_workspace_sizes(lib):
+    p = _params(T=5)
+    one = 4 * 64 * 64
+    assert lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 64, 64, 64, 1, 0) == 0
+    assert lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 64, 64, 64, 0, 0) == 2 * one
+    unf = lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 64, 64, 64, 1, 1)
+    assert unf == 2 * one * 48 + 2 * one
+    assert lib.tnrd_workspace_size(0, ctypes.byref(_params(T=1)), 1, 64, 64, 64, 0, 0) == 0
+    assert lib.tnrd_workspace_size(0, ctypes.byref(_params(ks=4)), 1, 64, 64, 64, 0, 0) == 0

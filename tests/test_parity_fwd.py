@@ -1,0 +1,111 @@
+"""GPU parity of the forward cascade (fused and unfused FP32 stage kernels)
+against the FP64 oracle, element by element.  Calls go through the C ABI.
+
+Tolerance: max |u_gpu - u_oracle| <= 1e-3 on the [0, 255] intensity scale
+(absolute), for every stage u_1..u_T.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from _cases import TOL_U_FP32, case, crop_window
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1702_07482_gb300 import binding, build
+    build.build()
+    binding.load()
+
+
+def _gpu_forward(p, f, algo="fused", keep=True):
+    from paper_1702_07482_gb300 import ops
+    m = ops.Model.create(p.filters, p.rbf_w, p.lam, p.mu0, p.delta, p.gamma)
+    ft = torch.tensor(f, dtype=torch.float32, device="cuda")
+    out = ops.forward(m, ft, keep_stages=keep, algo=algo)
+    torch.cuda.synchronize()
+    W = f.shape[-1]
+    return out[..., :W].double().cpu().numpy()
+
+
+def _oracle_all(p, f):
+    return np.stack([oracle.forward(f[n], p) for n in range(f.shape[0])], axis=1)
+
+
+# (H, W, ks, nk, T, N): the small workload of the table (128x128, 5x5x24, T=5),
+# several tiles with ragged tails (97 = 3*32 + 1 = 6*16 + 1 = 4*24 + 1 rows: the
+# last tile holds fewer than R rows), widths that need row padding, images
+# smaller than one tile, batches.
+CASES = [
+    (128, 128, 5, 24, 5, 1),
+    (97, 65, 7, 48, 2, 1),
+    (33, 41, 7, 48, 3, 2),
+    (20, 30, 7, 48, 2, 1),
+    (7, 7, 7, 48, 2, 1),
+    (64, 35, 3, 4, 4, 3),
+    (50, 100, 5, 24, 3, 1),
+    (40, 257, 7, 48, 1, 1),
+]
+
+
+@pytest.mark.parametrize("H,W,ks,nk,T,N", CASES)
+@pytest.mark.parametrize("algo", ["fused", "unfused"])
+def test_forward_matches_oracle(H, W, ks, nk, T, N, algo):
+    p, f = case(H, W, ks, nk, T, L=1, N=N, cfg=101 + H + W)
+    got = _gpu_forward(p, f, algo)            # [T+1][N][H][W]
+    ref = _oracle_all(p, f)
+    np.testing.assert_array_equal(got[0], f)  # u_0 = f copied exactly
+    err = np.abs(got - ref).max(axis=(1, 2, 3))
+    assert np.all(err <= TOL_U_FP32), f"max |du| per stage {err}"
+
+
+def test_final_only_equals_kept_last_stage():
+    p, f = case(61, 70, 7, 48, 3, N=2, cfg=120)
+    keep = _gpu_forward(p, f, keep=True)
+    last = _gpu_forward(p, f, keep=False)
+    np.testing.assert_array_equal(keep[-1], last)
+
+
+def test_fused_and_unfused_agree_closely():
+    p, f = case(96, 96, 7, 48, 3, cfg=121)
+    a = _gpu_forward(p, f, "fused", keep=False)
+    b = _gpu_forward(p, f, "unfused", keep=False)
+    assert np.abs(a - b).max() <= TOL_U_FP32
+
+
+def test_repeatable_bits():
+    p, f = case(80, 80, 7, 48, 2, cfg=122)
+    a = _gpu_forward(p, f, keep=False)
+    b = _gpu_forward(p, f, keep=False)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_zero_weights_is_pure_prox():
+    """All RBF weights 0: each stage is the data-term prox alone (the oracle's
+    closed-form reduction); the GPU result must follow it too."""
+    p, f = case(45, 77, 7, 48, 3, cfg=123)
+    p.rbf_w[:] = 0.0
+    got = _gpu_forward(p, f, keep=False)[0]
+    ref = oracle.forward(f[0], p)[-1]
+    assert np.abs(got - ref).max() <= TOL_U_FP32
+
+
+def test_512_full_size_sampled_windows():
+    """The 512x512, 7x7x48, T=5 workload at full size in the launch the bench
+    times (keep_stages off); the oracle computes sampled output pixels one by
+    one on crops large enough that the crop edge cannot reach them."""
+    H = W = 512
+    T, ks = 5, 7
+    p, f = case(H, W, ks, 48, T, cfg=2)
+    got = _gpu_forward(p, f, keep=False)[0]
+    M = 2 * (ks // 2) * T
+    g = np.random.Generator(np.random.PCG64(7))
+    pts = [(0, 0), (0, 511), (511, 0), (511, 511), (0, 200), (300, 511), (2, 3), (255, 256)]
+    pts += [tuple(x) for x in g.integers(0, 512, size=(8, 2))]
+    for (y, x) in pts:
+        y0, y1, x0, x1 = crop_window(H, W, y, x, M)
+        ref = oracle.forward(f[0, y0:y1, x0:x1], p)[-1][y - y0, x - x0]
+        assert abs(got[y, x] - ref) <= TOL_U_FP32, (y, x, got[y, x], ref)
