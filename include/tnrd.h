@@ -24,7 +24,7 @@
  *  - `workspace` is caller-allocated device scratch of at least the size that
  *    tnrd_workspace_size() returns for the same arguments; it may be reused
  *    between calls on the same stream.
- *  - Supported models: (ksize, nfilt) in {(3,4), (5,24), (7,48)}, nrbf <= 128,
+ *  - Supported models: (ksize, nfilt) in {(3,4), (5,24), (7,48)}, nrbf <= 64,
  *    rbf_delta >= rbf_gamma > 0 (the RBF sum is evaluated over the 13 centres
  *    nearest to z; the dropped terms are below 1.4e-9 * max|w|).  Images need
  *    H >= ksize and W >= ksize; N == 0 is a no-op.

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <string>
 
 namespace {
@@ -77,8 +78,14 @@ tnrd::RbfConst make_rbf(const tnrd_params* p)
     rc.mu0 = (float)mu0;
     rc.delta = (float)d;
     rc.inv_delta = (float)(1.0 / d);
-    rc.zlo = (float)(mu0 - (W + 0.5) * d);
-    rc.zhi = (float)(mu0 + (p->nrbf - 1 + W + 0.5) * d);
+    rc.zlo = (float)(mu0 - (W + 0.49) * d);
+    rc.zhi = (float)(mu0 + (p->nrbf - 1 + W + 0.49) * d);
+    rc.t_off = (float)(-mu0 / d);
+    rc.tmax = (float)(p->nrbf - 1 + W);
+    const double log2e = 1.4426950408889634;
+    rc.c_q2 = (float)(log2e * d / (g * g));
+    rc.c_p2a = (float)(log2e / (2.0 * g * g));
+    rc.c_p2b = (float)(log2e * W * d / (g * g));
     rc.cq = (float)(d / (g * g));
     rc.half_inv_g2 = (float)(1.0 / (2.0 * g * g));
     rc.inv_g2 = (float)(1.0 / (g * g));
@@ -90,19 +97,25 @@ tnrd::RbfConst make_rbf(const tnrd_params* p)
 // Pick the fused tile height minimising (max tiles per SM) x (work per tile).
 int pick_fused_th(int ks, int nk, int N, int H, int W)
 {
+    const int* list = tnrd::fused_th_list(ks);
+    if (const char* env = std::getenv("TNRD_FUSED_TH")) {   // tuning override
+        const int v = std::atoi(env);
+        for (const int* p = list; *p; ++p)
+            if (*p == v) return v;
+    }
+    (void)nk;
     int nsm = 148;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int R = ks / 2;
+    const int R = ks / 2, tw = 32 - 2 * R;
     double best = 1e300;
-    int best_th = 32;
-    for (int i = 0; i < tnrd::kNumFusedTH; ++i) {
-        const int th = tnrd::kFusedTH[i];
-        const long long tiles = (long long)N * ((H + th - 1) / th) * ((W + 31) / 32);
-        const long long per_sm = (tiles + nsm - 1) / nsm;
-        const double work = (double)(th + 2 * R) * (32 + 2 * R) * 2.0 + (double)th * 32;
-        const double cost = per_sm * work;
+    int best_th = list[0];
+    for (const int* p = list; *p; ++p) {
+        const int th = *p;
+        const long long tiles = (long long)N * ((H + th - 1) / th) * ((W + tw - 1) / tw);
+        const long long per_sm = (tiles + 2 * nsm - 1) / (2 * nsm);
+        const double cost = per_sm * (double)(th + 4 * R);
         if (cost < best * 0.999) {
             best = cost;
             best_th = th;
@@ -211,7 +224,7 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.H = H;
             a.W = W;
             a.pitch = pitch;
-            a.tiles_x = (W + 31) / 32;
+            a.tiles_x = (W + (32 - 2 * (ks / 2)) - 1) / (32 - 2 * (ks / 2));
             a.tiles_y = (H + th - 1) / th;
             a.k = kt;
             a.w = wt;

@@ -22,26 +22,32 @@ struct StageArgs {
 template <int KS, int NK, int TH>
 struct FusedCfg {
     static constexpr int R = KS / 2;
-    static constexpr int TW = 32;
-    static constexpr int NWARP = 4;
+    static constexpr int TW = 32 - 2 * R;          // output columns per tile
+    static constexpr int NWARP = NK >= 8 ? 8 : NK;
     static constexpr int NTHREADS = NWARP * 32;
+    static constexpr int MINB = 2;                 // CTAs per SM the registers are sized for
     static constexpr int FPW = NK / NWARP;
     static_assert(NK % NWARP == 0, "filters must split evenly over the warps");
-    static constexpr int UH = TH + 4 * R, UW = TW + 4 * R;
-    static constexpr int UP = UW | 1;          // odd pitch spreads column chunks over banks
-    static constexpr int ZH = TH + 2 * R, ZW = TW + 2 * R;
-    static constexpr int HP = ZW | 1;
-    static constexpr int XC = ZW - 32;         // columns beyond the 32 lanes (= 2R)
-    static constexpr int NCH = 32 / XC;        // row chunks for them
-    static constexpr int CHT = (ZH + NCH - 1) / NCH;
+    static constexpr int GROUPS_EXT = (TH + 6 * R + KS - 1) / KS;
+    static constexpr int GROUPS_INT = (TH + 4 * R + KS - 1) / KS;
+    static constexpr int UH_EXT = GROUPS_EXT * KS;
+    static constexpr int UH_INT = R + GROUPS_INT * KS;
+    static constexpr int UH = UH_EXT > UH_INT ? UH_EXT : UH_INT;   // u rows from y0 - 3R
+    static constexpr int UW = 32 + 2 * R;          // u cols from x0 - 2R
+    static constexpr int UP = UW;
+    static constexpr int H_FL = (TH + 2 * R) * 32; // h rows from y0 - R, one column per lane
     static constexpr int KPAD = (KS * KS + 3) & ~3;
     static constexpr int WPADN = MAX_NRBF + 2 * RBF_WPAD;
     static constexpr int U_FL = UH * UP;
-    static constexpr int V_FL = UH * UP;
-    static constexpr int H_FL = ZH * HP;
     static constexpr int KW_FL = KPAD + WPADN;
-    static constexpr int SMEM_FL = U_FL + NWARP * (V_FL + H_FL + KW_FL);
-    static constexpr size_t SMEM_BYTES = sizeof(float) * (size_t)SMEM_FL;
+    static constexpr int SMEM_FL = U_FL + NWARP * (H_FL + KW_FL);
+    static constexpr int TAB_OFF = (SMEM_FL + 3) & ~3;   // 16-byte aligned table base
+    // dynamic shared memory: the fixed part plus one RBF coefficient table per warp
+    static constexpr size_t smem_bytes(int nrbf)
+    {
+        (void)nrbf;
+        return sizeof(float) * ((size_t)TAB_OFF + (size_t)NWARP * RBF_TP * RBF_NCOEF);
+    }
 };
 
 // Tile origin along one axis: tiles of size T cover [0, n); the last tile is

@@ -14,7 +14,7 @@ namespace tnrd {
 // 2 * exp(-21.1) * max|w| < 1.4e-9 * max|w| -- far below FP32 rounding of phi.
 constexpr int RBF_WIN = 6;
 constexpr int RBF_TERMS = 2 * RBF_WIN + 1;
-constexpr int MAX_NRBF = 128;
+constexpr int MAX_NRBF = 64;
 // w is staged in shared memory with 2*RBF_WIN zeros on each side, so that the
 // 13-term window never needs a bounds test: wp[j + 2*RBF_WIN] = w_j.
 constexpr int RBF_WPAD = 2 * RBF_WIN;
@@ -23,13 +23,40 @@ struct RbfConst {
     float mu0;          // first centre
     float delta;        // centre spacing
     float inv_delta;
-    float zlo, zhi;     // z is clamped to [mu_0 - 6.5 delta, mu_last + 6.5 delta]
+    float zlo, zhi;     // z is clamped to [mu_0 - 6.49 delta, mu_last + 6.49 delta]
+    float t_off;        // -mu0 / delta
+    float tmax;         // nrbf - 1 + RBF_WIN: largest window centre index
     float cq;           // delta / gamma^2
     float half_inv_g2;  // 1 / (2 gamma^2)
     float inv_g2;       // 1 / gamma^2
-    int jmax;           // nrbf - 1 + RBF_WIN: largest window centre index
+    float c_q2;         // log2(e) delta / gamma^2
+    float c_p2a;        // log2(e) / (2 gamma^2)
+    float c_p2b;        // log2(e) RBF_WIN delta / gamma^2
+    int jmax;           // nrbf - 1 + RBF_WIN
     float E[RBF_WIN + 1];  // exp(-m^2 delta^2 / (2 gamma^2)), m = 0..RBF_WIN
 };
+
+// Window coefficient table of one influence function, built in shared memory
+// per filter, coefficient-major: entry (n, r) at tab[n * rows + r] with
+// r = j0 + RBF_WIN (j0 = -RBF_WIN .. nrbf-1+RBF_WIN) and
+//   C(n, r) = w_{j0 - RBF_WIN + n} * E[|n - RBF_WIN|],  n = 0 .. 2 RBF_WIN
+// (w_j = 0 outside [0, nrbf)).  Each lane gathers the 13 entries of its own
+// row; with this layout two lanes collide on a bank only when their rows
+// differ by a multiple of 32 centres.
+constexpr int RBF_NCOEF = RBF_TERMS;
+// Table pitch (rows) fixed at compile time so that the 13 gathers of a lane use
+// immediate offsets; tables hold up to MAX_NRBF centres.
+constexpr int RBF_TP = MAX_NRBF + 2 * RBF_WIN;
+
+__device__ __host__ __forceinline__ int rbf_table_rows(int nrbf) { return nrbf + 2 * RBF_WIN; }
+
+// 2^x with the SFU's ex2.approx (max relative error about 2^-22).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // Half-sample symmetric index into [0, n), any integer i (period 2n).
 __device__ __forceinline__ int sym_idx(int i, int n)
@@ -75,6 +102,62 @@ __device__ __forceinline__ float rbf_phi(float z, const float* wp, const RbfCons
         p = fmaf(p, win.q, wr[n] * rc.E[m < 0 ? -m : m]);
     }
     return win.pre * p;
+}
+
+// Window set-up from the table's point of view: j0 (clamped nearest centre),
+// q = exp(s delta / gamma^2) and pre = exp(-s^2/(2 gamma^2) - RBF_WIN s delta / gamma^2)
+// computed as powers of two with pre-scaled arguments; the nearest centre is
+// found with the 1.5 * 2^23 rounding trick (exact for |t| < 2^22).
+struct RbfWin2 {
+    float s, q, pre;
+    int row;   // table row j0 + RBF_WIN
+};
+
+__device__ __forceinline__ RbfWin2 rbf_win2(float z, const RbfConst& rc)
+{
+    RbfWin2 r;
+    const float zc = fminf(fmaxf(z, rc.zlo), rc.zhi);
+    // zc within 6.49 spacings of the grid: t rounds into [-RBF_WIN, nrbf-1+RBF_WIN]
+    const float t = fmaf(zc, rc.inv_delta, rc.t_off);
+    const float tm = t + 12582912.0f;
+    const float jf = tm - 12582912.0f;
+    r.row = __float_as_int(tm) - 0x4B400000 + RBF_WIN;
+    r.s = zc - fmaf(jf, rc.delta, rc.mu0);
+    r.q = ex2_approx(r.s * rc.c_q2);
+    r.pre = ex2_approx(-r.s * fmaf(r.s, rc.c_p2a, rc.c_p2b));
+    return r;
+}
+
+// Horner evaluation in q of the 13 window coefficients of table row `row`
+// (coefficient-major table of pitch RBF_TP).
+__device__ __forceinline__ float rbf_horner(const float* __restrict__ tab, int row, float q)
+{
+    const float* c = tab + row;
+    float p = c[(2 * RBF_WIN) * RBF_TP];
+#pragma unroll
+    for (int n = 2 * RBF_WIN - 1; n >= 0; --n) p = fmaf(p, q, c[n * RBF_TP]);
+    return p;
+}
+
+// phi(z) from a coefficient table.
+__device__ __forceinline__ float rbf_phi_tab(float z, const float* __restrict__ tab,
+                                             const RbfConst& rc)
+{
+    const RbfWin2 w = rbf_win2(z, rc);
+    return w.pre * rbf_horner(tab, w.row, w.q);
+}
+
+// Builds the coefficient table of one filter from its padded weights wp
+// (wp[j + RBF_WPAD] = w_j, zeros elsewhere); cooperative over the 32 lanes.
+__device__ __forceinline__ void rbf_build_table(float* tab, const float* wp, int nrbf,
+                                                const RbfConst& rc, int lane)
+{
+    const int rows = rbf_table_rows(nrbf);
+    for (int e = lane; e < RBF_NCOEF * rows; e += 32) {
+        const int n = e / rows, r = e - n * rows;
+        const int m = n - RBF_WIN;
+        tab[n * RBF_TP + r] = wp[r + n] * rc.E[m < 0 ? -m : m];
+    }
 }
 
 // Prox of G(u) = lam (u^2 - 2 f^2 log u) at u~ (Eq. subproblemGIdiv).  For

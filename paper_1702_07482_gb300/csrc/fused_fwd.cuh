@@ -1,155 +1,162 @@
 // Fused FP32 forward stage of TRDMD (Eq. diffusionprocessfinal):
 //   u_t = prox(u_{t-1} - sum_i K_i^T phi_i(K_i u_{t-1}))
-// in ONE kernel per stage.  A CTA owns a TH x 32 output tile; the N_k filter
-// responses z_i and v_i = phi_i(z_i) never leave shared memory/registers and
+// in ONE kernel per stage.  The N_k filter responses z_i, v_i = phi_i(z_i)
+// live only in registers; u_{t-1} is staged once per tile in shared memory and
 // only u_t is written to HBM.
 //
-// Tile geometry ("buffer" coordinates have their origin at image pixel
-// (y0 - 2R, x0 - 2R), R = ksize/2):
-//   U : u_{t-1} over rows [0, TH+4R) x cols [0, 32+4R), symmetric-padded
-//   z-region (where z_i, v_i are needed): rows [R, TH+3R) x cols [R, 32+3R)
-//   tile (outputs): rows [2R, TH+2R) x cols [2R, 34+... ) i.e. 32 columns
-//   V : v_i over the same extents as U; zero outside the image and outside
-//       the z-region (the zero margin lets the adjoint read without tests)
-//   h = sum_i C_i^T v_i, the zero-extended adjoint, over the "extended region"
-//       (= z-region) for tiles on the image border, over the tile otherwise.
-// The exact transpose of the symmetric-padded convolution folds h back:
-//   (K^T v)(q) = sum_{q' : sym(q') = q} h(q'),
-// so border pixels add the h values of their mirror images outside the image.
-//
-// Work split: 4 warps, each owning nfilt/4 filters for the whole tile, so the
-// filter loop needs no CTA barrier.  Inside a warp each lane owns one column
-// and walks it top to bottom ("strip"), keeping ksize rolling accumulators;
-// every input row read from shared memory (ksize values) feeds ksize^2 FMAs.
+// Tile: TH rows x TW = 32 - 2R output columns, R = ksize/2.  Warp lane j owns
+// z-column x0 - R + j, so the 32 lanes cover the tile plus the R-wide column
+// halo that the adjoint needs.  Each warp owns nfilt/NWARP filters; for each
+// filter it walks down its columns once ("walk"), one input row per step:
+//   1. z rows:   z(i) = sum_{a,b} k[a][b] u(i + R - a, x + R - b), kept in ksize
+//                rolling accumulators; row i is complete after input row i + R.
+//   2. v = phi(z) for the completed row (0 outside the image).
+//   3. the 2R+1 v values of the neighbouring columns come from warp shuffles,
+//   4. h rows:   h(i) = sum_{a,b} k[a][b] v(i - R + a, x - R + b), again ksize
+//                rolling accumulators; row i is complete after v row i + R,
+//                and is added into the warp's h buffer in shared memory.
+// h is the adjoint of the zero-extended convolution; the exact transpose of
+// the symmetric-padded convolution folds it back at the border:
+//   (K^T v)(q) = sum_{q' : sym(q') = q} h(q').
+// Tiles on the top/bottom row of tiles walk R extra h rows on each side (the
+// mirror sources); on the left/right the extra columns are the halo lanes,
+// whose missing neighbours lie outside the image where v = 0.
+// The epilogue sums the warps' h, folds, applies the prox and stores u_t.
 #pragma once
 #include "args.cuh"
 
 namespace tnrd {
 
-// z strip: lane column j (buffer coords), outputs rows [i0, i1).
-//   z(i, j) = sum_{a,b} k[a][b] U[i + R - a][j + R - b]
-// Input row rho = i0 - R + m feeds output i with a = (i - i0) + 2R - m; output
-// i is complete after a = 0.  Accumulator slot of output i: (i - i0) mod KS.
-template <int KS, int UP>
-__device__ __forceinline__ void z_strip(const float* __restrict__ sU, float* __restrict__ sV,
-                                        const float (&kr)[KS][KS], int j, int i0, int i1,
-                                        int img_y0, int img_x0, int H, int W,
-                                        const float* wp, const RbfConst& rc)
+// Value of lane + D's x.  With EDGE, 0 when lane + D falls outside the warp;
+// without, whatever the shuffle returns there (used only by halo lanes whose
+// h values an interior tile never reads).
+template <int D, bool EDGE>
+__device__ __forceinline__ float shfl_rel(float x, int lane)
 {
-    constexpr int R = KS / 2;
-    float acc[KS];
-#pragma unroll
-    for (int s = 0; s < KS; ++s) acc[s] = 0.0f;
-    const int nsteps = (i1 - i0) + 2 * R;
-    const int x_img = img_x0 + j;
-    const bool col_in = (unsigned)x_img < (unsigned)W;
-    const float* src = sU + (i0 - R) * UP + j + R;
-#pragma unroll 1
-    for (int m0 = 0; m0 < nsteps; m0 += KS) {
-#pragma unroll
-        for (int mm = 0; mm < KS; ++mm) {
-            const int m = m0 + mm;
-            if (m < nsteps) {
-                const float* row = src + m * UP;
-                float in[KS];
-#pragma unroll
-                for (int b = 0; b < KS; ++b) in[b] = row[-b];
-#pragma unroll
-                for (int a = 0; a < KS; ++a) {
-                    const int s = (mm + a + 2 * KS - 2 * R) % KS;
-#pragma unroll
-                    for (int b = 0; b < KS; ++b) acc[s] = fmaf(kr[a][b], in[b], acc[s]);
-                }
-                const int sf = (mm + 2 * KS - 2 * R) % KS;
-                if (m >= 2 * R) {
-                    const int i = i0 + m - 2 * R;
-                    const int y_img = img_y0 + i;
-                    float v = 0.0f;
-                    if (col_in && (unsigned)y_img < (unsigned)H) v = rbf_phi(acc[sf], wp, rc);
-                    sV[i * UP + j] = v;
-                }
-                acc[sf] = 0.0f;
-            }
-        }
+    if constexpr (D == 0) {
+        return x;
+    } else if constexpr (D > 0) {
+        const float y = __shfl_down_sync(0xffffffffu, x, D);
+        return (!EDGE || lane + D < 32) ? y : 0.0f;
+    } else {
+        const float y = __shfl_up_sync(0xffffffffu, x, -D);
+        return (!EDGE || lane + D >= 0) ? y : 0.0f;
     }
 }
 
-// h strip: lane column j, outputs rows [i0, i1), accumulated into sH.
-//   h(i, j) = sum_{a,b} k[a][b] V[i - R + a][j - R + b]
-// Input row rho = i0 - R + m feeds output i with a = m - (i - i0); output i is
-// complete after a = 2R.
-template <int KS, int UP, int HP>
-__device__ __forceinline__ void h_strip(const float* __restrict__ sV, float* __restrict__ sH,
-                                        const float (&kr)[KS][KS], int j, int i0, int i1)
+template <int KS, int B, bool EDGE>
+__device__ __forceinline__ void gather_row(float (&vw)[KS], float v, int lane)
+{
+    if constexpr (B < KS) {
+        vw[B] = shfl_rel<B - KS / 2, EDGE>(v, lane);
+        gather_row<KS, B + 1, EDGE>(vw, v, lane);
+    }
+}
+
+// One group of KS walk steps starting at step m0 (see the file comment).
+//   urow  : shared-memory pointer to u row of step 0 at this lane's z-column
+//           minus 2R columns (u(step m, column offset c - R) = urow[m*UP + c + R])
+//   hrow  : this warp's h buffer at the h row completed at step 0, this lane
+//   zrow0 : image row of the z row completed at step 0
+// INTERIOR: the tile touches no image border, so every z of a valid step is
+// inside the image and no v needs masking (partial z rows of the first 2R
+// steps only reach h rows above the tile, which are never stored).
+template <int KS, int UP, bool INTERIOR>
+__device__ __forceinline__ void walk_group(const float* __restrict__ urow, float* __restrict__ hrow,
+                                           const float (&kr)[KS][KS], float (&za)[KS],
+                                           float (&ha)[KS], int m0, int zrow0, int H, bool col_in,
+                                           int mz_lo, int mh_lo, int mh_hi, int lane,
+                                           const float* __restrict__ tab, const RbfConst& rc)
 {
     constexpr int R = KS / 2;
-    float acc[KS];
 #pragma unroll
-    for (int s = 0; s < KS; ++s) acc[s] = 0.0f;
-    const int nsteps = (i1 - i0) + 2 * R;
-    const float* src = sV + (i0 - R) * UP + j - R;
-    float* dst = sH + (i0 - R) * HP + (j - R);
-#pragma unroll 1
-    for (int m0 = 0; m0 < nsteps; m0 += KS) {
+    for (int mm = 0; mm < KS; ++mm) {
+        const int m = m0 + mm;
+        const float* row = urow + m * UP;
+        float in[KS];
 #pragma unroll
-        for (int mm = 0; mm < KS; ++mm) {
-            const int m = m0 + mm;
-            if (m < nsteps) {
-                const float* row = src + m * UP;
-                float in[KS];
+        for (int b = 0; b < KS; ++b) in[b] = row[2 * R - b];
+        // z: the input row feeds z slots (step + a) mod KS; slot mm completes (a = 0)
 #pragma unroll
-                for (int b = 0; b < KS; ++b) in[b] = row[b];
+        for (int b = 0; b < KS; ++b) {
 #pragma unroll
-                for (int a = 0; a < KS; ++a) {
-                    const int s = (mm - a + 2 * KS) % KS;
-#pragma unroll
-                    for (int b = 0; b < KS; ++b) acc[s] = fmaf(kr[a][b], in[b], acc[s]);
-                }
-                const int sf = (mm - 2 * R + 2 * KS) % KS;
-                if (m >= 2 * R) {
-                    float* o = dst + (m - 2 * R) * HP;
-                    *o += acc[sf];
-                }
-                acc[sf] = 0.0f;
+            for (int a = 0; a < KS; ++a) {
+                const int s = (mm + a) % KS;
+                za[s] = fmaf(kr[a][b], in[b], za[s]);
             }
         }
+        const float z = za[mm];
+        za[mm] = 0.0f;
+        float v = rbf_phi_tab(z, tab, rc);
+        if constexpr (!INTERIOR) {
+            const int zi = zrow0 + m;
+            const bool v_ok = col_in && (m >= mz_lo) && ((unsigned)zi < (unsigned)H);
+            v = v_ok ? v : 0.0f;
+        }
+        float vw[KS];
+        gather_row<KS, 0, !INTERIOR>(vw, v, lane);
+        // h: the v row feeds h slots (step - a) mod KS; slot (mm - 2R) completes (a = 2R)
+#pragma unroll
+        for (int b = 0; b < KS; ++b) {
+#pragma unroll
+            for (int a = 0; a < KS; ++a) {
+                const int s = (mm - a + 2 * KS) % KS;
+                ha[s] = fmaf(kr[a][b], vw[b], ha[s]);
+            }
+        }
+        const int sf = (mm - 2 * R + 2 * KS) % KS;
+        if (m >= mh_lo && m < mh_hi) hrow[m * 32] += ha[sf];
+        ha[sf] = 0.0f;
     }
 }
 
 template <int KS, int NK, int TH>
-__global__ void __launch_bounds__(FusedCfg<KS, NK, TH>::NTHREADS, 3)
+__global__ void __launch_bounds__(FusedCfg<KS, NK, TH>::NTHREADS, FusedCfg<KS, NK, TH>::MINB)
 fused_stage_fwd(const StageArgs a)
 {
     using C = FusedCfg<KS, NK, TH>;
     constexpr int R = C::R;
+    constexpr int TW = C::TW;
     extern __shared__ __align__(16) float smem[];
-    float* sU = smem;
-    float* sV = sU + C::U_FL;
-    float* sH = sV + C::NWARP * C::V_FL;
+    float* sU = smem;                          // rows [y0-3R, ...) x cols [x0-2R, x0+TW+2R)
+    float* sH = sU + C::U_FL;                  // per warp: rows [y0-R, y0+TH+R) x 32 lanes
     float* sKW = sH + C::NWARP * C::H_FL;
+    float* sTab = smem + C::TAB_OFF;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = blockIdx.y;
     const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x - ty * a.tiles_x;
     const int H = a.H, W = a.W;
-    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, 32, W);
-    const bool border = (ty == 0) || (ty == a.tiles_y - 1) || (tx == 0) || (tx == a.tiles_x - 1);
+    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
+    const bool ext = (ty == 0) || (ty == a.tiles_y - 1);
+    const bool border = ext || (tx == 0) || (tx == a.tiles_x - 1);
     const float* uin = a.u_in + (size_t)n * a.img_stride;
 
-    for (int i = threadIdx.x; i < C::NWARP * (C::V_FL + C::H_FL + C::KW_FL); i += C::NTHREADS)
-        sV[i] = 0.0f;
     for (int idx = threadIdx.x; idx < C::UH * C::UW; idx += C::NTHREADS) {
         const int i = idx / C::UW, j = idx - i * C::UW;
-        const int yy = sym_idx(y0 - 2 * R + i, H), xx = sym_idx(x0 - 2 * R + j, W);
+        const int yy = sym_idx(y0 - 3 * R + i, H), xx = sym_idx(x0 - 2 * R + j, W);
         sU[i * C::UP + j] = uin[(size_t)yy * a.pitch + xx];
     }
-    __syncthreads();
-
-    float* myV = sV + warp * C::V_FL;
     float* myH = sH + warp * C::H_FL;
     float* myK = sKW + warp * C::KW_FL;
     float* myW = myK + C::KPAD;
-    const int img_y0 = y0 - 2 * R, img_x0 = x0 - 2 * R;
+    float* myT = sTab + warp * RBF_TP * RBF_NCOEF;
+    for (int e = lane; e < C::H_FL; e += 32) myH[e] = 0.0f;
+    for (int e = lane; e < C::WPADN; e += 32) myW[e] = 0.0f;
+    __syncthreads();
+
+    // Walk geometry.  h rows [hy0, hy0 + nh); step m reads u row hy0 - 2R + m,
+    // completes z row hy0 - 3R + m (valid from m = 2R) and h row hy0 - 4R + m
+    // (valid for m in [4R, nh + 4R)).  Steps run in whole groups of KS; the
+    // U buffer has rows for the overhang and its results are never stored.
+    const int hy0 = ext ? y0 - R : y0;
+    const int nh = ext ? TH + 2 * R : TH;
+    const int nsteps = nh + 4 * R;
+    const int ub0 = ext ? 0 : R;                         // U buffer row of step 0
+    const float* urow = sU + ub0 * C::UP + lane;
+    float* hrow = myH + (hy0 - 4 * R - (y0 - R)) * 32 + lane;
+    const int zrow0 = hy0 - 3 * R;
+    const bool col_in = (unsigned)(x0 - R + lane) < (unsigned)W;
 
 #pragma unroll 1
     for (int fl = 0; fl < C::FPW; ++fl) {
@@ -157,33 +164,26 @@ fused_stage_fwd(const StageArgs a)
         for (int e = lane; e < KS * KS; e += 32) myK[e] = __ldg(a.k + fi * KS * KS + e);
         for (int e = lane; e < a.nrbf; e += 32) myW[RBF_WPAD + e] = __ldg(a.w + fi * a.nrbf + e);
         __syncwarp();
+        rbf_build_table(myT, myW, a.nrbf, a.rc, lane);
         float kr[KS][KS];
 #pragma unroll
         for (int p = 0; p < KS; ++p)
 #pragma unroll
             for (int q = 0; q < KS; ++q) kr[p][q] = myK[p * KS + q];
-
-        // z_i and v_i over the z-region: 32 full columns, then the 2R
-        // remaining columns in row chunks spread over the lanes.
-        z_strip<KS, C::UP>(sU, myV, kr, R + lane, R, R + C::ZH, img_y0, img_x0, H, W, myW, a.rc);
-        if (lane < C::XC * C::NCH) {
-            const int c = lane % C::XC, ch = lane / C::XC;
-            const int i0 = R + ch * C::CHT, i1 = min(i0 + C::CHT, R + C::ZH);
-            if (i0 < i1)
-                z_strip<KS, C::UP>(sU, myV, kr, R + 32 + c, i0, i1, img_y0, img_x0, H, W, myW, a.rc);
-        }
         __syncwarp();
-
-        // h += C_i^T v_i over the tile, or over the extended region on a border tile.
+        float za[KS], ha[KS];
+#pragma unroll
+        for (int s = 0; s < KS; ++s) za[s] = ha[s] = 0.0f;
         if (!border) {
-            h_strip<KS, C::UP, C::HP>(myV, myH, kr, 2 * R + lane, 2 * R, 2 * R + TH);
+#pragma unroll 1
+            for (int m0 = 0; m0 < nsteps; m0 += KS)
+                walk_group<KS, C::UP, true>(urow, hrow, kr, za, ha, m0, zrow0, H, col_in, 2 * R,
+                                            4 * R, nsteps, lane, myT, a.rc);
         } else {
-            h_strip<KS, C::UP, C::HP>(myV, myH, kr, R + lane, R, R + C::ZH);
-            if (lane < C::XC * C::NCH) {
-                const int c = lane % C::XC, ch = lane / C::XC;
-                const int i0 = R + ch * C::CHT, i1 = min(i0 + C::CHT, R + C::ZH);
-                if (i0 < i1) h_strip<KS, C::UP, C::HP>(myV, myH, kr, R + 32 + c, i0, i1);
-            }
+#pragma unroll 1
+            for (int m0 = 0; m0 < nsteps; m0 += KS)
+                walk_group<KS, C::UP, false>(urow, hrow, kr, za, ha, m0, zrow0, H, col_in, 2 * R,
+                                             4 * R, nsteps, lane, myT, a.rc);
         }
         __syncwarp();
     }
@@ -191,13 +191,12 @@ fused_stage_fwd(const StageArgs a)
 
     // Epilogue: g = fold(sum over warps of h), u_t = prox(u_{t-1} - g).
     const float lam = __ldg(a.lam);
-    const int tiles_y = a.tiles_y, tiles_x = a.tiles_x;
-    const int wy0 = tile_split(ty, TH, H, tiles_y, R), wy1 = tile_split(ty + 1, TH, H, tiles_y, R);
-    const int wx0 = tile_split(tx, 32, W, tiles_x, R), wx1 = tile_split(tx + 1, 32, W, tiles_x, R);
+    const int wy0 = tile_split(ty, TH, H, a.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, a.tiles_y, R);
+    const int wx0 = tile_split(tx, TW, W, a.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, a.tiles_x, R);
     const float* fimg = a.f + (size_t)n * a.img_stride;
     float* uout = a.u_out + (size_t)n * a.img_stride;
-    for (int idx = threadIdx.x; idx < TH * 32; idx += C::NTHREADS) {
-        const int qy = y0 + idx / 32, qx = x0 + (idx & 31);
+    for (int idx = threadIdx.x; idx < TH * TW; idx += C::NTHREADS) {
+        const int qy = y0 + idx / TW, qx = x0 + idx % TW;
         if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
         int sy[2], sx[2];
         int nsy = 1, nsx = 1;
@@ -212,14 +211,14 @@ fused_stage_fwd(const StageArgs a)
         float g = 0.0f;
         for (int p = 0; p < nsy; ++p) {
             for (int q = 0; q < nsx; ++q) {
-                const int hi = sy[p] - y0 + R, hj = sx[q] - x0 + R;  // H-buffer coords
+                const int hi = sy[p] - (y0 - R), hj = sx[q] - (x0 - R);
                 float hs = 0.0f;
 #pragma unroll
-                for (int wq = 0; wq < C::NWARP; ++wq) hs += sH[wq * C::H_FL + hi * C::HP + hj];
+                for (int wq = 0; wq < C::NWARP; ++wq) hs += sH[wq * C::H_FL + hi * 32 + hj];
                 g += hs;
             }
         }
-        const float up = sU[(qy - y0 + 2 * R) * C::UP + (qx - x0 + 2 * R)];
+        const float up = sU[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R)];
         const float fv = __ldg(fimg + (size_t)qy * a.pitch + qx);
         uout[(size_t)qy * a.pitch + qx] = prox_idiv(up - g, fv, lam);
     }

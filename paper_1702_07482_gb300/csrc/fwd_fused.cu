@@ -10,39 +10,41 @@ template <int KS, int NK, int TH>
 cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
 {
     using C = FusedCfg<KS, NK, TH>;
+    const size_t smem = C::smem_bytes(a.nrbf);
     cudaError_t e = cudaFuncSetAttribute(fused_stage_fwd<KS, NK, TH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM_BYTES);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(a.tiles_x * a.tiles_y, N);
-    fused_stage_fwd<KS, NK, TH><<<grid, C::NTHREADS, C::SMEM_BYTES, s>>>(a);
+    fused_stage_fwd<KS, NK, TH><<<grid, C::NTHREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int KS, int NK, int TH>
-int occupancy_one()
+int occupancy_one(int nrbf)
 {
     using C = FusedCfg<KS, NK, TH>;
+    const size_t smem = C::smem_bytes(nrbf);
     if (cudaFuncSetAttribute(fused_stage_fwd<KS, NK, TH>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)C::SMEM_BYTES) != cudaSuccess)
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_stage_fwd<KS, NK, TH>,
-                                                      C::NTHREADS, C::SMEM_BYTES) != cudaSuccess)
+                                                      C::NTHREADS, smem) != cudaSuccess)
         return 0;
     return nb;
 }
 
+// Tile heights per filter size: TH + 4R is a multiple of ksize, so the walk of
+// an interior tile has no partial group of steps.
 #define TNRD_FUSED_CASES(X)                                                         \
-    X(3, 4, 16) X(3, 4, 24) X(3, 4, 32) X(5, 24, 16) X(5, 24, 24) X(5, 24, 32)     \
-    X(7, 48, 16) X(7, 48, 24) X(7, 48, 32)
+    X(3, 4, 17) X(3, 4, 23) X(3, 4, 29) X(5, 24, 17) X(5, 24, 22) X(5, 24, 27)     \
+    X(5, 24, 32) X(7, 48, 16) X(7, 48, 23) X(7, 48, 30) X(7, 48, 37)
 
 }  // namespace
 
-size_t fused_fwd_smem(int ks, int nk, int th)
+size_t fused_fwd_smem(int ks, int nk, int th, int nrbf)
 {
-#define X(K, N, T) if (ks == K && nk == N && th == T) return FusedCfg<K, N, T>::SMEM_BYTES;
+#define X(K, N, T) if (ks == K && nk == N && th == T) return FusedCfg<K, N, T>::smem_bytes(nrbf);
     TNRD_FUSED_CASES(X)
 #undef X
     return 0;
@@ -56,9 +58,9 @@ int fused_fwd_threads(int ks, int nk, int th)
     return 0;
 }
 
-int fused_fwd_occupancy(int ks, int nk, int th)
+int fused_fwd_occupancy(int ks, int nk, int th, int nrbf)
 {
-#define X(K, N, T) if (ks == K && nk == N && th == T) return occupancy_one<K, N, T>();
+#define X(K, N, T) if (ks == K && nk == N && th == T) return occupancy_one<K, N, T>(nrbf);
     TNRD_FUSED_CASES(X)
 #undef X
     return 0;

@@ -6,15 +6,21 @@
 
 namespace tnrd {
 
-// Tile heights compiled for the fused forward stage (tiles are TH x 32).
-constexpr int kFusedTH[] = {16, 24, 32};
-constexpr int kNumFusedTH = 3;
+// Tile heights compiled for the fused forward stage, per filter size (tiles are
+// TH x (32 - 2R)); 0 terminates a list.
+inline const int* fused_th_list(int ks)
+{
+    static const int k3[] = {17, 23, 29, 0};
+    static const int k5[] = {17, 22, 27, 32, 0};
+    static const int k7[] = {16, 23, 30, 37, 0};
+    return ks == 3 ? k3 : ks == 5 ? k5 : k7;
+}
 
 // Shared memory bytes / threads of one fused-forward CTA, 0 if not built.
-size_t fused_fwd_smem(int ks, int nk, int th);
+size_t fused_fwd_smem(int ks, int nk, int th, int nrbf);
 int fused_fwd_threads(int ks, int nk, int th);
 // Blocks of the fused forward kernel resident per SM (occupancy query).
-int fused_fwd_occupancy(int ks, int nk, int th);
+int fused_fwd_occupancy(int ks, int nk, int th, int nrbf);
 
 cudaError_t launch_fused_fwd(int ks, int nk, int th, const StageArgs& a, int N, cudaStream_t s);
 cudaError_t launch_unfused_fwd(int ks, const UnfArgs& a, int N, cudaStream_t s);

@@ -60,6 +60,7 @@ def test_argument_errors_launch_nothing(lib):
     assert _fwd(lib, None) == 1
     assert _fwd(lib, _params(ks=9, nk=80)) == 2
     assert _fwd(lib, _params(nrbf=0)) == 2
+    assert _fwd(lib, _params(nrbf=65)) == 2
     p = _params()
     p.rbf_delta = 5.0  # centres closer than the width: window bound does not hold
     assert _fwd(lib, p) == 2
