@@ -115,6 +115,32 @@ TNRD_API tnrd_status tnrd_backward(const tnrd_params* params, int N, int H, int 
                           float* grad_lambda, tnrd_algo algo,
                           void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
+/* Largest batch (N * H * pitch floats) that tnrd_forward_noalloc accepts:
+ * 4 Mi floats = 16 MiB, e.g. one 2048 x 2048 image or four 1024 x 1024. */
+#define TNRD_NOALLOC_MAX_FLOATS (1u << 22)
+
+/* Forward cascade for callers that cannot allocate device memory.  The paper
+ * has no counterpart; this is a deployment convenience.  Some hosts own all
+ * device memory and forbid a library from calling cudaMalloc (plugin and
+ * media frameworks with a fixed memory budget, hard real-time loops where an
+ * allocation may stall or fail), so they cannot supply tnrd_forward's
+ * workspace.  This entry point computes exactly what
+ * tnrd_forward(params, N, H, W, pitch, f, u, keep_stages = 0,
+ * TNRD_ALGO_FUSED, ...) computes, with the image between stages held in a
+ * scratch array built into the library instead of a caller workspace:
+ *  - the array is TNRD_NOALLOC_MAX_FLOATS floats; every GPU that loads the
+ *    library holds it until the process exits;
+ *  - N * H * pitch above TNRD_NOALLOC_MAX_FLOATS returns TNRD_ERR_INVALID_ARG
+ *    and launches nothing;
+ *  - the first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture;
+ *  - every call shares the one array, so calls that overlap on the GPU (two
+ *    streams, two host threads) race and give wrong results: serialise them;
+ *  - it calls no cudaMalloc, cudaFree or other allocating routine. */
+TNRD_API tnrd_status tnrd_forward_noalloc(const tnrd_params* params, int N, int H, int W,
+                                          int pitch, const float* f, float* u,
+                                          cudaStream_t stream);
+
 /* Message describing the last error status returned on this host thread. */
 TNRD_API const char* tnrd_last_error(void);
 

@@ -23,7 +23,10 @@ OP_FORWARD, OP_BACKWARD = 0, 1
 
 # Every symbol include/tnrd.h declares (checked by the tests).
 EXPORTS = ["tnrd_workspace_size", "tnrd_forward", "tnrd_backward",
-           "tnrd_last_error", "tnrd_version"]
+           "tnrd_forward_noalloc", "tnrd_last_error", "tnrd_version"]
+
+# Largest N * H * pitch (floats) tnrd_forward_noalloc accepts (TNRD_NOALLOC_MAX_FLOATS).
+NOALLOC_MAX_FLOATS = 1 << 22
 
 
 class TnrdError(RuntimeError):
@@ -62,6 +65,8 @@ def load(path: str = LIB_PATH):
         L.tnrd_forward.argtypes = [pp, i, i, i, i, P, P, i, i, P, sz, P]
         L.tnrd_backward.restype = i
         L.tnrd_backward.argtypes = [pp, i, i, i, i, P, P, P, P, P, P, P, i, P, sz, P]
+        L.tnrd_forward_noalloc.restype = i
+        L.tnrd_forward_noalloc.argtypes = [pp, i, i, i, i, P, P, P]
         L.tnrd_last_error.restype = ctypes.c_char_p
         L.tnrd_last_error.argtypes = []
         L.tnrd_version.restype = i
@@ -118,3 +123,10 @@ def tnrd_backward(params: tnrd_params, N, H, W, pitch, f, u_stages, grad_uT, gra
                                _ptr(grad_uT), _ptr(grad_u0), _ptr(grad_filters),
                                _ptr(grad_rbf_w), _ptr(grad_lambda), int(algo),
                                _ptr(workspace), int(workspace_bytes), ctypes.c_void_p(stream)))
+
+
+def tnrd_forward_noalloc(params: tnrd_params, N, H, W, pitch, f, u, stream) -> None:
+    """Forward cascade (keep_stages 0, fused) with the library's built-in
+    scratch instead of a workspace; for callers that cannot allocate."""
+    check(load().tnrd_forward_noalloc(ctypes.byref(params), N, H, W, pitch, _ptr(f), _ptr(u),
+                                      ctypes.c_void_p(stream)))

@@ -26,6 +26,20 @@ tnrd_status fail(tnrd_status s, const char* fmt, ...)
     return s;
 }
 
+}  // namespace
+
+namespace tnrd {
+
+tnrd_status set_error(tnrd_status s, const char* msg)
+{
+    g_err = msg;
+    return s;
+}
+
+}  // namespace tnrd
+
+namespace {
+
 tnrd_status cuda_fail(cudaError_t e, const char* what)
 {
     return fail(TNRD_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));

@@ -3,8 +3,12 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "args.cuh"
+#include "tnrd.h"
 
 namespace tnrd {
+
+// Records `msg` for tnrd_last_error() on this host thread and returns s.
+tnrd_status set_error(tnrd_status s, const char* msg);
 
 // Tile heights compiled for the fused forward stage, per filter size (tiles are
 // TH x (32 - 2R)); 0 terminates a list.
