@@ -1,0 +1,45 @@
+"""torch.autograd binding of the TRDMD cascade.
+
+`TNRDFunction.apply(f, filters, rbf_w, lam, mu0, delta, gamma)` runs the
+forward cascade (tnrd_forward, keeping u_0..u_T as checkpoints) and, in
+backward, the library's gradient kernels (tnrd_backward).  The noisy input f
+is data: it gets no gradient.  Training lambda through lam = exp(beta) (Sec.
+3.2, Eq. derv5) is plain torch: pass beta.exp() as `lam`.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+from . import ops
+
+
+class TNRDFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, f, filters, rbf_w, lam, mu0=-310.0, delta=10.0, gamma=10.0):
+        model = ops.Model(filters.detach().contiguous(), rbf_w.detach().contiguous(),
+                          lam.detach().contiguous(), float(mu0), float(delta), float(gamma))
+        W = f.shape[-1]
+        fp = ops.to_pitched(f.detach())
+        u_all = ops.forward(model, fp, keep_stages=True, W=W)
+        ctx.model = model
+        ctx.W = W
+        ctx.save_for_backward(fp, u_all)
+        out = u_all[-1][..., :W]
+        return out if f.dim() == 3 else out[0]
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        fp, u_all = ctx.saved_tensors
+        W = ctx.W
+        g = grad_out if grad_out.dim() == 3 else grad_out.unsqueeze(0)
+        gp = ops.to_pitched(g.contiguous().float())
+        if gp.shape[-1] != fp.shape[-1]:
+            gp = torch.nn.functional.pad(gp, (0, fp.shape[-1] - gp.shape[-1]))
+        _, gk, gw, gl = ops.backward(ctx.model, fp, u_all, gp, want_grad_u0=False, W=W)
+        return None, gk, gw, gl, None, None, None
+
+
+def trdmd(f, filters, rbf_w, lam, mu0=-310.0, delta=10.0, gamma=10.0):
+    """u_T of the T-stage cascade, differentiable in filters, rbf_w and lam."""
+    return TNRDFunction.apply(f, filters, rbf_w, lam, mu0, delta, gamma)

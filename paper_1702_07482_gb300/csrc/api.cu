@@ -163,6 +163,35 @@ FwdLayout fwd_layout(const tnrd_params* p, int N, int H, int pitch, int keep, tn
     return L;
 }
 
+struct BwdLayout {
+    size_t d = 0, e0 = 0, e1 = 0, c = 0, v = 0, pw = 0, pk = 0, pl = 0, total = 0;
+    int tiles_x = 0, tiles_y = 0, dk_tiles_x = 0, dk_tiles_y = 0, prep_blocks = 0;
+};
+
+BwdLayout bwd_layout(const tnrd_params* p, int N, int H, int W, int pitch)
+{
+    BwdLayout L;
+    const int ks = p->ksize, R = ks / 2, tw = 32 - 2 * R, th = tnrd::bwd_tile_h(ks);
+    L.tiles_x = (W + tw - 1) / tw;
+    L.tiles_y = (H + th - 1) / th;
+    L.dk_tiles_x = (W + tnrd::DK_TW - 1) / tnrd::DK_TW;
+    L.dk_tiles_y = (H + tnrd::DK_TH - 1) / tnrd::DK_TH;
+    L.prep_blocks = (H * W + 255) / 256;
+    const size_t batch = sizeof(float) * (size_t)N * H * pitch;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.d = take(batch);
+    L.e0 = take(batch);
+    L.e1 = take(batch);
+    L.c = take(batch * (size_t)p->nfilt);
+    L.v = take(batch * (size_t)p->nfilt);
+    L.pw = take(sizeof(float) * (size_t)N * L.tiles_x * L.tiles_y * p->nfilt * p->nrbf);
+    L.pk = take(sizeof(float) * (size_t)N * L.dk_tiles_x * L.dk_tiles_y * p->nfilt * ks * ks);
+    L.pl = take(sizeof(float) * (size_t)N * L.prep_blocks);
+    L.total = off;
+    return L;
+}
+
 }  // namespace
 
 extern "C" {
@@ -177,6 +206,7 @@ size_t tnrd_workspace_size(tnrd_op op, const tnrd_params* params, int N, int H, 
     if (check_params(params) != TNRD_OK) return 0;
     if (check_images(N, H, W, pitch, params->ksize) != TNRD_OK) return 0;
     if (op == TNRD_OP_FORWARD) return fwd_layout(params, N, H, pitch, keep_stages, algo).total;
+    if (op == TNRD_OP_BACKWARD) return bwd_layout(params, N, H, W, pitch).total;
     return 0;
 }
 
@@ -276,10 +306,75 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
                           float* grad_lambda, tnrd_algo algo,
                           void* workspace, size_t workspace_bytes, cudaStream_t stream)
 {
-    (void)p; (void)N; (void)H; (void)W; (void)pitch; (void)f; (void)u_stages; (void)grad_uT;
-    (void)grad_u0; (void)grad_filters; (void)grad_rbf_w; (void)grad_lambda; (void)algo;
-    (void)workspace; (void)workspace_bytes; (void)stream;
-    return fail(TNRD_ERR_UNSUPPORTED, "tnrd_backward is not built yet");
+    tnrd_status st = check_params(p);
+    if (st != TNRD_OK) return st;
+    st = check_images(N, H, W, pitch, p->ksize);
+    if (st != TNRD_OK) return st;
+    if (algo != TNRD_ALGO_FUSED)
+        return fail(TNRD_ERR_UNSUPPORTED, "tnrd_backward supports TNRD_ALGO_FUSED only");
+    if (!grad_filters || !grad_rbf_w || !grad_lambda)
+        return fail(TNRD_ERR_INVALID_ARG, "null gradient output");
+    const int T = p->T, ks = p->ksize, nk = p->nfilt, nrbf = p->nrbf;
+    if (N == 0) {
+        // no images: every gradient is zero
+        cudaError_t e = cudaMemsetAsync(grad_filters, 0, sizeof(float) * (size_t)T * nk * ks * ks, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(grad_rbf_w, 0, sizeof(float) * (size_t)T * nk * nrbf, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(grad_lambda, 0, sizeof(float) * (size_t)T, stream);
+        return e == cudaSuccess ? TNRD_OK : cuda_fail(e, "zeroing gradients");
+    }
+    if (!f || !u_stages || !grad_uT) return fail(TNRD_ERR_INVALID_ARG, "null image pointer");
+    if (!aligned16(f) || !aligned16(u_stages) || !aligned16(grad_uT) ||
+        (grad_u0 && !aligned16(grad_u0)))
+        return fail(TNRD_ERR_INVALID_ARG, "image pointers must be 16-byte aligned");
+    const BwdLayout L = bwd_layout(p, N, H, W, pitch);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(TNRD_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", L.total,
+                    workspace ? workspace_bytes : (size_t)0);
+    char* ws = (char*)workspace;
+    const size_t batch = (size_t)N * H * pitch;
+    float* ebuf[2] = {(float*)(ws + L.e0), (float*)(ws + L.e1)};
+
+    tnrd::BwdArgs a{};
+    a.f = f;
+    a.d = (float*)(ws + L.d);
+    a.cpl = (float*)(ws + L.c);
+    a.vpl = (float*)(ws + L.v);
+    a.part_w = (float*)(ws + L.pw);
+    a.part_k = (float*)(ws + L.pk);
+    a.part_l = (float*)(ws + L.pl);
+    a.img_stride = (long long)H * pitch;
+    a.H = H;
+    a.W = W;
+    a.pitch = pitch;
+    a.tiles_x = L.tiles_x;
+    a.tiles_y = L.tiles_y;
+    a.dk_tiles_x = L.dk_tiles_x;
+    a.dk_tiles_y = L.dk_tiles_y;
+    a.prep_blocks = L.prep_blocks;
+    a.nfilt = nk;
+    a.nrbf = nrbf;
+    a.rc = make_rbf(p);
+
+    for (int t = T - 1; t >= 0; --t) {
+        a.u_prev = u_stages + (size_t)t * batch;
+        a.u_cur = u_stages + (size_t)(t + 1) * batch;
+        a.e_cur = (t == T - 1) ? grad_uT : ebuf[(t + 1) & 1];
+        a.e_prev = (t == 0 && grad_u0) ? grad_u0 : ebuf[t & 1];
+        a.k = p->filters + (size_t)t * nk * ks * ks;
+        a.w = p->rbf_w + (size_t)t * nk * nrbf;
+        a.lam = p->lambda + t;
+        cudaError_t e = tnrd::launch_bwd_stage(ks, nk, a, N, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "backward stage launch");
+        e = tnrd::launch_bwd_reduce(a.part_k, N * L.dk_tiles_x * L.dk_tiles_y, nk * ks * ks,
+                                    grad_filters + (size_t)t * nk * ks * ks, stream);
+        if (e == cudaSuccess)
+            e = tnrd::launch_bwd_reduce(a.part_w, N * L.tiles_x * L.tiles_y, nk * nrbf,
+                                        grad_rbf_w + (size_t)t * nk * nrbf, stream);
+        if (e == cudaSuccess)
+            e = tnrd::launch_bwd_reduce(a.part_l, N * L.prep_blocks, 1, grad_lambda + t, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "gradient reduce launch");
+    }
+    return TNRD_OK;
 }
 
 }  // extern "C"

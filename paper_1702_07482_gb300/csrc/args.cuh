@@ -87,4 +87,68 @@ struct UnfArgs {
     RbfConst rc;
 };
 
+
+// ---------------------------------------------------------------------------
+// Backward stage (Sec. 3.2).  One stage t is four launches:
+//   bwd_prep : d = y .* e (Eq. derv2), per-block sums of x .* e (Eq. derv4)
+//   bwd_bank : z_i = K_i u, b_i = K_i d, c_i = -phi_i'(z_i) .* b_i, v_i = phi_i(z_i),
+//              e_{t-1} = d + sum_i K_i^T c_i (Eq. derv1-1), per-tile dL/dw partials;
+//              c_i and v_i of the tile's own pixels go to planes for bwd_dk
+//   bwd_dk   : per-tile dL/dk partials sum_p c_i(p) u(p+.) - v_i(p) d(p+.)
+//   bwd_reduce: fixed-order sums of all partials into this stage's gradients
+// ---------------------------------------------------------------------------
+struct BwdArgs {
+    const float* u_prev;   // u_{t-1}   [N][H][pitch]
+    const float* u_cur;    // u_t       [N][H][pitch]
+    const float* f;        //           [N][H][pitch]
+    const float* e_cur;    // dL/du_t   [N][H][pitch]
+    float* d;              // y .* e    [N][H][pitch]
+    float* e_prev;         // dL/du_{t-1} [N][H][pitch]
+    float* cpl;            // c planes  [N][nfilt][H][pitch]
+    float* vpl;            // v planes  [N][nfilt][H][pitch]
+    float* part_w;         // [N * bank tiles][nfilt][nrbf]
+    float* part_k;         // [N * dk tiles][nfilt][ks*ks]
+    float* part_l;         // [N * prep blocks]
+    long long img_stride;  // floats between images of a plane set
+    int H, W, pitch;
+    int tiles_x, tiles_y;      // bwd_bank tiling
+    int dk_tiles_x, dk_tiles_y;
+    int prep_blocks;           // per image
+    const float* k;
+    const float* w;
+    const float* lam;
+    int nfilt, nrbf;
+    RbfConst rc;
+};
+
+template <int KS, int NK, int TH>
+struct BwdCfg {
+    static constexpr int R = KS / 2;
+    static constexpr int TW = 32 - 2 * R;
+    static constexpr int NWARP = NK >= 4 ? 4 : NK;
+    static constexpr int NTHREADS = NWARP * 32;
+    static constexpr int FPW = NK / NWARP;
+    static_assert(NK % NWARP == 0, "filters must split evenly over the warps");
+    static constexpr int GROUPS_EXT = (TH + 6 * R + KS - 1) / KS;
+    static constexpr int GROUPS_INT = (TH + 4 * R + KS - 1) / KS;
+    static constexpr int UH_EXT = GROUPS_EXT * KS;
+    static constexpr int UH_INT = R + GROUPS_INT * KS;
+    static constexpr int UH = UH_EXT > UH_INT ? UH_EXT : UH_INT;
+    static constexpr int UW = 32 + 2 * R;
+    static constexpr int UP = UW;
+    static constexpr int H_FL = (TH + 2 * R) * 32;
+    static constexpr int KPAD = (KS * KS + 3) & ~3;
+    static constexpr int WPADN = MAX_NRBF + 2 * RBF_WPAD;
+    static constexpr int KW_FL = KPAD + WPADN;
+    static constexpr int HIST_FL = MAX_NRBF * 32;     // per-lane dL/dw bins: [j][lane]
+    static constexpr int TAB_FL = RBF_TP * RBF_NCOEF;
+    static constexpr int SMEM_FL = 2 * UH * UP + NWARP * (H_FL + KW_FL + HIST_FL + TAB_FL);
+    static constexpr size_t SMEM_BYTES = sizeof(float) * (size_t)SMEM_FL;
+};
+
+// bwd_dk tiling: 32-column tiles of DK_TH rows, NWARP_DK warps each owning
+// nfilt / NWARP_DK filters.
+constexpr int DK_TH = 32;
+constexpr int DK_TW = 32;
+
 }  // namespace tnrd

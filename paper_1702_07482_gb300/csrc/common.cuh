@@ -139,6 +139,38 @@ __device__ __forceinline__ float rbf_horner(const float* __restrict__ tab, int r
     return p;
 }
 
+// Horner evaluation of P(q) = sum_n C_n q^n and of q P'(q) = sum_n n C_n q^n
+// from one pass over the table row (the derivative recurrence of Horner).
+__device__ __forceinline__ void rbf_horner_d(const float* __restrict__ tab, int row, float q,
+                                             float& P, float& QdP)
+{
+    const float* c = tab + row;
+    float p = c[(2 * RBF_WIN) * RBF_TP];
+    float dp = 0.0f;
+#pragma unroll
+    for (int n = 2 * RBF_WIN - 1; n >= 0; --n) {
+        dp = fmaf(dp, q, p);
+        p = fmaf(p, q, c[n * RBF_TP]);
+    }
+    P = p;
+    QdP = q * dp;
+}
+
+// phi(z) and phi'(z) from a coefficient table.  With z = mu_{j0} + s,
+//   phi'(z) = -(1/gamma^2) sum_j w_j (z - mu_j) G_j(z)
+//           = -(1/gamma^2) (s phi(z) - delta pre sum_n (n - RBF_WIN) C_n q^n).
+__device__ __forceinline__ void rbf_phi_dphi_tab(float z, const float* __restrict__ tab,
+                                                 const RbfConst& rc, float& phi, float& dphi,
+                                                 RbfWin2& win)
+{
+    win = rbf_win2(z, rc);
+    float P, QdP;
+    rbf_horner_d(tab, win.row, win.q, P, QdP);
+    phi = win.pre * P;
+    const float m1 = win.pre * fmaf(-(float)RBF_WIN, P, QdP);   // pre sum (n - W) C_n q^n
+    dphi = -rc.inv_g2 * fmaf(win.s, phi, -rc.delta * m1);
+}
+
 // phi(z) from a coefficient table.
 __device__ __forceinline__ float rbf_phi_tab(float z, const float* __restrict__ tab,
                                              const RbfConst& rc)
