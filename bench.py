@@ -38,6 +38,10 @@ CFG_ID = 2
 # 2*N_k*k^2, phi as the method's full sum 2*N_k*N_rbf (one FMA per RBF term;
 # the exps are on top), prox ~12 flops.
 FLOPS_PER_PX_STAGE = 2 * NK * KS * KS * 2 + 2 * NK * 63 + 12
+CONFIG = {"workload": "TRDMD forward, 1 x 512x512 per GPU, 7x7x48, 63 RBF, T=5, L=1, "
+                      "fused FP32 stage kernel",
+          "H": H, "W": W, "images_per_gpu": 1, "ksize": KS, "nfilt": NK, "nrbf": 63, "T": T,
+          "looks": L, "l2": "flushed between steps (256 MiB write outside the events)"}
 
 
 def _peaks():
@@ -46,6 +50,30 @@ def _peaks():
             return json.load(fh), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# DRAM bytes (read + write) per launch of the stage kernel at this workload,
+# from one ncu capture (profiles/fused_stage_fwd_7x7x48_512x512.md), valid only
+# for the kernel sources it was taken on (their hash is checked at run time).
+_TRAFFIC = {"sources_sha256_16": "20c231ed885ecf70", "bytes_per_launch": 2205440}
+
+
+def _kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("fused_fwd.cuh", "common.cuh", "args.cuh"):
+        with open(os.path.join(ROOT, "paper_1702_07482_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _measured_traffic():
+    try:
+        if _kernel_sources_hash() == _TRAFFIC["sources_sha256_16"]:
+            return _TRAFFIC["bytes_per_launch"]
+    except OSError:
+        pass
+    return None
 
 
 def _fp32_peak_tflops(sm_mhz: float, n_sm: int) -> float:
@@ -157,8 +185,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "TRDMD forward, 1 x 512x512, 7x7x48, 63 RBF, T=5, L=1",
-                   "H": H, "W": W, "ksize": KS, "nfilt": NK, "T": T, "looks": L},
+        "config": CONFIG,
         "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
@@ -246,14 +273,10 @@ def run_ours(args):
 
     ms = statistics.mean(step_ms)
     ms_e2e = statistics.mean(e2e_ms)
-    if world > 1:
-        t = torch.tensor([ms, ms_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
-
-    px = H * W * world
-    value = px / (ms / 1e3) / 1e6
-    e2e_value = px / (ms_e2e / 1e3) / 1e6
+    # every rank ran its own image: all ranks' pixels over the slowest rank's time
+    from paper_1702_07482_gb300.shard import global_rate
+    value, ms = global_rate(H * W, ms)
+    e2e_value, ms_e2e = global_rate(H * W, ms_e2e)
     out = None
     if rank == 0:
         peaks, src = _peaks()
@@ -262,12 +285,7 @@ def run_ours(args):
         peak_tf = _fp32_peak_tflops(sm_max, n_sm)
         launch_ms = ms / T   # T launches of the stage kernel per step, back to back
         achieved_tf = H * W * FLOPS_PER_PX_STAGE / (launch_ms / 1e3) / 1e12
-        traffic = None
-        try:
-            with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as fh:
-                traffic = json.load(fh).get("fused_stage_fwd_7x7x48_512")
-        except (OSError, ValueError):
-            traffic = None
+        traffic = _measured_traffic()
         cpu = None
         if not args.no_cpu_baseline:
             import oracle
@@ -285,11 +303,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "TRDMD forward, 1 x 512x512 per GPU, 7x7x48, 63 RBF, "
-                                   "T=5, L=1, fused FP32 stage kernel",
-                       "H": H, "W": W, "images_per_gpu": 1, "ksize": KS, "nfilt": NK,
-                       "nrbf": 63, "T": T, "looks": L,
-                       "l2": "flushed between steps (256 MiB write outside the events)"},
+            "config": CONFIG,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
                          "traffic": traffic,

@@ -1,0 +1,64 @@
+"""Multi-rank host logic on CPU (gloo, world size 2): image sharding and the
+whole-job rate reduction that bench.py uses with one process per GPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+from paper_1702_07482_gb300.shard import global_rate, shard_images
+
+
+def test_shard_partitions_and_balances():
+    sizes = [(256 + 37 * i % 700, 300 + 53 * i % 650) for i in range(64)]
+    for world in (1, 2, 3, 8):
+        parts = [shard_images(sizes, world, r) for r in range(world)]
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(64))
+        loads = [sum(sizes[i][0] * sizes[i][1] for i in p) for p in parts]
+        biggest = max(h * w for h, w in sizes)
+        assert max(loads) - min(loads) <= biggest
+    with pytest.raises(ValueError):
+        shard_images(sizes, 2, 2)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sizes = [(512, 512), (256, 1024), (300, 700), (1000, 260), (512, 300)]
+    mine = shard_images(sizes, world, rank)
+    px = sum(sizes[i][0] * sizes[i][1] for i in mine)
+    ms = 10.0 + 5.0 * rank            # rank 1 is the slower one
+    rate, ms_max = global_rate(px, ms)
+    q.put((rank, sorted(mine), rate, ms_max))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_rate_uses_all_pixels_and_slowest_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    out.sort()
+    total = 512 * 512 + 256 * 1024 + 300 * 700 + 1000 * 260 + 512 * 300
+    assert sorted(out[0][1] + out[1][1]) == [0, 1, 2, 3, 4]
+    for _, _, rate, ms_max in out:
+        assert ms_max == 15.0
+        assert rate == pytest.approx(total / 15e-3 / 1e6)
