@@ -115,6 +115,57 @@ TNRD_API tnrd_status tnrd_backward(const tnrd_params* params, int N, int H, int 
                           float* grad_lambda, tnrd_algo algo,
                           void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
+/* ---- Batched forward over images of different sizes ---------------------
+ * A plan describes a fixed batch: every image with its own size, input and
+ * output buffers and one of several parameter sets (e.g. one per number of
+ * looks L).  tnrd_batch_forward then runs all T stages of all images in ONE
+ * persistent kernel launch: CTAs take (stage, image, tile) items from a
+ * stage-major queue; a tile of stage t waits until the 3 x 3 neighbouring
+ * tiles of its image have finished stage t-1 (each wait bounded, see
+ * tnrd_plan_set_wait_limit).  The launch is recorded in a CUDA graph at plan
+ * creation and replayed by tnrd_batch_forward. */
+typedef struct {
+    const float* f;     /* device [H][pitch] noisy input (u_0)                 */
+    float* u;           /* device [H][pitch] receives u_T; must not overlap f   */
+    int H, W, pitch;    /* pitch in floats, multiple of 4, >= W                 */
+    int param_set;      /* index into the plan's parameter sets                */
+} tnrd_image;
+
+typedef struct tnrd_plan tnrd_plan;
+
+/* Creates a plan for `nimg` images (host array, copied) and `nsets` parameter
+ * sets (host array of tnrd_params with device arrays, copied; all sets must
+ * share T, ksize, nfilt, nrbf).  algo must be TNRD_ALGO_FUSED.  This is the one
+ * call that allocates device memory (work lists, per-tile stage counters, the
+ * inter-stage images, a status word).  With autotune != 0 it times each
+ * compiled tile height on the actual images (running the forward, which
+ * writes the outputs) on `stream` and keeps the fastest; otherwise a size
+ * heuristic picks it.  Synchronises `stream`. */
+TNRD_API tnrd_status tnrd_plan_create(tnrd_plan** plan, const tnrd_image* images, int nimg,
+                                      const tnrd_params* sets, int nsets, tnrd_algo algo,
+                                      int autotune, cudaStream_t stream);
+
+/* Runs the planned batch on `stream` (asynchronous; graph replay, or a direct
+ * launch when `stream` is being captured).  Device-side failures (a wait that
+ * hit its limit) are reported by tnrd_plan_status, not here. */
+TNRD_API tnrd_status tnrd_batch_forward(const tnrd_plan* plan, cudaStream_t stream);
+
+/* Synchronous: TNRD_OK, or TNRD_ERR_TIMEOUT if a tile of the last
+ * tnrd_batch_forward gave up waiting for its neighbours (its outputs are then
+ * incomplete). */
+TNRD_API tnrd_status tnrd_plan_status(const tnrd_plan* plan);
+
+/* Bound, in SM clock cycles, on each wait of a tile for its neighbours
+ * (default 2e9, about one second).  0 makes every wait give up at once, which
+ * tests the error path.  Synchronous. */
+TNRD_API tnrd_status tnrd_plan_set_wait_limit(tnrd_plan* plan, long long cycles);
+
+/* Tile height the plan uses (tiles are TH x (32 - 2 * (ksize / 2)) pixels). */
+TNRD_API int tnrd_plan_tile_height(const tnrd_plan* plan);
+
+/* Frees the plan's device memory and graph (synchronous). */
+TNRD_API void tnrd_plan_destroy(tnrd_plan* plan);
+
 /* Largest batch (N * H * pitch floats) that tnrd_forward_noalloc accepts:
  * 4 Mi floats = 16 MiB, e.g. one 2048 x 2048 image or four 1024 x 1024. */
 #define TNRD_NOALLOC_MAX_FLOATS (1u << 22)

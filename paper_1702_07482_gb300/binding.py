@@ -22,7 +22,9 @@ ALGO = {"fused": 0, "unfused": 1, "tf32": 2, "bf16": 3}
 OP_FORWARD, OP_BACKWARD = 0, 1
 
 # Every symbol include/tnrd.h declares (checked by the tests).
-EXPORTS = ["tnrd_workspace_size", "tnrd_forward", "tnrd_backward",
+EXPORTS = ["tnrd_workspace_size", "tnrd_forward", "tnrd_backward", "tnrd_plan_create",
+           "tnrd_batch_forward", "tnrd_plan_status", "tnrd_plan_set_wait_limit",
+           "tnrd_plan_tile_height", "tnrd_plan_destroy",
            "tnrd_forward_noalloc", "tnrd_last_error", "tnrd_version"]
 
 # Largest N * H * pitch (floats) tnrd_forward_noalloc accepts (TNRD_NOALLOC_MAX_FLOATS).
@@ -41,6 +43,11 @@ class tnrd_params(ctypes.Structure):
                 ("rbf_delta", ctypes.c_float), ("rbf_gamma", ctypes.c_float),
                 ("filters", ctypes.c_void_p), ("rbf_w", ctypes.c_void_p),
                 ("lambda_", ctypes.c_void_p)]
+
+
+class tnrd_image(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p), ("u", ctypes.c_void_p), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("pitch", ctypes.c_int), ("param_set", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -65,6 +72,19 @@ def load(path: str = LIB_PATH):
         L.tnrd_forward.argtypes = [pp, i, i, i, i, P, P, i, i, P, sz, P]
         L.tnrd_backward.restype = i
         L.tnrd_backward.argtypes = [pp, i, i, i, i, P, P, P, P, P, P, P, i, P, sz, P]
+        L.tnrd_plan_create.restype = i
+        L.tnrd_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(tnrd_image),
+                                       i, pp, i, i, i, P]
+        L.tnrd_batch_forward.restype = i
+        L.tnrd_batch_forward.argtypes = [P, P]
+        L.tnrd_plan_status.restype = i
+        L.tnrd_plan_status.argtypes = [P]
+        L.tnrd_plan_set_wait_limit.restype = i
+        L.tnrd_plan_set_wait_limit.argtypes = [P, ctypes.c_longlong]
+        L.tnrd_plan_tile_height.restype = i
+        L.tnrd_plan_tile_height.argtypes = [P]
+        L.tnrd_plan_destroy.restype = None
+        L.tnrd_plan_destroy.argtypes = [P]
         L.tnrd_forward_noalloc.restype = i
         L.tnrd_forward_noalloc.argtypes = [pp, i, i, i, i, P, P, P]
         L.tnrd_last_error.restype = ctypes.c_char_p
@@ -130,3 +150,40 @@ def tnrd_forward_noalloc(params: tnrd_params, N, H, W, pitch, f, u, stream) -> N
     scratch instead of a workspace; for callers that cannot allocate."""
     check(load().tnrd_forward_noalloc(ctypes.byref(params), N, H, W, pitch, _ptr(f), _ptr(u),
                                       ctypes.c_void_p(stream)))
+
+
+class Plan:
+    """Owns a tnrd_plan (tnrd_plan_create ... tnrd_plan_destroy)."""
+
+    def __init__(self, images, sets, algo=0, autotune=False, stream=0):
+        arr = (tnrd_image * len(images))(*images)
+        parr = (tnrd_params * len(sets))(*sets)
+        self._keep = (arr, parr)
+        self.handle = ctypes.c_void_p()
+        check(load().tnrd_plan_create(ctypes.byref(self.handle), arr, len(images), parr,
+                                      len(sets), int(algo), int(bool(autotune)),
+                                      ctypes.c_void_p(stream)))
+
+    def forward(self, stream) -> None:
+        check(load().tnrd_batch_forward(self.handle, ctypes.c_void_p(stream)))
+
+    def status(self) -> int:
+        return load().tnrd_plan_status(self.handle)
+
+    def set_wait_limit(self, cycles: int) -> None:
+        check(load().tnrd_plan_set_wait_limit(self.handle, int(cycles)))
+
+    @property
+    def tile_height(self) -> int:
+        return load().tnrd_plan_tile_height(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            load().tnrd_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -8,8 +8,10 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <algorithm>
 #include <cstdlib>
 #include <string>
+#include <vector>
 
 namespace {
 
@@ -375,6 +377,297 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
         if (e != cudaSuccess) return cuda_fail(e, "gradient reduce launch");
     }
     return TNRD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched forward: plans.
+// ---------------------------------------------------------------------------
+struct tnrd_plan {
+    int device = 0;
+    int ks = 0, nk = 0, nrbf = 0, T = 0;
+    int th = 0;
+    int nimg = 0, nsets = 0, ntiles = 0, ntiles_max = 0;
+    int grid = 0;
+    std::vector<tnrd_image> imgs;
+    std::vector<tnrd_params> sets;
+    char* block = nullptr;          // the plan's one device allocation
+    size_t off_imgs = 0, off_sets = 0, off_tiles = 0, off_counters = 0, off_limit = 0, off_tmp = 0;
+    std::vector<size_t> tmp_off;    // per image, offset of its inter-stage image
+    tnrd::BatchArgs args{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int batch_tiles(const tnrd_image& im, int ks, int th, int* tx, int* ty)
+{
+    const int tw = 32 - 2 * (ks / 2);
+    *tx = (im.W + tw - 1) / tw;
+    *ty = (im.H + th - 1) / th;
+    return *tx * *ty;
+}
+
+// Uploads the image/tile tables of tile height th and points plan->args at them.
+tnrd_status plan_build(tnrd_plan* P, int th, cudaStream_t s)
+{
+    std::vector<tnrd::BatchImg> bi(P->nimg);
+    std::vector<int2> tiles;
+    int base = 0;
+    for (int i = 0; i < P->nimg; ++i) {
+        const tnrd_image& im = P->imgs[i];
+        int tx, ty;
+        const int n = batch_tiles(im, P->ks, th, &tx, &ty);
+        bi[i].f = im.f;
+        bi[i].u = im.u;
+        bi[i].tmp = (float*)(P->block + P->tmp_off[i]);
+        bi[i].H = im.H;
+        bi[i].W = im.W;
+        bi[i].pitch = im.pitch;
+        bi[i].tiles_x = tx;
+        bi[i].tiles_y = ty;
+        bi[i].tile_base = base;
+        bi[i].set = im.param_set;
+        for (int k = 0; k < n; ++k) tiles.push_back(make_int2(i, k));
+        base += n;
+    }
+    P->th = th;
+    P->ntiles = base;
+    cudaError_t e = cudaMemcpyAsync(P->block + P->off_imgs, bi.data(), sizeof(tnrd::BatchImg) * bi.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->block + P->off_tiles, tiles.data(), sizeof(int2) * tiles.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "plan upload");
+    tnrd::BatchArgs& A = P->args;
+    A.imgs = (const tnrd::BatchImg*)(P->block + P->off_imgs);
+    A.sets = (const tnrd::BatchSet*)(P->block + P->off_sets);
+    A.tile_img = (const int2*)(P->block + P->off_tiles);
+    A.work_counter = (int*)(P->block + P->off_counters);
+    A.status = A.work_counter + 1;
+    A.tile_done = A.work_counter + 2;
+    A.wait_limit = (const long long*)(P->block + P->off_limit);
+    A.ntiles = P->ntiles;
+    A.T = P->T;
+    A.nfilt = P->nk;
+    A.ksize = P->ks;
+    A.nrbf = P->nrbf;
+    const int occ = tnrd::batch_fwd_occupancy(P->ks, P->nk, th, P->nrbf);
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
+    P->grid = std::max(1, nsm * std::max(occ, 1));
+    return TNRD_OK;
+}
+
+cudaError_t plan_enqueue(const tnrd_plan* P, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(P->block + P->off_counters, 0, sizeof(int) * (2 + (size_t)P->ntiles), s);
+    if (e != cudaSuccess) return e;
+    return tnrd::launch_batch_fwd(P->ks, P->nk, P->th, P->args, P->grid, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg,
+                             const tnrd_params* sets, int nsets, tnrd_algo algo, int autotune,
+                             cudaStream_t stream)
+{
+    if (!out) return fail(TNRD_ERR_INVALID_ARG, "plan pointer is null");
+    *out = nullptr;
+    if (!images || nimg < 1 || !sets || nsets < 1)
+        return fail(TNRD_ERR_INVALID_ARG, "need at least one image and one parameter set");
+    if (algo != TNRD_ALGO_FUSED) return fail(TNRD_ERR_UNSUPPORTED, "batched forward supports TNRD_ALGO_FUSED");
+    for (int s = 0; s < nsets; ++s) {
+        tnrd_status st = check_params(&sets[s]);
+        if (st != TNRD_OK) return st;
+        if (sets[s].T != sets[0].T || sets[s].ksize != sets[0].ksize || sets[s].nfilt != sets[0].nfilt ||
+            sets[s].nrbf != sets[0].nrbf)
+            return fail(TNRD_ERR_INVALID_ARG, "parameter sets differ in T, ksize, nfilt or nrbf");
+    }
+    const int ks = sets[0].ksize;
+    for (int i = 0; i < nimg; ++i) {
+        const tnrd_image& im = images[i];
+        tnrd_status st = check_images(1, im.H, im.W, im.pitch, ks);
+        if (st != TNRD_OK) return st;
+        if (!im.f || !im.u || !aligned16(im.f) || !aligned16(im.u))
+            return fail(TNRD_ERR_INVALID_ARG, "image %d: null or misaligned pointer", i);
+        if (im.param_set < 0 || im.param_set >= nsets)
+            return fail(TNRD_ERR_INVALID_ARG, "image %d: param_set %d out of range", i, im.param_set);
+        const size_t n = (size_t)im.H * im.pitch;
+        if ((const float*)im.u < im.f + n && im.f < (const float*)im.u + n)
+            return fail(TNRD_ERR_INVALID_ARG, "image %d: u overlaps f", i);
+    }
+    tnrd_plan* P = new tnrd_plan();
+    cudaGetDevice(&P->device);
+    P->ks = ks;
+    P->nk = sets[0].nfilt;
+    P->nrbf = sets[0].nrbf;
+    P->T = sets[0].T;
+    P->nimg = nimg;
+    P->nsets = nsets;
+    P->imgs.assign(images, images + nimg);
+    P->sets.assign(sets, sets + nsets);
+    const int* ths = tnrd::fused_th_list(ks);
+    int tmax = 0;
+    for (const int* p = ths; *p; ++p) {
+        int n = 0;
+        for (int i = 0; i < nimg; ++i) {
+            int tx, ty;
+            n += batch_tiles(images[i], ks, *p, &tx, &ty);
+        }
+        tmax = std::max(tmax, n);
+    }
+    P->ntiles_max = tmax;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
+    P->off_imgs = take(sizeof(tnrd::BatchImg) * nimg);
+    P->off_sets = take(sizeof(tnrd::BatchSet) * nsets);
+    P->off_tiles = take(sizeof(int2) * tmax);
+    P->off_counters = take(sizeof(int) * (2 + (size_t)tmax));
+    P->off_limit = take(sizeof(long long));
+    P->tmp_off.resize(nimg);
+    for (int i = 0; i < nimg; ++i) P->tmp_off[i] = take(sizeof(float) * (size_t)images[i].H * images[i].pitch);
+    cudaError_t e = cudaMalloc((void**)&P->block, off);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_fail(e, "plan allocation");
+    }
+    std::vector<tnrd::BatchSet> bs(nsets);
+    for (int s = 0; s < nsets; ++s) {
+        bs[s].k = sets[s].filters;
+        bs[s].w = sets[s].rbf_w;
+        bs[s].lam = sets[s].lambda;
+        bs[s].rc = make_rbf(&sets[s]);
+    }
+    const long long limit = 2000000000LL;
+    e = cudaMemcpyAsync(P->block + P->off_sets, bs.data(), sizeof(tnrd::BatchSet) * nsets,
+                        cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->block + P->off_limit, &limit, sizeof limit, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        tnrd_plan_destroy(P);
+        return cuda_fail(e, "plan upload");
+    }
+
+    // tile height: timed on the data (autotune) or by total work incl. halos
+    int best = ths[0];
+    if (autotune) {
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (const int* p = ths; *p; ++p) {
+            tnrd_status st = plan_build(P, *p, stream);
+            if (st != TNRD_OK) { tnrd_plan_destroy(P); return st; }
+            float ms = 0.0f;
+            e = plan_enqueue(P, stream);   // warm-up
+            for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+                cudaEventRecord(e0, stream);
+                e = plan_enqueue(P, stream);
+                cudaEventRecord(e1, stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float m = 0.0f;
+                cudaEventElapsedTime(&m, e0, e1);
+                ms += m;
+            }
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                tnrd_plan_destroy(P);
+                return cuda_fail(e, "autotune run");
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = *p;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    } else {
+        const int R = ks / 2;
+        double best_cost = 1e300;
+        for (const int* p = ths; *p; ++p) {
+            double cost = 0.0;
+            for (int i = 0; i < nimg; ++i) {
+                int tx, ty;
+                cost += (double)batch_tiles(images[i], ks, *p, &tx, &ty) * (*p + 4 * R);
+            }
+            if (cost < best_cost * 0.999) {
+                best_cost = cost;
+                best = *p;
+            }
+        }
+    }
+    tnrd_status st = plan_build(P, best, stream);
+    if (st != TNRD_OK) { tnrd_plan_destroy(P); return st; }
+
+    // record the launch in a graph
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = plan_enqueue(P, cs);
+            e = cudaStreamEndCapture(cs, &P->graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, P->graph, 0);
+        cudaStreamDestroy(cs);
+    }
+    if (e != cudaSuccess) {
+        tnrd_plan_destroy(P);
+        return cuda_fail(e, "plan graph capture");
+    }
+    *out = P;
+    return TNRD_OK;
+}
+
+tnrd_status tnrd_batch_forward(const tnrd_plan* P, cudaStream_t stream)
+{
+    if (!P) return fail(TNRD_ERR_INVALID_ARG, "plan is null");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "stream query");
+    if (cap == cudaStreamCaptureStatusActive) e = plan_enqueue(P, stream);
+    else e = cudaGraphLaunch(P->exec, stream);
+    return e == cudaSuccess ? TNRD_OK : cuda_fail(e, "batch launch");
+}
+
+tnrd_status tnrd_plan_status(const tnrd_plan* P)
+{
+    if (!P) return fail(TNRD_ERR_INVALID_ARG, "plan is null");
+    int st = 0;
+    cudaError_t e = cudaMemcpy(&st, P->block + P->off_counters + sizeof(int), sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st == TNRD_ERR_TIMEOUT) return fail(TNRD_ERR_TIMEOUT, "a tile gave up waiting for its neighbours");
+    return st == 0 ? TNRD_OK : fail((tnrd_status)st, "device status %d", st);
+}
+
+tnrd_status tnrd_plan_set_wait_limit(tnrd_plan* P, long long cycles)
+{
+    if (!P || cycles < 0) return fail(TNRD_ERR_INVALID_ARG, "bad plan or negative limit");
+    cudaError_t e = cudaMemcpy(P->block + P->off_limit, &cycles, sizeof cycles, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? TNRD_OK : cuda_fail(e, "wait limit");
+}
+
+int tnrd_plan_tile_height(const tnrd_plan* P) { return P ? P->th : 0; }
+
+void tnrd_plan_destroy(tnrd_plan* P)
+{
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->block) {
+        cudaDeviceSynchronize();
+        cudaFree(P->block);
+    }
+    delete P;
 }
 
 }  // extern "C"

@@ -19,6 +19,20 @@ struct StageArgs {
     RbfConst rc;
 };
 
+// One tile of one stage for stage_tile(): pointers already offset to the image.
+struct TileJob {
+    const float* u_in;
+    float* u_out;
+    const float* f;
+    int H, W, pitch;
+    int tiles_x, tiles_y, ty, tx;
+    const float* k;
+    const float* w;
+    const float* lam;
+    int nrbf;
+    const RbfConst* rc;
+};
+
 template <int KS, int NK, int TH>
 struct FusedCfg {
     static constexpr int R = KS / 2;
@@ -150,5 +164,37 @@ struct BwdCfg {
 // nfilt / NWARP_DK filters.
 constexpr int DK_TH = 32;
 constexpr int DK_TW = 32;
+
+// ---------------------------------------------------------------------------
+// Persistent batched forward (tnrd_batch_forward).
+// ---------------------------------------------------------------------------
+struct BatchImg {
+    const float* f;
+    float* u;          // final output u_T
+    float* tmp;        // inter-stage image (ping-pong partner of u)
+    int H, W, pitch;
+    int tiles_x, tiles_y, tile_base;   // tiles of this image: [tile_base, +tiles_x*tiles_y)
+    int set;
+};
+
+struct BatchSet {
+    const float* k;    // [T][nfilt][ks][ks]
+    const float* w;    // [T][nfilt][nrbf]
+    const float* lam;  // [T]
+    RbfConst rc;
+};
+
+struct BatchArgs {
+    const BatchImg* imgs;
+    const BatchSet* sets;
+    const int2* tile_img;        // global tile -> (image, tile within the image)
+    int* work_counter;
+    int* tile_done;              // per global tile: stages completed
+    int* status;                 // 0, or TNRD_ERR_TIMEOUT
+    const long long* wait_limit; // cycles
+    int ntiles;                  // tiles per stage over all images
+    int T;
+    int nfilt, ksize, nrbf;
+};
 
 }  // namespace tnrd

@@ -110,32 +110,33 @@ __device__ __forceinline__ void walk_group(const float* __restrict__ urow, float
     }
 }
 
+// One stage on one tile (the whole CTA).  Loads of u_{t-1} go through L2
+// (ld.global.cg) so that a persistent kernel can read tiles that other CTAs
+// wrote earlier in the same launch; ends with a CTA barrier after the stores.
 template <int KS, int NK, int TH>
-__global__ void __launch_bounds__(FusedCfg<KS, NK, TH>::NTHREADS, FusedCfg<KS, NK, TH>::MINB)
-fused_stage_fwd(const StageArgs a)
+__device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
 {
     using C = FusedCfg<KS, NK, TH>;
     constexpr int R = C::R;
     constexpr int TW = C::TW;
-    extern __shared__ __align__(16) float smem[];
     float* sU = smem;                          // rows [y0-3R, ...) x cols [x0-2R, x0+TW+2R)
     float* sH = sU + C::U_FL;                  // per warp: rows [y0-R, y0+TH+R) x 32 lanes
     float* sKW = sH + C::NWARP * C::H_FL;
     float* sTab = smem + C::TAB_OFF;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = blockIdx.y;
-    const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x - ty * a.tiles_x;
-    const int H = a.H, W = a.W;
+    const int ty = j.ty, tx = j.tx;
+    const int H = j.H, W = j.W;
     const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
-    const bool ext = (ty == 0) || (ty == a.tiles_y - 1);
-    const bool border = ext || (tx == 0) || (tx == a.tiles_x - 1);
-    const float* uin = a.u_in + (size_t)n * a.img_stride;
+    const bool ext = (ty == 0) || (ty == j.tiles_y - 1);
+    const bool border = ext || (tx == 0) || (tx == j.tiles_x - 1);
+    const float* uin = j.u_in;
+    const RbfConst& rc = *j.rc;
 
     for (int idx = threadIdx.x; idx < C::UH * C::UW; idx += C::NTHREADS) {
-        const int i = idx / C::UW, j = idx - i * C::UW;
-        const int yy = sym_idx(y0 - 3 * R + i, H), xx = sym_idx(x0 - 2 * R + j, W);
-        sU[i * C::UP + j] = uin[(size_t)yy * a.pitch + xx];
+        const int i = idx / C::UW, jj = idx - i * C::UW;
+        const int yy = sym_idx(y0 - 3 * R + i, H), xx = sym_idx(x0 - 2 * R + jj, W);
+        sU[i * C::UP + jj] = __ldcg(uin + (size_t)yy * j.pitch + xx);
     }
     float* myH = sH + warp * C::H_FL;
     float* myK = sKW + warp * C::KW_FL;
@@ -161,10 +162,10 @@ fused_stage_fwd(const StageArgs a)
 #pragma unroll 1
     for (int fl = 0; fl < C::FPW; ++fl) {
         const int fi = warp * C::FPW + fl;
-        for (int e = lane; e < KS * KS; e += 32) myK[e] = __ldg(a.k + fi * KS * KS + e);
-        for (int e = lane; e < a.nrbf; e += 32) myW[RBF_WPAD + e] = __ldg(a.w + fi * a.nrbf + e);
+        for (int e = lane; e < KS * KS; e += 32) myK[e] = __ldg(j.k + fi * KS * KS + e);
+        for (int e = lane; e < j.nrbf; e += 32) myW[RBF_WPAD + e] = __ldg(j.w + fi * j.nrbf + e);
         __syncwarp();
-        rbf_build_table(myT, myW, a.nrbf, a.rc, lane);
+        rbf_build_table(myT, myW, j.nrbf, rc, lane);
         float kr[KS][KS];
 #pragma unroll
         for (int p = 0; p < KS; ++p)
@@ -178,23 +179,21 @@ fused_stage_fwd(const StageArgs a)
 #pragma unroll 1
             for (int m0 = 0; m0 < nsteps; m0 += KS)
                 walk_group<KS, C::UP, true>(urow, hrow, kr, za, ha, m0, zrow0, H, col_in, 2 * R,
-                                            4 * R, nsteps, lane, myT, a.rc);
+                                            4 * R, nsteps, lane, myT, rc);
         } else {
 #pragma unroll 1
             for (int m0 = 0; m0 < nsteps; m0 += KS)
                 walk_group<KS, C::UP, false>(urow, hrow, kr, za, ha, m0, zrow0, H, col_in, 2 * R,
-                                             4 * R, nsteps, lane, myT, a.rc);
+                                             4 * R, nsteps, lane, myT, rc);
         }
         __syncwarp();
     }
     __syncthreads();
 
     // Epilogue: g = fold(sum over warps of h), u_t = prox(u_{t-1} - g).
-    const float lam = __ldg(a.lam);
-    const int wy0 = tile_split(ty, TH, H, a.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, a.tiles_y, R);
-    const int wx0 = tile_split(tx, TW, W, a.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, a.tiles_x, R);
-    const float* fimg = a.f + (size_t)n * a.img_stride;
-    float* uout = a.u_out + (size_t)n * a.img_stride;
+    const float lam = __ldg(j.lam);
+    const int wy0 = tile_split(ty, TH, H, j.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, j.tiles_y, R);
+    const int wx0 = tile_split(tx, TW, W, j.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, j.tiles_x, R);
     for (int idx = threadIdx.x; idx < TH * TW; idx += C::NTHREADS) {
         const int qy = y0 + idx / TW, qx = x0 + idx % TW;
         if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
@@ -219,9 +218,35 @@ fused_stage_fwd(const StageArgs a)
             }
         }
         const float up = sU[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R)];
-        const float fv = __ldg(fimg + (size_t)qy * a.pitch + qx);
-        uout[(size_t)qy * a.pitch + qx] = prox_idiv(up - g, fv, lam);
+        const float fv = __ldg(j.f + (size_t)qy * j.pitch + qx);
+        j.u_out[(size_t)qy * j.pitch + qx] = prox_idiv(up - g, fv, lam);
     }
+    __syncthreads();
+}
+
+template <int KS, int NK, int TH>
+__global__ void __launch_bounds__(FusedCfg<KS, NK, TH>::NTHREADS, FusedCfg<KS, NK, TH>::MINB)
+fused_stage_fwd(const __grid_constant__ StageArgs a)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int n = blockIdx.y;
+    TileJob j;
+    j.u_in = a.u_in + (size_t)n * a.img_stride;
+    j.u_out = a.u_out + (size_t)n * a.img_stride;
+    j.f = a.f + (size_t)n * a.img_stride;
+    j.H = a.H;
+    j.W = a.W;
+    j.pitch = a.pitch;
+    j.tiles_x = a.tiles_x;
+    j.tiles_y = a.tiles_y;
+    j.ty = blockIdx.x / a.tiles_x;
+    j.tx = blockIdx.x - j.ty * a.tiles_x;
+    j.k = a.k;
+    j.w = a.w;
+    j.lam = a.lam;
+    j.nrbf = a.nrbf;
+    j.rc = &a.rc;
+    stage_tile<KS, NK, TH>(j, smem);
 }
 
 }  // namespace tnrd

@@ -29,6 +29,10 @@ int fused_fwd_occupancy(int ks, int nk, int th, int nrbf);
 cudaError_t launch_fused_fwd(int ks, int nk, int th, const StageArgs& a, int N, cudaStream_t s);
 cudaError_t launch_unfused_fwd(int ks, const UnfArgs& a, int N, cudaStream_t s);
 
+// Persistent batched forward.
+cudaError_t launch_batch_fwd(int ks, int nk, int th, const BatchArgs& a, int grid, cudaStream_t s);
+int batch_fwd_occupancy(int ks, int nk, int th, int nrbf);
+
 // Backward: tile height of bwd_bank (tiles are TH x (32 - 2R)), one stage's
 // prep + bank + filter-gradient launches, and the fixed-order partial reduce.
 int bwd_tile_h(int ks);

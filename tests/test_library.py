@@ -91,3 +91,21 @@ def test_workspace_sizes(lib):
     assert unf == 2 * one * 48 + 2 * one
     assert lib.tnrd_workspace_size(0, ctypes.byref(_params(T=1)), 1, 64, 64, 64, 0, 0) == 0
     assert lib.tnrd_workspace_size(0, ctypes.byref(_params(ks=4)), 1, 64, 64, 64, 0, 0) == 0
+
+
+def test_plan_create_rejects_bad_batches_before_touching_the_device(lib):
+    p = _params()
+    pp = (B.tnrd_params * 1)(p)
+    h = ctypes.c_void_p()
+    img = B.tnrd_image(0x10000, 0x200000, 64, 64, 64, 0)
+    arr = (B.tnrd_image * 1)(img)
+    assert lib.tnrd_plan_create(ctypes.byref(h), arr, 0, pp, 1, 0, 0, None) == 1
+    bad = (B.tnrd_image * 1)(B.tnrd_image(0x10000, 0x200000, 64, 64, 64, 3))
+    assert lib.tnrd_plan_create(ctypes.byref(h), bad, 1, pp, 1, 0, 0, None) == 1
+    small = (B.tnrd_image * 1)(B.tnrd_image(0x10000, 0x200000, 5, 64, 64, 0))
+    assert lib.tnrd_plan_create(ctypes.byref(h), small, 1, pp, 1, 0, 0, None) == 1
+    assert lib.tnrd_plan_create(ctypes.byref(h), arr, 1, pp, 1, 1, 0, None) == 2
+    p2 = _params(T=3)
+    two = (B.tnrd_params * 2)(p, p2)
+    assert lib.tnrd_plan_create(ctypes.byref(h), arr, 1, two, 2, 0, 0, None) == 1
+    assert not h.value
