@@ -1,13 +1,19 @@
 #!/usr/bin/env python3
-"""Throughput of the TRDMD forward cascade on GB300.
+"""Throughput of the TRDMD despeckling cascade on GB300.
 
-Workload (per GPU): one 512x512 speckled image (L = 1), T = 5 stages of 48
-zero-mean 7x7 filters with 63-RBF influence functions, plain FP32, fused stage
-kernel -- one "step" is the whole T-stage forward of that image.  With N GPUs
-(torchrun), every rank runs its own image (independent problems, no
+Default workload (per GPU): one 512x512 speckled image (L = 1), T = 5 stages of
+48 zero-mean 7x7 filters with 63-RBF influence functions, plain FP32, fused
+stage kernel -- one "step" is the whole T-stage forward of that image.  With N
+GPUs (torchrun), every rank runs its own image (independent problems, no
 collective on the data path): weak scaling.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload fwd512|fwd512_unfused|small128|batched|train]
+
+The other workloads (one GPU) measure the rest of the table with the same
+contract: fwd512_unfused (three kernels per stage), small128 (1 x 128^2,
+5x5x24), batched (64 images of 256-1024 px per side, four parameter sets, one
+persistent launch per step), train (32 x 180^2 crops, forward + backward).
 
 Prints ONE JSON line (rank 0).  `value` is Mpixel/s over all ranks with the
 inputs resident in HBM (L2 flushed between steps by a 256 MiB write, outside
@@ -139,42 +145,298 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _inputs():
+def _p32(p):
     import numpy as np
-    import synth
-    p = synth.params(T, KS, NK, seed=synth.seed_for(CFG_ID, 0, "params"))
-    p = p.astype(np.float32).astype(np.float64)
-    _, f = synth.single_image(H, W, L, CFG_ID, index=0)
-    return p, f.astype(np.float32).astype(np.float64)
+    return p.astype(np.float32).astype(np.float64)
 
 
-def _cpu_oracle_rate(p, f, rows: int):
-    """Mpixel/s of the FP64 oracle on a band of `rows` image rows (T stages)."""
-    import oracle
-    band = f[:rows].copy()
-    t0 = time.perf_counter()
-    oracle.forward(band, p)
-    dt = time.perf_counter() - t0
-    return rows * W / dt / 1e6, dt
+# Algorithmic flops per pixel-stage of the backward at 7x7x48 (fwd: FLOPS_PER_PX_STAGE):
+# convolutions z = K u, b = K d, the adjoint of c and the two filter-gradient
+# correlations (5 x 2 N_k k^2), phi, phi' and the RBF-weight gradient
+# (3 x 2 N_k N_rbf), ~20 for y, x and d.
+BWD_FLOPS_PER_PX_STAGE = 5 * 2 * NK * KS * KS + 3 * 2 * NK * 63 + 20
+
+
+class Workload:
+    """One benchmark workload: device-resident step, end-to-end step, and the
+    numbers the JSON line needs.  Subclasses set the attributes in setup()."""
+    name = ""
+    config = {}
+    px = 0                 # pixels processed per step (per rank)
+    launches = 0           # our kernel launches per step
+    flops = 0.0            # algorithmic flops per step
+    kernel = ""
+    h2d = 0
+    d2h = 0
+    traffic = None
+
+    def __init__(self, dev):
+        self.dev = dev
+
+    def step(self):
+        raise NotImplementedError
+
+    def e2e(self):
+        raise NotImplementedError
+
+    def cpu_baseline(self):
+        return None
+
+
+def _rows_rate(fn, rows0, target_s, max_rows):
+    """Runs fn(rows) growing the row count until one call takes ~target_s."""
+    rows = rows0
+    dt = 0.0
+    for _ in range(4):
+        t0 = time.perf_counter()
+        fn(rows)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * target_s or rows >= max_rows:
+            break
+        rows = int(min(max_rows, max(rows + 1, rows * target_s / max(dt, 1e-3))))
+    return rows, dt
+
+
+class Fwd(Workload):
+    def __init__(self, dev, H=512, W=512, ks=KS, nk=NK, T_=T, algo="fused", cfg=CFG_ID):
+        super().__init__(dev)
+        import numpy as np
+        import torch
+        import synth
+        from paper_1702_07482_gb300 import binding, ops
+        self.Hh, self.Ww, self.T = H, W, T_
+        self.p = _p32(synth.params(T_, ks, nk, seed=synth.seed_for(cfg, 0, "params")))
+        _, f = synth.single_image(H, W, L, cfg, index=0)
+        self.f = f.astype(np.float32).astype(np.float64)
+        m = ops.Model.create(self.p.filters, self.p.rbf_w, self.p.lam, device=dev)
+        self.prm = m.params()
+        self.model = m
+        self.P = ops.pitch_for(W)
+        self.f_dev = ops.to_pitched(torch.tensor(self.f, dtype=torch.float32, device=dev))
+        self.u_dev = torch.empty_like(self.f_dev)
+        self.algo = binding.ALGO[algo]
+        self.ws_bytes = binding.tnrd_workspace_size(binding.OP_FORWARD, self.prm, 1, H, W, self.P,
+                                                    0, self.algo)
+        self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=dev)
+        self.sp = torch.cuda.current_stream(dev).cuda_stream
+        self.f_host = self.f_dev.cpu().pin_memory()
+        self.u_host = torch.empty_like(self.f_host).pin_memory()
+        self.px = H * W
+        self.launches = T_ * (1 if algo == "fused" else 3)
+        fl = 2 * nk * ks * ks * 2 + 2 * nk * 63 + 12
+        self.flops = float(H * W) * T_ * fl
+        self.flops_per_px_stage = fl
+        self.kernel = f"fused_stage_fwd<{ks},{nk},TH>" if algo == "fused" else \
+            f"unf_bank_phi + unf_adjoint + unf_prox <{ks}>"
+        self.h2d = self.d2h = int(self.f_host.numel() * 4)
+        self.traffic = _measured_traffic() if (algo == "fused" and H == 512 and ks == 7) else None
+        self.config = {"workload": f"TRDMD forward, 1 x {H}x{W} per GPU, {ks}x{ks}x{nk}, 63 RBF, "
+                                   f"T={T_}, L={L}, {algo} FP32 stage kernel" +
+                                   ("" if algo == "fused" else "s"),
+                       "H": H, "W": W, "images_per_gpu": 1, "ksize": ks, "nfilt": nk,
+                       "nrbf": 63, "T": T_, "looks": L,
+                       "l2": "flushed between steps (256 MiB write outside the events)"}
+
+    def step(self):
+        from paper_1702_07482_gb300 import binding
+        binding.tnrd_forward(self.prm, 1, self.Hh, self.Ww, self.P, self.f_dev, self.u_dev, 0,
+                             self.algo, self.ws, self.ws_bytes, self.sp)
+
+    def e2e(self):
+        self.f_dev.copy_(self.f_host, non_blocking=True)
+        self.step()
+        self.u_host.copy_(self.u_dev, non_blocking=True)
+
+    def cpu_baseline(self):
+        import oracle
+        oracle.build()
+        band = lambda r: oracle.forward(self.f[:r].copy(), self.p)
+        rows, dt = _rows_rate(band, 8, 12.0, self.Hh)
+        return {"value": rows * self.Ww / dt / 1e6, "unit": "Mpixel/s",
+                "cores": oracle.get_threads(), "kind": "oracle",
+                "sample": f"rows 0..{rows - 1} of the {self.Hh}x{self.Ww} image, all "
+                          f"T={self.T} stages ({dt:.1f} s)"}
+
+
+class Batched(Workload):
+    def __init__(self, dev, n=64, lo=256, hi=1024, T_=T, cfg=3):
+        super().__init__(dev)
+        import numpy as np
+        import torch
+        import synth
+        from paper_1702_07482_gb300 import binding as B
+        from paper_1702_07482_gb300 import ops
+        looks = (1, 2, 4, 8)
+        self.T = T_
+        self.sizes = synth.uneven_batch(n, lo, hi, cfg, looks)
+        self.params = [_p32(synth.params(T_, KS, NK, seed=synth.seed_for(cfg, s, "params")))
+                       for s in range(len(looks))]
+        self.models = [ops.Model.create(p.filters, p.rbf_w, p.lam, device=dev) for p in self.params]
+        offs, tot = [], 0
+        for (Hh, Ww, Lk) in self.sizes:
+            offs.append(tot)
+            tot += Hh * ops.pitch_for(Ww)
+        self.f_host = torch.zeros(tot, dtype=torch.float32).pin_memory()
+        self.fs = []
+        for i, (Hh, Ww, Lk) in enumerate(self.sizes):
+            _, f = synth.single_image(Hh, Ww, Lk, cfg, index=i)
+            f = f.astype(np.float32)
+            P = ops.pitch_for(Ww)
+            view = self.f_host[offs[i]:offs[i] + Hh * P].view(Hh, P)
+            view[:, :Ww] = torch.from_numpy(f)
+            if i == 0:
+                self.fs.append(f.astype(np.float64))
+        self.f_dev = self.f_host.to(dev)
+        self.u_dev = torch.zeros_like(self.f_dev)
+        self.u_host = torch.empty_like(self.f_host).pin_memory()
+        imgs = []
+        for i, (Hh, Ww, Lk) in enumerate(self.sizes):
+            P = ops.pitch_for(Ww)
+            imgs.append(B.tnrd_image(self.f_dev[offs[i]:].data_ptr(), self.u_dev[offs[i]:].data_ptr(),
+                                     Hh, Ww, P, looks.index(Lk)))
+        self.sp = torch.cuda.current_stream(dev).cuda_stream
+        self.plan = B.Plan(imgs, [m.params() for m in self.models], autotune=True, stream=self.sp)
+        self.px = sum(Hh * Ww for (Hh, Ww, _) in self.sizes)
+        self.launches = 1
+        self.flops = float(self.px) * T_ * FLOPS_PER_PX_STAGE
+        self.flops_per_px_stage = FLOPS_PER_PX_STAGE
+        self.kernel = f"batch_persistent_fwd<7,48,{self.plan.tile_height}>"
+        self.h2d = self.d2h = int(self.f_host.numel() * 4)
+        self.config = {"workload": f"TRDMD batched forward, {n} images with sides U[{lo},{hi}] "
+                                   f"({self.px / 1e6:.1f} Mpx), L in {{1,2,4,8}} with one "
+                                   f"7x7x48 63-RBF parameter set each, T={T_}, one persistent "
+                                   f"launch per step (CUDA graph), autotuned tile height "
+                                   f"{self.plan.tile_height}",
+                       "images": n, "pixels": self.px, "ksize": KS, "nfilt": NK, "nrbf": 63,
+                       "T": T_, "tile_height": self.plan.tile_height,
+                       "l2": f"inputs ({self.h2d / 2 ** 20:.0f} MiB) larger than L2"}
+
+    def step(self):
+        self.plan.forward(self.sp)
+
+    def e2e(self):
+        self.f_dev.copy_(self.f_host, non_blocking=True)
+        self.step()
+        self.u_host.copy_(self.u_dev, non_blocking=True)
+
+    def cpu_baseline(self):
+        import oracle
+        oracle.build()
+        f0 = self.fs[0]
+        p0 = self.params[0]
+        band = lambda r: oracle.forward(f0[:r].copy(), p0)
+        rows, dt = _rows_rate(band, 8, 12.0, f0.shape[0])
+        return {"value": rows * f0.shape[1] / dt / 1e6, "unit": "Mpixel/s",
+                "cores": oracle.get_threads(), "kind": "oracle",
+                "sample": f"rows 0..{rows - 1} of image 0 ({f0.shape[0]}x{f0.shape[1]}), all "
+                          f"T={self.T} stages ({dt:.1f} s)"}
+
+
+class Train(Workload):
+    def __init__(self, dev, n=32, S=180, T_=T, cfg=4):
+        super().__init__(dev)
+        import numpy as np
+        import torch
+        import synth
+        from paper_1702_07482_gb300 import binding as B
+        from paper_1702_07482_gb300 import ops
+        self.T, self.n, self.S = T_, n, S
+        self.p = _p32(synth.params(T_, KS, NK, seed=synth.seed_for(cfg, 0, "params")))
+        pairs = [synth.single_image(S, S, 1, cfg, index=i) for i in range(n)]
+        self.clean = np.stack([c for c, _ in pairs]).astype(np.float32)
+        self.f = np.stack([f for _, f in pairs]).astype(np.float32)
+        self.m = ops.Model.create(self.p.filters, self.p.rbf_w, self.p.lam, device=dev)
+        self.P = ops.pitch_for(S)
+        self.f_dev = ops.to_pitched(torch.tensor(self.f, device=dev))
+        self.c_dev = ops.to_pitched(torch.tensor(self.clean, device=dev))
+        self.f_host = self.f_dev.cpu().pin_memory()
+        self.c_host = self.c_dev.cpu().pin_memory()
+        self.u_all = torch.empty((T_ + 1,) + tuple(self.f_dev.shape), device=dev)
+        self.ws_bytes = ops.workspace_size(self.m, n, S, S, self.P, 1, op=B.OP_BACKWARD)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.g_host = torch.empty(self.m.filters.numel() + self.m.rbf_w.numel() + T_,
+                                  dtype=torch.float32).pin_memory()
+        self.grads = None
+        self.px = n * S * S
+        self.launches = T_ + T_ * 6
+        self.flops = float(self.px) * T_ * (FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE)
+        self.flops_per_px_stage = FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE
+        self.kernel = "fused_stage_fwd + bwd_prep/bwd_bank/bwd_dk/bwd_reduce <7,48>"
+        self.h2d = int((self.f_host.numel() + self.c_host.numel()) * 4)
+        self.d2h = int(self.g_host.numel() * 4)
+        self.config = {"workload": f"TRDMD training step (forward + backward), {n} crops of "
+                                   f"{S}x{S}, L=1, 7x7x48, 63 RBF, T={T_}, loss 1/2|u_T - clean|^2, "
+                                   "gradients of all filters, RBF weights and lambda",
+                       "batch": n, "crop": S, "ksize": KS, "nfilt": NK, "nrbf": 63, "T": T_,
+                       "l2": f"working set (checkpoints + response planes, "
+                             f"{self.ws_bytes / 2 ** 20:.0f} MiB workspace) larger than L2"}
+
+    def step(self):
+        from paper_1702_07482_gb300 import ops
+        u = ops.forward(self.m, self.f_dev, keep_stages=True, out=self.u_all, W=self.S)
+        e = u[-1] - self.c_dev
+        self.grads = ops.backward(self.m, self.f_dev, u, e, want_grad_u0=False, W=self.S,
+                                  workspace=self.ws)
+
+    def e2e(self):
+        import torch
+        self.f_dev.copy_(self.f_host, non_blocking=True)
+        self.c_dev.copy_(self.c_host, non_blocking=True)
+        self.step()
+        _, gk, gw, gl = self.grads
+        flat = torch.cat([gk.reshape(-1), gw.reshape(-1), gl.reshape(-1)])
+        self.g_host.copy_(flat, non_blocking=True)
+
+    def cpu_baseline(self):
+        import oracle
+        oracle.build()
+        f0 = self.f[0].astype("float64")
+        c0 = self.clean[0].astype("float64")
+
+        def band(r):
+            ua = oracle.forward(f0[:r].copy(), self.p)
+            oracle.backward(f0[:r].copy(), self.p, ua, ua[-1] - c0[:r])
+
+        rows, dt = _rows_rate(band, 6, 12.0, self.S)
+        return {"value": rows * self.S / dt / 1e6, "unit": "Mpixel/s",
+                "cores": oracle.get_threads(), "kind": "oracle",
+                "sample": f"rows 0..{rows - 1} of crop 0, forward + backward of all "
+                          f"T={self.T} stages ({dt:.1f} s)"}
+
+
+def make_workload(name, dev):
+    if name == "fwd512":
+        return Fwd(dev)
+    if name == "fwd512_unfused":
+        return Fwd(dev, algo="unfused")
+    if name == "small128":
+        return Fwd(dev, H=128, W=128, ks=5, nk=24, cfg=1)
+    if name == "batched":
+        return Batched(dev)
+    if name == "train":
+        return Train(dev)
+    raise ValueError(name)
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import numpy as np
     import oracle
+    import synth
     oracle.build()
-    p, f = _inputs()
-    # size the row band so that one step takes about 1-4 s
-    rows = 8
-    _, dt = _cpu_oracle_rate(p, f, rows)
-    rows = int(max(4, min(H, rows * 2.0 / max(dt, 1e-3))))
+    p = _p32(synth.params(T, KS, NK, seed=synth.seed_for(CFG_ID, 0, "params")))
+    _, f = synth.single_image(H, W, L, CFG_ID, index=0)
+    f = f.astype(np.float32).astype(np.float64)
+    band = lambda r: oracle.forward(f[:r].copy(), p)
+    rows, _ = _rows_rate(band, 8, 2.0, H)     # one step about 1-4 s
     for _ in range(args.warmup):
-        _cpu_oracle_rate(p, f, rows)
+        band(rows)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.forward(f[:rows].copy(), p)
+        band(rows)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(times)
     value = rows * W / (ms / 1e3) / 1e6
@@ -196,126 +458,91 @@ def run_reference(args):
 
 
 def run_ours(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.workload != "fwd512":
+        if rank == 0:
+            print(json.dumps({"workload": args.workload,
+                              "unavailable": "multi-GPU runs use the default fwd512 workload"}))
+        return 0
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    from paper_1702_07482_gb300 import binding, build, ops
+    from paper_1702_07482_gb300 import binding, build
     build.build()
     binding.load()
-
-    p, f = _inputs()
-    m = ops.Model.create(p.filters, p.rbf_w, p.lam, p.mu0, p.delta, p.gamma, device=dev)
-    f_dev = torch.tensor(f, dtype=torch.float32, device=dev).unsqueeze(0).contiguous()
-    u_dev = torch.empty_like(f_dev)
-    prm = m.params()
-    ws_bytes = binding.tnrd_workspace_size(binding.OP_FORWARD, prm, 1, H, W, W, 0, 0)
-    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+    wl = make_workload(args.workload, dev)
     stream = torch.cuda.current_stream(dev)
-    sp = stream.cuda_stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    def step():
-        binding.tnrd_forward(prm, 1, H, W, W, f_dev, u_dev, 0, 0, ws, ws_bytes, sp)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    barrier()
+    def timed(fn):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        barrier()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)          # evict the previous step's data from L2
+            evs[i][0].record(stream)
+            fn()
+            evs[i][1].record(stream)
+        barrier()
+        return [a.elapsed_time(b) for a, b in evs]
 
+    for _ in range(max(args.warmup, 3)):
+        wl.step()
+    barrier()
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    barrier()
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)          # evict the image from L2 between steps
-        evs[i][0].record(stream)
-        step()
-        evs[i][1].record(stream)
-    barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-
-    # end to end through the C ABI: pinned host input -> device -> stage
-    # cascade -> pinned host output, all inside the events
-    f_host = torch.tensor(f, dtype=torch.float32).unsqueeze(0).contiguous().pin_memory()
-    u_host = torch.empty_like(f_host).pin_memory()
-    e2e_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
+    step_ms = timed(wl.step)
+    # end to end through the C ABI: pinned host inputs -> device -> path ->
+    # pinned host result, all inside the events
     for _ in range(3):
-        f_dev.copy_(f_host, non_blocking=True)
-        step()
-        u_host.copy_(u_dev, non_blocking=True)
-    barrier()
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        e2e_evs[i][0].record(stream)
-        f_dev.copy_(f_host, non_blocking=True)
-        step()
-        u_host.copy_(u_dev, non_blocking=True)
-        e2e_evs[i][1].record(stream)
-    barrier()
+        wl.e2e()
+    e2e_ms = timed(wl.e2e)
     clocks = sampler.stop()
-    e2e_ms = [a.elapsed_time(b) for a, b in e2e_evs]
 
-    ms = statistics.mean(step_ms)
-    ms_e2e = statistics.mean(e2e_ms)
-    # every rank ran its own image: all ranks' pixels over the slowest rank's time
     from paper_1702_07482_gb300.shard import global_rate
-    value, ms = global_rate(H * W, ms)
-    e2e_value, ms_e2e = global_rate(H * W, ms_e2e)
+    value, ms = global_rate(wl.px, statistics.mean(step_ms))
+    e2e_value, ms_e2e = global_rate(wl.px, statistics.mean(e2e_ms))
     out = None
     if rank == 0:
         peaks, src = _peaks()
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak_tf = _fp32_peak_tflops(sm_max, n_sm)
-        launch_ms = ms / T   # T launches of the stage kernel per step, back to back
-        achieved_tf = H * W * FLOPS_PER_PX_STAGE / (launch_ms / 1e3) / 1e12
-        traffic = _measured_traffic()
-        cpu = None
-        if not args.no_cpu_baseline:
-            import oracle
-            oracle.build()
-            rows = 16
-            rate, dt = _cpu_oracle_rate(p, f, rows)
-            rows = int(max(8, min(H, rows * 12.0 / max(dt, 1e-3))))
-            rate, dt = _cpu_oracle_rate(p, f, rows)
-            cpu = {"value": rate, "unit": "Mpixel/s", "cores": oracle.get_threads(),
-                   "kind": "oracle",
-                   "sample": f"rows 0..{rows - 1} of the 512x512 image, all T={T} stages "
-                             f"({dt:.1f} s)"}
+        achieved_tf = wl.flops / (ms / 1e3) / 1e12
+        cpu = None if args.no_cpu_baseline else wl.cpu_baseline()
         out = {
             "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": CONFIG,
+            "config": wl.config,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                         "traffic": traffic,
-                         "kernel": "fused_stage_fwd<7,48,TH>",
+                         "traffic": wl.traffic,
+                         "kernel": wl.kernel,
+                         "launches_per_step": wl.launches,
+                         "achieved_basis": "algorithmic flops per step / step time (the step's "
+                                           "launches run back to back on one stream)",
                          "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x "
                                         f"{sm_max:.0f} MHz ({src} sm_max_mhz)",
-                         "flops_per_px_stage": FLOPS_PER_PX_STAGE},
+                         "flops_per_px_stage": wl.flops_per_px_stage},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "Mpixel/s",
-                    "h2d_bytes_per_step": int(f_host.numel() * 4),
-                    "d2h_bytes_per_step": int(u_host.numel() * 4)},
-            "gpu_launches": args.steps * T,
+            "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": wl.h2d,
+                    "d2h_bytes_per_step": wl.d2h},
+            "gpu_launches": args.steps * wl.launches,
             "clocks": clocks,
         }
     if world > 1:
@@ -332,6 +559,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="fwd512",
+                    choices=["fwd512", "fwd512_unfused", "small128", "batched", "train"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
