@@ -57,7 +57,10 @@ typedef enum {
 /* How the stage is computed.  All give the same result within the stated
  * tolerances; FUSED and UNFUSED compute in FP32, the tensor-core variants run
  * the filter bank and its adjoint with TF32 / BF16 operands and FP32
- * accumulation, phi and the prox in FP32. */
+ * accumulation, phi and the prox in FP32.  TNRD_ALGO_TC_TF32: the filter bank
+ * and the adjoint run as tcgen05 implicit GEMMs with TF32 operands (u, the
+ * filters and phi's outputs rounded to TF32, 10-bit mantissa); its error
+ * against the FP64 result is larger than the FP32 paths' (see the tests). */
 typedef enum {
     TNRD_ALGO_FUSED = 0,      /* one kernel per stage, responses kept on chip      */
     TNRD_ALGO_UNFUSED = 1,    /* three kernels per stage, N_k response planes in HBM */
@@ -191,6 +194,12 @@ TNRD_API void tnrd_plan_destroy(tnrd_plan* plan);
 TNRD_API tnrd_status tnrd_forward_noalloc(const tnrd_params* params, int N, int H, int W,
                                           int pitch, const float* f, float* u,
                                           cudaStream_t stream);
+
+/* Synchronous: TNRD_OK, or TNRD_ERR_TIMEOUT if a tensor-core stage launched
+ * since the last call gave up waiting for its tensor-core operations (a
+ * bounded wait; the affected tile's output is then not written).  Reading
+ * clears the device-side word. */
+TNRD_API tnrd_status tnrd_device_status(void);
 
 /* Message describing the last error status returned on this host thread. */
 TNRD_API const char* tnrd_last_error(void);

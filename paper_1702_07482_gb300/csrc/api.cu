@@ -200,6 +200,15 @@ extern "C" {
 
 const char* tnrd_last_error(void) { return g_err.c_str(); }
 
+tnrd_status tnrd_device_status(void)
+{
+    int v = 0;
+    cudaError_t e = tnrd::tc_take_error(&v);
+    if (e != cudaSuccess) return cuda_fail(e, "device status read");
+    if (v != 0) return fail((tnrd_status)v, "a tensor-core stage gave up waiting for its MMAs");
+    return TNRD_OK;
+}
+
 int tnrd_version(void) { return 1 * 10000 + 0 * 100 + 0; }
 
 size_t tnrd_workspace_size(tnrd_op op, const tnrd_params* params, int N, int H, int W,
@@ -220,7 +229,7 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
     if (st != TNRD_OK) return st;
     st = check_images(N, H, W, pitch, p->ksize);
     if (st != TNRD_OK) return st;
-    if (algo != TNRD_ALGO_FUSED && algo != TNRD_ALGO_UNFUSED)
+    if (algo != TNRD_ALGO_FUSED && algo != TNRD_ALGO_UNFUSED && algo != TNRD_ALGO_TC_TF32)
         return fail(TNRD_ERR_UNSUPPORTED, "algo %d not available in tnrd_forward", (int)algo);
     if (N == 0) return TNRD_OK;
     if (!f || !u) return fail(TNRD_ERR_INVALID_ARG, "null image pointer");
@@ -244,6 +253,11 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
     const tnrd::RbfConst rc = make_rbf(p);
     const int ks = p->ksize, nk = p->nfilt;
     const int th = (algo == TNRD_ALGO_FUSED) ? pick_fused_th(ks, nk, N, H, W) : 0;
+    int tc_nb = 2;
+    if (const char* env = std::getenv("TNRD_TC_NB")) {   // tuning override
+        const int v = std::atoi(env);
+        if (v == 2 || v == 3) tc_nb = v;
+    }
 
     for (int t = 0; t < p->T; ++t) {
         const float* in;
@@ -278,6 +292,24 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.nrbf = p->nrbf;
             a.rc = rc;
             e = tnrd::launch_fused_fwd(ks, nk, th, a, N, stream);
+        } else if (algo == TNRD_ALGO_TC_TF32) {
+            tnrd::StageArgs a{};
+            const int tw = 32 - 2 * (ks / 2), tth = tnrd::tc_tile_h(ks, tc_nb);
+            a.u_in = in;
+            a.u_out = out;
+            a.f = f;
+            a.img_stride = (long long)plane;
+            a.H = H;
+            a.W = W;
+            a.pitch = pitch;
+            a.tiles_x = (W + tw - 1) / tw;
+            a.tiles_y = (H + tth - 1) / tth;
+            a.k = kt;
+            a.w = wt;
+            a.lam = p->lambda + t;
+            a.nrbf = p->nrbf;
+            a.rc = rc;
+            e = tnrd::launch_tc_fwd(ks, nk, tc_nb, a, N, stream);
         } else {
             tnrd::UnfArgs a{};
             a.u_in = in;

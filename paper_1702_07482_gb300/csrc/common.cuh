@@ -171,6 +171,22 @@ __device__ __forceinline__ void rbf_phi_dphi_tab(float z, const float* __restric
     dphi = -rc.inv_g2 * fmaf(win.s, phi, -rc.delta * m1);
 }
 
+// phi(z) straight from the padded weights wp (wp[j + RBF_WPAD] = w_j): the
+// same window and Horner evaluation as rbf_phi_tab, with each coefficient
+// formed as w_j * E[|m|] on the fly instead of read from a table.
+__device__ __forceinline__ float rbf_phi_w(float z, const float* __restrict__ wp, const RbfConst& rc)
+{
+    const RbfWin2 w = rbf_win2(z, rc);
+    const float* wr = wp + w.row;   // wr[n] = wp[j0 + RBF_WIN + n] = w_{j0 - RBF_WIN + n}
+    float p = wr[2 * RBF_WIN] * rc.E[RBF_WIN];
+#pragma unroll
+    for (int n = 2 * RBF_WIN - 1; n >= 0; --n) {
+        const int m = n - RBF_WIN;
+        p = fmaf(p, w.q, wr[n] * rc.E[m < 0 ? -m : m]);
+    }
+    return w.pre * p;
+}
+
 // phi(z) from a coefficient table.
 __device__ __forceinline__ float rbf_phi_tab(float z, const float* __restrict__ tab,
                                              const RbfConst& rc)

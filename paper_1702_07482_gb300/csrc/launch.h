@@ -29,6 +29,12 @@ int fused_fwd_occupancy(int ks, int nk, int th, int nrbf);
 cudaError_t launch_fused_fwd(int ks, int nk, int th, const StageArgs& a, int N, cudaStream_t s);
 cudaError_t launch_unfused_fwd(int ks, const UnfArgs& a, int N, cudaStream_t s);
 
+// Tensor-core forward stage: tile height for NB row blocks, launcher, and the
+// device error word (read and cleared).
+int tc_tile_h(int ks, int nb);
+cudaError_t launch_tc_fwd(int ks, int nk, int nb, const StageArgs& a, int N, cudaStream_t s);
+cudaError_t tc_take_error(int* out);
+
 // Persistent batched forward.
 cudaError_t launch_batch_fwd(int ks, int nk, int th, const BatchArgs& a, int grid, cudaStream_t s);
 int batch_fwd_occupancy(int ks, int nk, int th, int nrbf);

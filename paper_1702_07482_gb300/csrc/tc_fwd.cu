@@ -1,0 +1,45 @@
+// Instantiations and launcher of the tensor-core forward stage.
+#include "launch.h"
+#include "tc_fwd.cuh"
+
+namespace tnrd {
+
+namespace {
+
+template <int KS, int NK, int NB>
+cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
+{
+    using C = TcCfg<KS, NK, NB>;
+    cudaError_t e = cudaFuncSetAttribute(tc_stage_fwd<KS, NK, NB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    tc_stage_fwd<KS, NK, NB><<<dim3(a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
+}
+
+#define TNRD_TC_CASES(X) \
+    X(3, 4, 2) X(3, 4, 3) X(5, 24, 2) X(5, 24, 3) X(7, 48, 2) X(7, 48, 3)
+
+}  // namespace
+
+int tc_tile_h(int ks, int nb) { return 16 * nb - 2 * (ks / 2); }
+
+cudaError_t launch_tc_fwd(int ks, int nk, int nb, const StageArgs& a, int N, cudaStream_t s)
+{
+#define X(K, NN, B) if (ks == K && nk == NN && nb == B) return launch_one<K, NN, B>(a, N, s);
+    TNRD_TC_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_take_error(int* out)
+{
+    int v = 0, zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_error, sizeof v);
+    if (e == cudaSuccess && v != 0) e = cudaMemcpyToSymbol(g_tc_error, &zero, sizeof zero);
+    *out = v;
+    return e;
+}
+
+}  // namespace tnrd

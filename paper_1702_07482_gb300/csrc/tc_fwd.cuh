@@ -1,0 +1,231 @@
+// Tensor-core forward stage (TNRD_ALGO_TC_TF32):
+//   z = K u      as an implicit GEMM  D_z[pixel][filter] (tcgen05, TF32 in, FP32 acc)
+//   v = phi(z)   on the CUDA cores (FP32), each thread one pixel, all filters
+//   Y = V Kmat   as a GEMM            D_Y[pixel][tap] = sum_i v_i(pixel) k_i[tap]
+//   h(q) = sum_tap Y[q + off(tap)][tap]   (adjoint; scattered on the CUDA cores)
+//   u_t = prox(u_{t-1} - fold(h))         (FP32, IEEE sqrt/div)
+//
+// Tile: TH = 16 NB - 2R rows x TW = 32 - 2R columns of output; its z-region is
+// 16 NB rows x 32 columns.  One MMA group = 128 z positions: 16 rows of one
+// row block x 8 columns of one residue class (columns r, r+4, .., r+28).
+//
+// Filter-bank operand A needs no im2col: for residue r the tile of u is kept
+// as a copy shifted by r columns (u_r[i][j] = u[i][j + r], TF32-rounded).  A
+// K-major core matrix is 8 rows of 16 bytes, rows 16 bytes apart, so reading
+// u_r with rows 4 floats apart gives A[m][b'] = u_r[row][4 m + b'] directly:
+// row m of the core matrix is pixel column r + 4 m, K index b' is the tap
+// column.  The second K core matrix (taps 4..7) starts 16 bytes later
+// (leading offset 16 B, overlapping the first); the next 8-pixel group is the
+// next image row (stride offset = the copy's row pitch).  Kernel row a is one
+// MMA of K = 8 with the start row shifted by a; taps b' >= ksize are zero in B.
+#pragma once
+#include "args.cuh"
+#include "tc_ptx.cuh"
+
+namespace tnrd {
+
+// Device-side failure word of the tensor-core kernels (0 = none); read and
+// cleared by tnrd_device_status().  Defined here: only tc_fwd.cu includes this
+// header (the library is built without relocatable device code).
+__device__ int g_tc_error = 0;
+
+template <int KS, int NK, int NB>
+__global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ StageArgs a)
+{
+    using C = TcCfg<KS, NK, NB>;
+    constexpr int R = C::R, TW = C::TW, TH = C::TH;
+    constexpr long long WAIT_LIMIT = 1ll << 31;   // SM cycles, about one second
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float* sU = reinterpret_cast<float*>(smem + C::OFF_U);
+    float* sBz = reinterpret_cast<float*>(smem + C::OFF_BZ);
+    float* sKm = reinterpret_cast<float*>(smem + C::OFF_KM);
+    float* sV = reinterpret_cast<float*>(smem + C::OFF_V);
+    float* sW = reinterpret_cast<float*>(smem + C::OFF_W);
+    float* sH = reinterpret_cast<float*>(smem + C::OFF_H);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + C::OFF_MISC);
+    uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n = blockIdx.y;
+    const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x - ty * a.tiles_x;
+    const int H = a.H, W = a.W;
+    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
+    const bool border = (ty == 0) || (ty == a.tiles_y - 1) || (tx == 0) || (tx == a.tiles_x - 1);
+    const float* uin = a.u_in + (size_t)n * a.img_stride;
+
+    // ---- stage operands in shared memory ----------------------------------
+    constexpr int UCOPY = C::UROWS * C::UPITCH;
+    for (int idx = tid; idx < 4 * UCOPY; idx += 128) {
+        const int r = idx / UCOPY, rem = idx - r * UCOPY;
+        const int i = rem / C::UPITCH, j = rem - i * C::UPITCH;
+        const int yy = sym_idx(y0 - 2 * R + i, H), xx = sym_idx(x0 - 2 * R + j + r, W);
+        sU[idx] = tc::to_tf32(__ldcg(uin + (size_t)yy * a.pitch + xx));
+    }
+    // B of the filter bank, per kernel row ka: B[nn][b'] = k_nn[ka][KS-1-b'],
+    // K-major core matrices [nn/8][b'/4][nn%8][b'%4]
+    for (int e = tid; e < KS * C::NPAD * 8; e += 128) {
+        const int ka = e / (C::NPAD * 8), rem = e - ka * (C::NPAD * 8);
+        const int nn = rem / 8, k = rem - nn * 8;
+        const float v = (nn < NK && k < KS) ? __ldg(a.k + (nn * KS + ka) * KS + (KS - 1 - k)) : 0.0f;
+        sBz[ka * C::NPAD * 8 + ((nn / 8) * 2 + k / 4) * 32 + (nn % 8) * 4 + (k % 4)] = tc::to_tf32(v);
+    }
+    // B of the adjoint GEMM: B[tap][i] = k_i[tap], core matrices [i/4][tap/8][tap%8][i%4]
+    for (int e = tid; e < C::NT * C::NKP; e += 128) {
+        const int tap = e / C::NKP, i = e - tap * C::NKP;
+        const float v = (tap < KS * KS && i < NK) ? __ldg(a.k + i * KS * KS + tap) : 0.0f;
+        sKm[((i / 4) * (C::NT / 8) + tap / 8) * 32 + (tap % 8) * 4 + (i % 4)] = tc::to_tf32(v);
+    }
+    for (int e = tid; e < NK * C::WPADN; e += 128) {
+        const int i = e / C::WPADN, jj = e - i * C::WPADN - RBF_WPAD;
+        sW[e] = (jj >= 0 && jj < a.nrbf) ? __ldg(a.w + i * a.nrbf + jj) : 0.0f;
+    }
+    for (int e = tid; e < 128 * C::NKP; e += 128) sV[e] = 0.0f;
+    for (int e = tid; e < 4 * C::HROWS * C::HPITCH; e += 128) sH[e] = 0.0f;
+    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (warp == 0) tc::tmem_alloc(tbase, C::TMEM_COLS);
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tbase;
+    const uint32_t tz = tmem, tyv = tmem + 64;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    constexpr uint32_t ID_Z = tc::idesc(tc::FMT_TF32, 128, C::NPAD);
+    constexpr uint32_t ID_Y = tc::idesc(tc::FMT_TF32, 128, C::NT);
+    constexpr uint32_t LBO_KM = (C::NT / 8) * 128;
+    const RbfConst& rc = a.rc;
+
+    const int g = tid >> 3, mp = tid & 7;       // this thread's pixel in every group
+    float* myh = sH + warp * (C::HROWS * C::HPITCH);
+    uint32_t phase = 0;
+    int ok = 1;
+
+#pragma unroll 1
+    for (int nb = 0; nb < NB; ++nb) {
+#pragma unroll 1
+        for (int r = 0; r < 4; ++r) {
+            // ---- z = K u for the 128 positions of group (nb, r) ----------------
+            if (ok) {
+                if (tid == 0) {
+                    const float* ur = sU + r * UCOPY;
+#pragma unroll
+                    for (int ka = 0; ka < KS; ++ka) {
+                        const uint64_t da = tc::sdesc(tc::smem_u32(ur + (16 * nb + 2 * R - ka) * C::UPITCH),
+                                                      16, C::UPITCH * 4);
+                        const uint64_t db = tc::sdesc(tc::smem_u32(sBz + ka * C::NPAD * 8), 128, 256);
+                        tc::mma_tf32(tz, da, db, ID_Z, ka > 0);
+                    }
+                    tc::commit(mbar);
+                }
+                ok = tc::mbar_wait(mbar, phase & 1, WAIT_LIMIT);
+                ++phase;
+                tc::fence_after();
+            }
+            ok = __syncthreads_and(ok);
+            // ---- v = phi(z) into the A operand of the adjoint GEMM ---------------
+            const int yy = y0 - R + 16 * nb + g, xx = x0 - R + r + 4 * mp;
+            const bool inside = (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
+            if (ok) {
+#pragma unroll 1
+                for (int c8 = 0; c8 < NK; c8 += 8) {
+                    float z[8], v[8];
+                    tc::tmem_ld8(tz + lane_base + c8, z);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int i = c8 + q;
+                        v[q] = (i < NK && inside) ? rbf_phi_w(z[q], sW + i * C::WPADN, rc) : 0.0f;
+                    }
+                    // A layout [filter/4][g][mp][filter%4]: core matrices of 8 positions x 4 filters
+                    float4* d0 = reinterpret_cast<float4*>(sV + ((c8 / 4) * 16 + g) * 32 + mp * 4);
+                    *d0 = make_float4(tc::to_tf32(v[0]), tc::to_tf32(v[1]), tc::to_tf32(v[2]), tc::to_tf32(v[3]));
+                    if (c8 + 4 < C::NKP) {
+                        float4* d1 = reinterpret_cast<float4*>(sV + ((c8 / 4 + 1) * 16 + g) * 32 + mp * 4);
+                        *d1 = make_float4(tc::to_tf32(v[4]), tc::to_tf32(v[5]), tc::to_tf32(v[6]), tc::to_tf32(v[7]));
+                    }
+                }
+            }
+            tc::fence_async_smem();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+            // ---- Y = V Kmat --------------------------------------------------------
+            if (ok) {
+                if (tid == 0) {
+#pragma unroll
+                    for (int s = 0; s < C::NKP / 8; ++s) {
+                        const uint64_t da = tc::sdesc(tc::smem_u32(sV + s * 2 * (16 * 32)), 16 * 128, 128);
+                        const uint64_t db = tc::sdesc(tc::smem_u32(sKm + s * 2 * (LBO_KM / 4)), LBO_KM, 128);
+                        tc::mma_tf32(tyv, da, db, ID_Y, s > 0);
+                    }
+                    tc::commit(mbar);
+                }
+                ok = tc::mbar_wait(mbar, phase & 1, WAIT_LIMIT);
+                ++phase;
+                tc::fence_after();
+            }
+            ok = __syncthreads_and(ok);
+            // ---- scatter: h(p - off(tap)) += Y[p][tap] into this warp's partial ----
+            // (tcgen05.ld is warp-collective: every lane loads; lanes outside the
+            // image have v = 0, hence Y = 0, and add zeros at in-range indices)
+            if (ok) {
+                const int base = (16 * nb + g + 2 * R) * C::HPITCH + (r + 4 * mp + 2 * R);
+#pragma unroll
+                for (int c8 = 0; c8 < KS * KS; c8 += 8) {
+                    float y[8];
+                    tc::tmem_ld8(tyv + lane_base + c8, y);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int t = c8 + q;
+                        if (t < KS * KS) myh[base - (t / KS) * C::HPITCH - (t % KS)] += y[q];
+                    }
+                }
+            }
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+        }
+    }
+
+    // ---- epilogue: g = fold(sum of the warps' h), u_t = prox(u_{t-1} - g) ------
+    if (ok) {
+        const float lam = __ldg(a.lam);
+        const int wy0 = tile_split(ty, TH, H, a.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, a.tiles_y, R);
+        const int wx0 = tile_split(tx, TW, W, a.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, a.tiles_x, R);
+        const float* fimg = a.f + (size_t)n * a.img_stride;
+        float* uout = a.u_out + (size_t)n * a.img_stride;
+        for (int idx = tid; idx < TH * TW; idx += 128) {
+            const int qy = y0 + idx / TW, qx = x0 + idx % TW;
+            if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
+            int sy[2], sx[2];
+            int nsy = 1, nsx = 1;
+            sy[0] = qy;
+            sx[0] = qx;
+            if (border) {
+                if (qy < R) sy[nsy++] = -1 - qy;
+                else if (qy >= H - R) sy[nsy++] = 2 * H - 1 - qy;
+                if (qx < R) sx[nsx++] = -1 - qx;
+                else if (qx >= W - R) sx[nsx++] = 2 * W - 1 - qx;
+            }
+            float gsum = 0.0f;
+            for (int p = 0; p < nsy; ++p) {
+                for (int q = 0; q < nsx; ++q) {
+                    const int hi = sy[p] - (y0 - 2 * R), hj = sx[q] - (x0 - 2 * R);
+                    float hs = 0.0f;
+#pragma unroll
+                    for (int wq = 0; wq < 4; ++wq) hs += sH[wq * (C::HROWS * C::HPITCH) + hi * C::HPITCH + hj];
+                    gsum += hs;
+                }
+            }
+            const float up = __ldcg(uin + (size_t)qy * a.pitch + qx);
+            const float fv = __ldg(fimg + (size_t)qy * a.pitch + qx);
+            uout[(size_t)qy * a.pitch + qx] = prox_idiv(up - gsum, fv, lam);
+        }
+    } else if (tid == 0) {
+        atomicExch(&g_tc_error, 4);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+}  // namespace tnrd
