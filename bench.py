@@ -8,12 +8,15 @@ GPUs (torchrun), every rank runs its own image (independent problems, no
 collective on the data path): weak scaling.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fwd512|fwd512_unfused|small128|batched|train]
+                  [--workload fwd512|fwd512_unfused|small128|batched|train|
+                              mixed_tf32|mixed_fp32]
 
 The other workloads (one GPU) measure the rest of the table with the same
 contract: fwd512_unfused (three kernels per stage), small128 (1 x 128^2,
 5x5x24), batched (64 images of 256-1024 px per side, four parameter sets, one
-persistent launch per step), train (32 x 180^2 crops, forward + backward).
+persistent launch per step), train (32 x 180^2 crops, forward + backward),
+mixed_tf32 / mixed_fp32 (16 x 2048^2, L = 2, T = 8, tensor-core TF32 vs plain
+FP32; the line adds the path's error against the FP64 oracle).
 
 Prints ONE JSON line (rank 0).  `value` is Mpixel/s over all ranks with the
 inputs resident in HBM (L2 flushed between steps by a 256 MiB write, outside
@@ -404,6 +407,94 @@ class Train(Workload):
                           f"T={self.T} stages ({dt:.1f} s)"}
 
 
+class Mixed(Workload):
+    """16 images of 2048 x 2048, L = 2, 7x7x48, T = 8, as one batch."""
+
+    def __init__(self, dev, algo="tf32", n=16, S=2048, T_=8, cfg=5):
+        super().__init__(dev)
+        import numpy as np
+        import torch
+        import synth
+        from paper_1702_07482_gb300 import binding as B
+        from paper_1702_07482_gb300 import ops
+        self.T, self.n, self.S, self.algo = T_, n, S, algo
+        self.dtype = "tf32 operands, f32 accumulate" if algo == "tf32" else "f32"
+        self.p = _p32(synth.params(T_, KS, NK, seed=synth.seed_for(cfg, 0, "params")))
+        self.m = ops.Model.create(self.p.filters, self.p.rbf_w, self.p.lam, device=dev)
+        self.prm = self.m.params()
+        self.f_host = torch.empty((n, S, S), dtype=torch.float32).pin_memory()
+        self.f0 = None
+        for i in range(n):
+            _, f = synth.single_image(S, S, 2, cfg, index=i)
+            self.f_host[i] = torch.from_numpy(f.astype(np.float32))
+            if i == 0:
+                self.f0 = f.astype(np.float32).astype(np.float64)
+        self.f_dev = self.f_host.to(dev)
+        self.u_dev = torch.empty_like(self.f_dev)
+        self.u_host = torch.empty_like(self.f_host).pin_memory()
+        self.code = B.ALGO["fused" if algo == "fp32" else algo]
+        self.ws_bytes = B.tnrd_workspace_size(B.OP_FORWARD, self.prm, n, S, S, S, 0, self.code)
+        self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=dev)
+        self.sp = torch.cuda.current_stream(dev).cuda_stream
+        self.px = n * S * S
+        self.launches = T_
+        self.flops = float(self.px) * T_ * FLOPS_PER_PX_STAGE
+        self.flops_per_px_stage = FLOPS_PER_PX_STAGE
+        self.kernel = ("tc_stage_fwd<7,48,2> (tcgen05 TF32 filter bank and adjoint, FP32 phi/prox)"
+                       if algo == "tf32" else "fused_stage_fwd<7,48,TH> (FP32)")
+        self.h2d = self.d2h = int(self.f_host.numel() * 4)
+        self.config = {"workload": f"TRDMD forward, {n} x {S}x{S}, L=2, 7x7x48, 63 RBF, T={T_}, "
+                                   f"{'filter bank and adjoint on tensor cores (TF32 operands, FP32 accumulate), phi and prox FP32' if algo == 'tf32' else 'plain FP32 fused stage kernel'}",
+                       "images": n, "H": S, "W": S, "ksize": KS, "nfilt": NK, "nrbf": 63, "T": T_,
+                       "looks": 2, "precision": algo,
+                       "l2": f"inputs ({self.h2d / 2 ** 20:.0f} MiB) larger than L2"}
+
+    def step(self):
+        from paper_1702_07482_gb300 import binding as B
+        B.tnrd_forward(self.prm, self.n, self.S, self.S, self.S, self.f_dev, self.u_dev, 0,
+                       self.code, self.ws, self.ws_bytes, self.sp)
+
+    def e2e(self):
+        self.f_dev.copy_(self.f_host, non_blocking=True)
+        self.step()
+        self.u_host.copy_(self.u_dev, non_blocking=True)
+
+    def accuracy(self):
+        """max |du| and PSNR against the FP64 oracle on sampled pixels of image 0
+        (the oracle runs on crops the crop edge cannot reach, radius 2RT)."""
+        import numpy as np
+        import oracle
+        oracle.build()
+        self.step()
+        import torch
+        torch.cuda.synchronize()
+        u0 = self.u_dev[0].double().cpu().numpy()
+        S, M = self.S, 2 * (KS // 2) * self.T
+        g = np.random.Generator(np.random.PCG64(5))
+        pts = [(0, 0), (S - 1, S - 1), (0, S // 2)] + [tuple(x) for x in g.integers(0, S, size=(9, 2))]
+        d = []
+        for (y, x) in pts:
+            y0, y1 = max(0, y - M), min(S, y + M + 1)
+            x0, x1 = max(0, x - M), min(S, x + M + 1)
+            ref = oracle.forward(self.f0[y0:y1, x0:x1].copy(), self.p)[-1][y - y0, x - x0]
+            d.append(u0[y, x] - ref)
+        d = np.array(d)
+        mse = float((d ** 2).mean())
+        return {"vs": "FP64 oracle", "pixels": len(pts), "max_abs": float(np.abs(d).max()),
+                "psnr_db": 10 * np.log10(255.0 ** 2 / max(mse, 1e-30)),
+                "scale": "[0, 255] intensities"}
+
+    def cpu_baseline(self):
+        import oracle
+        oracle.build()
+        band = lambda r: oracle.forward(self.f0[:r].copy(), self.p)
+        rows, dt = _rows_rate(band, 4, 12.0, self.S)
+        return {"value": rows * self.S / dt / 1e6, "unit": "Mpixel/s",
+                "cores": oracle.get_threads(), "kind": "oracle",
+                "sample": f"rows 0..{rows - 1} of image 0 (2048 wide), all T={self.T} stages "
+                          f"({dt:.1f} s)"}
+
+
 def make_workload(name, dev):
     if name == "fwd512":
         return Fwd(dev)
@@ -415,6 +506,10 @@ def make_workload(name, dev):
         return Batched(dev)
     if name == "train":
         return Train(dev)
+    if name == "mixed_tf32":
+        return Mixed(dev, algo="tf32")
+    if name == "mixed_fp32":
+        return Mixed(dev, algo="fp32")
     raise ValueError(name)
 
 
@@ -523,11 +618,12 @@ def run_ours(args):
         peak_tf = _fp32_peak_tflops(sm_max, n_sm)
         achieved_tf = wl.flops / (ms / 1e3) / 1e12
         cpu = None if args.no_cpu_baseline else wl.cpu_baseline()
+        acc = wl.accuracy() if hasattr(wl, "accuracy") else None
         out = {
             "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": getattr(wl, "dtype", "f32"), "data": "synthetic",
             "config": wl.config,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
@@ -545,6 +641,8 @@ def run_ours(args):
             "gpu_launches": args.steps * wl.launches,
             "clocks": clocks,
         }
+        if acc is not None:
+            out["accuracy"] = acc
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -560,7 +658,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fwd512",
-                    choices=["fwd512", "fwd512_unfused", "small128", "batched", "train"])
+                    choices=["fwd512", "fwd512_unfused", "small128", "batched", "train",
+                             "mixed_tf32", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
