@@ -44,15 +44,22 @@ def clean_image(H: int, W: int, seed: int) -> np.ndarray:
     img = 40.0 + 60.0 * xx / max(W, 1) + 40.0 * yy / max(H, 1)
     n_shapes = int(np.ceil(20.0 * H * W / (256.0 * 256.0)))
     for s in range(n_shapes):
-        cy, cx = g.uniform(0, H), g.uniform(0, W)
+        cy = g.uniform(0, H)
+        cx = g.uniform(0, W)
         hy = 0.5 * g.uniform(0.05, 0.40) * H
         hx = 0.5 * g.uniform(0.05, 0.40) * W
         val = g.uniform(1.0, 255.0)
+        # only the shape's bounding box can hold pixels of the shape
+        r0, r1 = max(0, int(np.floor(cy - hy)) - 1), min(H, int(np.ceil(cy + hy)) + 2)
+        c0, c1 = max(0, int(np.floor(cx - hx)) - 1), min(W, int(np.ceil(cx + hx)) + 2)
+        if r0 >= r1 or c0 >= c1:
+            continue
+        by, bx = yy[r0:r1, c0:c1], xx[r0:r1, c0:c1]
         if s % 2 == 0:
-            m = (np.abs(yy - cy) <= hy) & (np.abs(xx - cx) <= hx)
+            m = (np.abs(by - cy) <= hy) & (np.abs(bx - cx) <= hx)
         else:
-            m = ((yy - cy) / hy) ** 2 + ((xx - cx) / hx) ** 2 <= 1.0
-        img[m] = val
+            m = ((by - cy) / hy) ** 2 + ((bx - cx) / hx) ** 2 <= 1.0
+        img[r0:r1, c0:c1][m] = val
     return np.clip(img, 1.0, 255.0)
 
 
