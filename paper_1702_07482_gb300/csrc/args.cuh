@@ -226,7 +226,7 @@ struct TcCfg {
     static constexpr size_t OFF_H = al(OFF_W + 4ull * NK * WPADN);
     static constexpr size_t OFF_MISC = al(OFF_H + 4ull * 4 * HROWS * HPITCH);
     static constexpr size_t SMEM_BYTES = OFF_MISC + 128;
-    static constexpr uint32_t TMEM_COLS = 128;
+    static constexpr uint32_t TMEM_COLS = 256;   // z double buffer (2 x 64) + Y (64), 2 CTAs per SM
 };
 
 }  // namespace tnrd

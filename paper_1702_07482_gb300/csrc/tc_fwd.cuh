@@ -42,8 +42,9 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
     float* sV = reinterpret_cast<float*>(smem + C::OFF_V);
     float* sW = reinterpret_cast<float*>(smem + C::OFF_W);
     float* sH = reinterpret_cast<float*>(smem + C::OFF_H);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + C::OFF_MISC);
-    uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC + 8);
+    uint64_t* mbz = reinterpret_cast<uint64_t*>(smem + C::OFF_MISC);       // 2 barriers
+    uint64_t* mby = reinterpret_cast<uint64_t*>(smem + C::OFF_MISC + 16);
+    uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC + 24);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int n = blockIdx.y;
@@ -81,14 +82,19 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
     }
     for (int e = tid; e < 128 * C::NKP; e += 128) sV[e] = 0.0f;
     for (int e = tid; e < 4 * C::HROWS * C::HPITCH; e += 128) sH[e] = 0.0f;
-    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (tid == 0) {
+        tc::mbar_init(mbz + 0, 1);
+        tc::mbar_init(mbz + 1, 1);
+        tc::mbar_init(mby, 1);
+    }
     if (warp == 0) tc::tmem_alloc(tbase, C::TMEM_COLS);
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tbase;
-    const uint32_t tz = tmem, tyv = tmem + 64;
+    // TMEM columns: z of even groups at 0, z of odd groups at 64, Y at 128
+    const uint32_t tyv = tmem + 128;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     constexpr uint32_t ID_Z = tc::idesc(tc::FMT_TF32, 128, C::NPAD);
     constexpr uint32_t ID_Y = tc::idesc(tc::FMT_TF32, 128, C::NT);
@@ -97,93 +103,105 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
 
     const int g = tid >> 3, mp = tid & 7;       // this thread's pixel in every group
     float* myh = sH + warp * (C::HROWS * C::HPITCH);
-    uint32_t phase = 0;
+    uint32_t phz = 0u, phy = 0u;   // bit b of phz: parity of z buffer b's next phase
     int ok = 1;
+    constexpr int NG = 4 * NB;                  // groups (row block, residue) per tile
+
+    // z = K u of group gi into TMEM buffer zb: one K = 8 MMA per kernel row
+    auto issue_z = [&](int gi, int zb) {
+        const int nb = gi >> 2, r = gi & 3;
+        const float* ur = sU + r * UCOPY;
+#pragma unroll
+        for (int ka = 0; ka < KS; ++ka) {
+            const uint64_t da = tc::sdesc(tc::smem_u32(ur + (16 * nb + 2 * R - ka) * C::UPITCH), 16,
+                                          C::UPITCH * 4);
+            const uint64_t db = tc::sdesc(tc::smem_u32(sBz + ka * C::NPAD * 8), 128, 256);
+            tc::mma_tf32(tmem + 64u * zb, da, db, ID_Z, ka > 0);
+        }
+        tc::commit(mbz + zb);
+    };
+    if (tid == 0) issue_z(0, 0);
 
 #pragma unroll 1
-    for (int nb = 0; nb < NB; ++nb) {
-#pragma unroll 1
-        for (int r = 0; r < 4; ++r) {
-            // ---- z = K u for the 128 positions of group (nb, r) ----------------
-            if (ok) {
-                if (tid == 0) {
-                    const float* ur = sU + r * UCOPY;
-#pragma unroll
-                    for (int ka = 0; ka < KS; ++ka) {
-                        const uint64_t da = tc::sdesc(tc::smem_u32(ur + (16 * nb + 2 * R - ka) * C::UPITCH),
-                                                      16, C::UPITCH * 4);
-                        const uint64_t db = tc::sdesc(tc::smem_u32(sBz + ka * C::NPAD * 8), 128, 256);
-                        tc::mma_tf32(tz, da, db, ID_Z, ka > 0);
-                    }
-                    tc::commit(mbar);
-                }
-                ok = tc::mbar_wait(mbar, phase & 1, WAIT_LIMIT);
-                ++phase;
-                tc::fence_after();
-            }
-            ok = __syncthreads_and(ok);
-            // ---- v = phi(z) into the A operand of the adjoint GEMM ---------------
-            const int yy = y0 - R + 16 * nb + g, xx = x0 - R + r + 4 * mp;
-            const bool inside = (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
-            if (ok) {
-#pragma unroll 1
-                for (int c8 = 0; c8 < NK; c8 += 8) {
-                    float z[8], v[8];
-                    tc::tmem_ld8(tz + lane_base + c8, z);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int i = c8 + q;
-                        v[q] = (i < NK && inside) ? rbf_phi_w(z[q], sW + i * C::WPADN, rc) : 0.0f;
-                    }
-                    // A layout [filter/4][g][mp][filter%4]: core matrices of 8 positions x 4 filters
-                    float4* d0 = reinterpret_cast<float4*>(sV + ((c8 / 4) * 16 + g) * 32 + mp * 4);
-                    *d0 = make_float4(tc::to_tf32(v[0]), tc::to_tf32(v[1]), tc::to_tf32(v[2]), tc::to_tf32(v[3]));
-                    if (c8 + 4 < C::NKP) {
-                        float4* d1 = reinterpret_cast<float4*>(sV + ((c8 / 4 + 1) * 16 + g) * 32 + mp * 4);
-                        *d1 = make_float4(tc::to_tf32(v[4]), tc::to_tf32(v[5]), tc::to_tf32(v[6]), tc::to_tf32(v[7]));
-                    }
-                }
-            }
-            tc::fence_async_smem();
-            tc::fence_before();
-            __syncthreads();
-            tc::fence_after();
-            // ---- Y = V Kmat --------------------------------------------------------
-            if (ok) {
-                if (tid == 0) {
-#pragma unroll
-                    for (int s = 0; s < C::NKP / 8; ++s) {
-                        const uint64_t da = tc::sdesc(tc::smem_u32(sV + s * 2 * (16 * 32)), 16 * 128, 128);
-                        const uint64_t db = tc::sdesc(tc::smem_u32(sKm + s * 2 * (LBO_KM / 4)), LBO_KM, 128);
-                        tc::mma_tf32(tyv, da, db, ID_Y, s > 0);
-                    }
-                    tc::commit(mbar);
-                }
-                ok = tc::mbar_wait(mbar, phase & 1, WAIT_LIMIT);
-                ++phase;
-                tc::fence_after();
-            }
-            ok = __syncthreads_and(ok);
-            // ---- scatter: h(p - off(tap)) += Y[p][tap] into this warp's partial ----
-            // (tcgen05.ld is warp-collective: every lane loads; lanes outside the
-            // image have v = 0, hence Y = 0, and add zeros at in-range indices)
-            if (ok) {
-                const int base = (16 * nb + g + 2 * R) * C::HPITCH + (r + 4 * mp + 2 * R);
-#pragma unroll
-                for (int c8 = 0; c8 < KS * KS; c8 += 8) {
-                    float y[8];
-                    tc::tmem_ld8(tyv + lane_base + c8, y);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int t = c8 + q;
-                        if (t < KS * KS) myh[base - (t / KS) * C::HPITCH - (t % KS)] += y[q];
-                    }
-                }
-            }
-            tc::fence_before();
-            __syncthreads();
+    for (int gi = 0; gi < NG; ++gi) {
+        const int nb = gi >> 2, r = gi & 3, zb = gi & 1;
+        if (ok) {
+            ok = tc::mbar_wait(mbz + zb, (phz >> zb) & 1u, WAIT_LIMIT);
+            phz ^= 1u << zb;
             tc::fence_after();
         }
+        ok = __syncthreads_and(ok);
+        // the next group's filter bank runs on the tensor core during phi
+        if (ok && tid == 0 && gi + 1 < NG) issue_z(gi + 1, zb ^ 1);
+        // ---- v = phi(z) into the A operand of the adjoint GEMM -------------------
+        const int yy = y0 - R + 16 * nb + g, xx = x0 - R + r + 4 * mp;
+        const bool inside = (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
+        if (ok) {
+#pragma unroll 1
+            for (int c8 = 0; c8 < NK; c8 += 8) {
+                float z[8], v[8];
+                tc::tmem_ld8(tmem + 64u * zb + lane_base + c8, z);
+                // branch-free: the 8 evaluations are independent and interleave
+                // (z is finite everywhere: u is mirror-loaded), then masked
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int i = c8 + q;
+                    const float ph = rbf_phi_w(z[q], sW + (i < NK ? i : 0) * C::WPADN, rc);
+                    v[q] = (i < NK && inside) ? ph : 0.0f;
+                }
+                // A layout [filter/4][g][mp][filter%4]: core matrices of 8 positions x 4 filters
+                float4* d0 = reinterpret_cast<float4*>(sV + ((c8 / 4) * 16 + g) * 32 + mp * 4);
+                *d0 = make_float4(tc::to_tf32(v[0]), tc::to_tf32(v[1]), tc::to_tf32(v[2]), tc::to_tf32(v[3]));
+                if (c8 + 4 < C::NKP) {
+                    float4* d1 = reinterpret_cast<float4*>(sV + ((c8 / 4 + 1) * 16 + g) * 32 + mp * 4);
+                    *d1 = make_float4(tc::to_tf32(v[4]), tc::to_tf32(v[5]), tc::to_tf32(v[6]), tc::to_tf32(v[7]));
+                }
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        // ---- Y = V Kmat ----------------------------------------------------------
+        if (ok) {
+            if (tid == 0) {
+#pragma unroll
+                for (int s = 0; s < C::NKP / 8; ++s) {
+                    const uint64_t da = tc::sdesc(tc::smem_u32(sV + s * 2 * (16 * 32)), 16 * 128, 128);
+                    const uint64_t db = tc::sdesc(tc::smem_u32(sKm + s * 2 * (LBO_KM / 4)), LBO_KM, 128);
+                    tc::mma_tf32(tyv, da, db, ID_Y, s > 0);
+                }
+                tc::commit(mby);
+            }
+            ok = tc::mbar_wait(mby, phy & 1, WAIT_LIMIT);
+            ++phy;
+            tc::fence_after();
+        }
+        ok = __syncthreads_and(ok);
+        // ---- scatter: h(p - off(tap)) += Y[p][tap] into this warp's partial ------
+        // (tcgen05.ld is warp-collective: every lane loads; lanes outside the
+        // image have v = 0, hence Y = 0, and add zeros at in-range indices)
+        if (ok) {
+            const int base = (16 * nb + g + 2 * R) * C::HPITCH + (r + 4 * mp + 2 * R);
+#pragma unroll
+            for (int c8 = 0; c8 < KS * KS; c8 += 8) {
+                float y[8];
+                tc::tmem_ld8(tyv + lane_base + c8, y);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int t = c8 + q;
+                    if (t < KS * KS) myh[base - (t / KS) * C::HPITCH - (t % KS)] += y[q];
+                }
+            }
+        }
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+    }
+    if (!ok) {
+        // give the MMAs in flight a bounded chance to finish before TMEM is freed
+        tc::mbar_wait(mbz + 0, phz & 1u, WAIT_LIMIT);
+        tc::mbar_wait(mbz + 1, (phz >> 1) & 1u, WAIT_LIMIT);
     }
 
     // ---- epilogue: g = fold(sum of the warps' h), u_t = prox(u_{t-1} - g) ------
