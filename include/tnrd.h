@@ -94,7 +94,8 @@ TNRD_API size_t tnrd_workspace_size(tnrd_op op, const tnrd_params* params, int N
  *   u      keep_stages != 0: [T+1][N][H][pitch] receives u_0 = f, u_1 .. u_T
  *                            (the checkpoints tnrd_backward needs);
  *          keep_stages == 0: [N][H][pitch] receives u_T only.
- * u must not overlap f.  Padding columns (W..pitch) are not written. */
+ * u must not overlap f.  Padding columns (W..pitch) of u_1..u_T are not
+ * written; u_0 is a byte copy of f, padding included. */
 TNRD_API tnrd_status tnrd_forward(const tnrd_params* params, int N, int H, int W, int pitch,
                          const float* f, float* u, int keep_stages, tnrd_algo algo,
                          void* workspace, size_t workspace_bytes, cudaStream_t stream);
