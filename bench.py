@@ -361,10 +361,10 @@ class Train(Workload):
                                   dtype=torch.float32).pin_memory()
         self.grads = None
         self.px = n * S * S
-        self.launches = T_ + T_ * 6
+        self.launches = T_ + T_ * 5   # forward stages; prep, zb, adj, dk, reduce per stage
         self.flops = float(self.px) * T_ * (FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE)
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE
-        self.kernel = "fused_stage_fwd + bwd_prep/bwd_bank/bwd_dk/bwd_reduce <7,48>"
+        self.kernel = "fused_stage_fwd + bwd_prep/bwd_zb/bwd_adj/bwd_dk/bwd_reduce <7,48>"
         self.h2d = int((self.f_host.numel() + self.c_host.numel()) * 4)
         self.d2h = int(self.g_host.numel() * 4)
         self.config = {"workload": f"TRDMD training step (forward + backward), {n} crops of "

@@ -167,17 +167,20 @@ FwdLayout fwd_layout(const tnrd_params* p, int N, int H, int pitch, int keep, tn
 
 struct BwdLayout {
     size_t d = 0, e0 = 0, e1 = 0, c = 0, v = 0, pw = 0, pk = 0, pl = 0, total = 0;
-    int tiles_x = 0, tiles_y = 0, dk_tiles_x = 0, dk_tiles_y = 0, prep_blocks = 0;
+    int zb_tiles_x = 0, zb_tiles_y = 0, tiles_x = 0, tiles_y = 0, dk_tiles_x = 0,
+        dk_tiles_y = 0, prep_blocks = 0;
 };
 
 BwdLayout bwd_layout(const tnrd_params* p, int N, int H, int W, int pitch)
 {
     BwdLayout L;
     const int ks = p->ksize, R = ks / 2, tw = 32 - 2 * R, th = tnrd::bwd_tile_h(ks);
+    L.zb_tiles_x = (W + 31) / 32;
+    L.zb_tiles_y = (H + th - 1) / th;
     L.tiles_x = (W + tw - 1) / tw;
     L.tiles_y = (H + th - 1) / th;
-    L.dk_tiles_x = (W + tnrd::DK_TW - 1) / tnrd::DK_TW;
-    L.dk_tiles_y = (H + tnrd::DK_TH - 1) / tnrd::DK_TH;
+    L.dk_tiles_x = (W + 31) / 32;
+    L.dk_tiles_y = (H + th - 1) / th;
     L.prep_blocks = (H * W + 255) / 256;
     const size_t batch = sizeof(float) * (size_t)N * H * pitch;
     size_t off = 0;
@@ -187,7 +190,7 @@ BwdLayout bwd_layout(const tnrd_params* p, int N, int H, int W, int pitch)
     L.e1 = take(batch);
     L.c = take(batch * (size_t)p->nfilt);
     L.v = take(batch * (size_t)p->nfilt);
-    L.pw = take(sizeof(float) * (size_t)N * L.tiles_x * L.tiles_y * p->nfilt * p->nrbf);
+    L.pw = take(sizeof(float) * (size_t)N * L.zb_tiles_x * L.zb_tiles_y * p->nfilt * p->nrbf);
     L.pk = take(sizeof(float) * (size_t)N * L.dk_tiles_x * L.dk_tiles_y * p->nfilt * ks * ks);
     L.pl = take(sizeof(float) * (size_t)N * L.prep_blocks);
     L.total = off;
@@ -380,6 +383,8 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
     a.H = H;
     a.W = W;
     a.pitch = pitch;
+    a.zb_tiles_x = L.zb_tiles_x;
+    a.zb_tiles_y = L.zb_tiles_y;
     a.tiles_x = L.tiles_x;
     a.tiles_y = L.tiles_y;
     a.dk_tiles_x = L.dk_tiles_x;
@@ -399,13 +404,13 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
         a.lam = p->lambda + t;
         cudaError_t e = tnrd::launch_bwd_stage(ks, nk, a, N, stream);
         if (e != cudaSuccess) return cuda_fail(e, "backward stage launch");
-        e = tnrd::launch_bwd_reduce(a.part_k, N * L.dk_tiles_x * L.dk_tiles_y, nk * ks * ks,
-                                    grad_filters + (size_t)t * nk * ks * ks, stream);
-        if (e == cudaSuccess)
-            e = tnrd::launch_bwd_reduce(a.part_w, N * L.tiles_x * L.tiles_y, nk * nrbf,
-                                        grad_rbf_w + (size_t)t * nk * nrbf, stream);
-        if (e == cudaSuccess)
-            e = tnrd::launch_bwd_reduce(a.part_l, N * L.prep_blocks, 1, grad_lambda + t, stream);
+        tnrd::RedArgs r{};
+        r.s[0] = {a.part_k, N * L.dk_tiles_x * L.dk_tiles_y, nk * ks * ks,
+                  grad_filters + (size_t)t * nk * ks * ks};
+        r.s[1] = {a.part_w, N * L.zb_tiles_x * L.zb_tiles_y, nk * nrbf,
+                  grad_rbf_w + (size_t)t * nk * nrbf};
+        r.s[2] = {a.part_l, N * L.prep_blocks, 1, grad_lambda + t};
+        e = tnrd::launch_bwd_reduce(r, stream);
         if (e != cudaSuccess) return cuda_fail(e, "gradient reduce launch");
     }
     return TNRD_OK;

@@ -103,12 +103,13 @@ struct UnfArgs {
 
 
 // ---------------------------------------------------------------------------
-// Backward stage (Sec. 3.2).  One stage t is four launches:
-//   bwd_prep : d = y .* e (Eq. derv2), per-block sums of x .* e (Eq. derv4)
-//   bwd_bank : z_i = K_i u, b_i = K_i d, c_i = -phi_i'(z_i) .* b_i, v_i = phi_i(z_i),
-//              e_{t-1} = d + sum_i K_i^T c_i (Eq. derv1-1), per-tile dL/dw partials;
-//              c_i and v_i of the tile's own pixels go to planes for bwd_dk
-//   bwd_dk   : per-tile dL/dk partials sum_p c_i(p) u(p+.) - v_i(p) d(p+.)
+// Backward stage (Sec. 3.2).  One stage t is five launches:
+//   bwd_prep  : d = y .* e (Eq. derv2), per-block sums of x .* e (Eq. derv4)
+//   bwd_zb    : z_i = K_i u, b_i = K_i d, c_i = -phi_i'(z_i) .* b_i, v_i = phi_i(z_i)
+//               on each tile's own pixels, written to the c and v planes, and
+//               per-tile dL/dw partials
+//   bwd_adj   : e_{t-1} = d + sum_i K_i^T c_i (Eq. derv1-1) from the c planes
+//   bwd_dk    : per-tile dL/dk partials sum_p c_i(p) u(p+.) - v_i(p) d(p+.)
 //   bwd_reduce: fixed-order sums of all partials into this stage's gradients
 // ---------------------------------------------------------------------------
 struct BwdArgs {
@@ -120,14 +121,15 @@ struct BwdArgs {
     float* e_prev;         // dL/du_{t-1} [N][H][pitch]
     float* cpl;            // c planes  [N][nfilt][H][pitch]
     float* vpl;            // v planes  [N][nfilt][H][pitch]
-    float* part_w;         // [N * bank tiles][nfilt][nrbf]
+    float* part_w;         // [N * zb tiles][nfilt][nrbf]
     float* part_k;         // [N * dk tiles][nfilt][ks*ks]
     float* part_l;         // [N * prep blocks]
     long long img_stride;  // floats between images of a plane set
     int H, W, pitch;
-    int tiles_x, tiles_y;      // bwd_bank tiling
+    int zb_tiles_x, zb_tiles_y;    // bwd_zb tiling (32 x ZB_TH, plain)
+    int tiles_x, tiles_y;          // bwd_adj tiling (as the fused forward)
     int dk_tiles_x, dk_tiles_y;
-    int prep_blocks;           // per image
+    int prep_blocks;               // per image
     const float* k;
     const float* w;
     const float* lam;
@@ -135,35 +137,57 @@ struct BwdArgs {
     RbfConst rc;
 };
 
+// bwd_zb: tiles of 32 columns (one per lane) x TH rows that do not overlap;
+// u and d are staged with an R-wide symmetric halo.  Each warp owns nfilt /
+// NWARP filters and keeps, per filter, a private dL/dw histogram per lane with
+// 2 RBF_WIN guard bins on each side (bin j at row j + 2 RBF_WIN), so that the
+// 13 window bins of any clamped z need no bounds test.
 template <int KS, int NK, int TH>
-struct BwdCfg {
+struct ZbCfg {
     static constexpr int R = KS / 2;
-    static constexpr int TW = 32 - 2 * R;
-    static constexpr int NWARP = NK >= 4 ? 4 : NK;
+    static constexpr int NWARP = NK >= 8 ? 8 : NK;
     static constexpr int NTHREADS = NWARP * 32;
     static constexpr int FPW = NK / NWARP;
     static_assert(NK % NWARP == 0, "filters must split evenly over the warps");
-    static constexpr int GROUPS_EXT = (TH + 6 * R + KS - 1) / KS;
-    static constexpr int GROUPS_INT = (TH + 4 * R + KS - 1) / KS;
-    static constexpr int UH_EXT = GROUPS_EXT * KS;
-    static constexpr int UH_INT = R + GROUPS_INT * KS;
-    static constexpr int UH = UH_EXT > UH_INT ? UH_EXT : UH_INT;
-    static constexpr int UW = 32 + 2 * R;
+    static constexpr int GROUPS = (TH + 2 * R + KS - 1) / KS;   // walk groups of KS steps
+    static constexpr int UH = GROUPS * KS;                       // u/d rows from y0 - R
+    static constexpr int UW = 32 + 2 * R;                        // u/d cols from x0 - R
     static constexpr int UP = UW;
-    static constexpr int H_FL = (TH + 2 * R) * 32;
+    static constexpr int U_FL = UH * UP;
+    static constexpr int HIST_ROWS = MAX_NRBF + 4 * RBF_WIN;
+    static constexpr int HIST_FL = HIST_ROWS * 32;
     static constexpr int KPAD = (KS * KS + 3) & ~3;
-    static constexpr int WPADN = MAX_NRBF + 2 * RBF_WPAD;
-    static constexpr int KW_FL = KPAD + WPADN;
-    static constexpr int HIST_FL = MAX_NRBF * 32;     // per-lane dL/dw bins: [j][lane]
-    static constexpr int TAB_FL = RBF_TP * RBF_NCOEF;
-    static constexpr int SMEM_FL = 2 * UH * UP + NWARP * (H_FL + KW_FL + HIST_FL + TAB_FL);
+    static constexpr int WPADN = (MAX_NRBF + 2 * RBF_WPAD + 3) & ~3;
+    static constexpr int PW_FL = HIST_FL + KPAD + WPADN;         // per warp
+    static constexpr int SMEM_FL = 2 * U_FL + NWARP * PW_FL;
     static constexpr size_t SMEM_BYTES = sizeof(float) * (size_t)SMEM_FL;
 };
 
-// bwd_dk tiling: 32-column tiles of DK_TH rows, NWARP_DK warps each owning
-// nfilt / NWARP_DK filters.
-constexpr int DK_TH = 32;
-constexpr int DK_TW = 32;
+// bwd_adj: tiles as the fused forward stage (TH rows x 32 - 2R columns, lane j
+// on column x0 - R + j); each warp accumulates the zero-extended adjoint h of
+// its filters in a private buffer of TH + 2R rows.
+template <int KS, int NK, int TH>
+struct AdjCfg {
+    static constexpr int R = KS / 2;
+    static constexpr int TW = 32 - 2 * R;
+    static constexpr int NWARP = NK >= 8 ? 8 : NK;
+    static constexpr int NTHREADS = NWARP * 32;
+    static constexpr int FPW = NK / NWARP;
+    static_assert(NK % NWARP == 0, "filters must split evenly over the warps");
+    static constexpr int H_FL = (TH + 2 * R) * 32;
+    static constexpr size_t SMEM_BYTES = sizeof(float) * (size_t)NWARP * H_FL;
+};
+
+// Gradient reduction: up to three (partials, rows, parameters, output) sets in
+// one launch, blockIdx.y selecting the set.
+struct RedSet {
+    const float* part;   // [nrows][nparam]
+    int nrows, nparam;
+    float* out;          // [nparam]
+};
+struct RedArgs {
+    RedSet s[3];
+};
 
 // ---------------------------------------------------------------------------
 // Persistent batched forward (tnrd_batch_forward).

@@ -59,14 +59,14 @@ __global__ void __launch_bounds__(256) bwd_prep(const BwdArgs a)
     }
 }
 
-// One group of KS walk steps of the backward bank kernel (geometry as in
-// walk_group of the forward stage; urow/drow index the u and d buffers).
+// One group of KS walk steps of bwd_zb starting at step m0.  Step m takes
+// u and d row y0 - R + m (shared-memory rows m); z and b of image row
+// y0 - 2R + m complete there (rolling accumulators, slot (step + a) mod KS).
 template <int KS, int UP>
-__device__ __forceinline__ void bwd_walk_group(
-    const float* __restrict__ urow, const float* __restrict__ drow, float* __restrict__ hrow,
-    const float (&kr)[KS][KS], float (&za)[KS], float (&ba)[KS], float (&ha)[KS], int m0,
-    int zrow0, int H, bool col_in, bool col_own, int wy0, int wy1, int mh_lo, int mh_hi, int lane,
-    const float* __restrict__ tab, float* __restrict__ hist, int nrbf, const RbfConst& rc,
+__device__ __forceinline__ void zb_group(
+    const float* __restrict__ urow, const float* __restrict__ drow, const float (&kr)[KS][KS],
+    float (&za)[KS], float (&ba)[KS], int m0, int y0, int H, int TH, bool col_in, int lane,
+    const float* __restrict__ wp, float* __restrict__ hist_lane, const RbfConst& rc,
     float* __restrict__ cpl_col, float* __restrict__ vpl_col, int pitch)
 {
     constexpr int R = KS / 2;
@@ -93,97 +93,66 @@ __device__ __forceinline__ void bwd_walk_group(
         const float z = za[mm], bv = ba[mm];
         za[mm] = 0.0f;
         ba[mm] = 0.0f;
-        const int zi = zrow0 + m;
-        const bool inside = col_in && (m >= 2 * R) && ((unsigned)zi < (unsigned)H);
-        float v, dphi;
-        RbfWin2 win;
-        rbf_phi_dphi_tab(z, tab, rc, v, dphi, win);
-        const float c = inside ? -dphi * bv : 0.0f;
-        v = inside ? v : 0.0f;
-        if (col_own && zi >= wy0 && zi < wy1) {
-            // own pixel: keep c and v for the filter gradient, and add
-            // -b G_j(z) to the lane's bins j = j0 - RBF_WIN .. j0 + RBF_WIN
+        const int zr = m - 2 * R;            // tile row of the completed z
+        const int zi = y0 + zr;
+        if (col_in && zr >= 0 && zr < TH && zi < H) {
+            float v, dphi;
+            RbfWin2 win;
+            rbf_phi_dphi_w(z, wp, rc, v, dphi, win);
+            const float c = -dphi * bv;
             cpl_col[(size_t)zi * pitch] = c;
             vpl_col[(size_t)zi * pitch] = v;
+            // dL/dw_j += -b G_j(z) for the window bins j = j0 - RBF_WIN + nn,
+            // stored at histogram row j + 2 RBF_WIN = win.row + nn
             float g = -bv * win.pre;
-            const int j_lo = win.row - 2 * RBF_WIN;     // j of coefficient n = 0
+            float* hp = hist_lane + win.row * 32;
 #pragma unroll
             for (int nn = 0; nn <= 2 * RBF_WIN; ++nn) {
-                const int mdev = nn - RBF_WIN;
-                const int j = j_lo + nn;
-                if (j >= 0 && j < nrbf) hist[j * 32 + lane] += g * rc.E[mdev < 0 ? -mdev : mdev];
+                const int md = nn - RBF_WIN;
+                hp[nn * 32] = fmaf(g, rc.E[md < 0 ? -md : md], hp[nn * 32]);
                 g *= win.q;
             }
         }
-        float cw[KS];
-        gather_row<KS, 0, true>(cw, c, lane);
-#pragma unroll
-        for (int b = 0; b < KS; ++b) {
-#pragma unroll
-            for (int q = 0; q < KS; ++q) {
-                const int s = (mm - q + 2 * KS) % KS;
-                ha[s] = fmaf(kr[q][b], cw[b], ha[s]);
-            }
-        }
-        const int sf = (mm - 2 * R + 2 * KS) % KS;
-        if (m >= mh_lo && m < mh_hi) hrow[m * 32] += ha[sf];
-        ha[sf] = 0.0f;
     }
 }
 
-// grid (tiles_x * tiles_y, N), BwdCfg::NTHREADS threads
+// grid (zb_tiles_x * zb_tiles_y, N), ZbCfg::NTHREADS threads, 2 CTAs per SM
 template <int KS, int NK, int TH>
-__global__ void __launch_bounds__(BwdCfg<KS, NK, TH>::NTHREADS)
-bwd_bank(const BwdArgs a)
+__global__ void __launch_bounds__(ZbCfg<KS, NK, TH>::NTHREADS, 2)
+bwd_zb(const __grid_constant__ BwdArgs a)
 {
-    using C = BwdCfg<KS, NK, TH>;
+    using C = ZbCfg<KS, NK, TH>;
     constexpr int R = C::R;
-    constexpr int TW = C::TW;
     extern __shared__ __align__(16) float smem[];
     float* sU = smem;
-    float* sD = sU + C::UH * C::UP;
-    float* sW = sD + C::UH * C::UP;   // per-warp blocks: H | KW | HIST | TAB
-
+    float* sD = sU + C::U_FL;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* myHist = sD + C::U_FL + warp * C::PW_FL;
+    float* myK = myHist + C::HIST_FL;
+    float* myWp = myK + C::KPAD;
+
     const int n = blockIdx.y;
-    const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x - ty * a.tiles_x;
+    const int ty = blockIdx.x / a.zb_tiles_x, tx = blockIdx.x - ty * a.zb_tiles_x;
     const int H = a.H, W = a.W;
-    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
-    const bool ext = (ty == 0) || (ty == a.tiles_y - 1);
-    const bool border = ext || (tx == 0) || (tx == a.tiles_x - 1);
+    const int y0 = ty * TH, x0 = tx * 32;
     const size_t ioff = (size_t)n * a.img_stride;
 
-    for (int idx = threadIdx.x; idx < C::UH * C::UW; idx += C::NTHREADS) {
+    for (int idx = threadIdx.x; idx < C::U_FL; idx += C::NTHREADS) {
         const int i = idx / C::UW, j = idx - i * C::UW;
-        const int yy = sym_idx(y0 - 3 * R + i, H), xx = sym_idx(x0 - 2 * R + j, W);
+        const int yy = sym_idx(y0 - R + i, H), xx = sym_idx(x0 - R + j, W);
         const size_t o = ioff + (size_t)yy * a.pitch + xx;
-        sU[i * C::UP + j] = a.u_prev[o];
-        sD[i * C::UP + j] = a.d[o];
+        sU[idx] = a.u_prev[o];
+        sD[idx] = a.d[o];
     }
-    float* myH = sW + warp * (C::H_FL + C::KW_FL + C::HIST_FL + C::TAB_FL);
-    float* myK = myH + C::H_FL;
-    float* myWp = myK + C::KPAD;
-    float* myHist = myK + C::KW_FL;
-    float* myT = myHist + C::HIST_FL;
-    for (int e = lane; e < C::H_FL; e += 32) myH[e] = 0.0f;
-    for (int e = lane; e < C::WPADN; e += 32) myWp[e] = 0.0f;
     for (int e = lane; e < C::HIST_FL; e += 32) myHist[e] = 0.0f;
+    for (int e = lane; e < C::WPADN; e += 32) myWp[e] = 0.0f;
     __syncthreads();
 
-    const int wy0 = tile_split(ty, TH, H, a.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, a.tiles_y, R);
-    const int wx0 = tile_split(tx, TW, W, a.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, a.tiles_x, R);
-    const int hy0 = ext ? y0 - R : y0;
-    const int nh = ext ? TH + 2 * R : TH;
-    const int nsteps = nh + 4 * R;
-    const int ub0 = ext ? 0 : R;
-    const float* urow = sU + ub0 * C::UP + lane;
-    const float* drow = sD + ub0 * C::UP + lane;
-    float* hrow = myH + (hy0 - 4 * R - (y0 - R)) * 32 + lane;
-    const int zrow0 = hy0 - 3 * R;
-    const int xcol = x0 - R + lane;
-    const bool col_in = (unsigned)xcol < (unsigned)W;
-    const bool col_own = xcol >= wx0 && xcol < wx1;
-    const int cta = n * (a.tiles_x * a.tiles_y) + blockIdx.x;
+    const int x = x0 + lane;
+    const bool col_in = x < W;
+    const float* urow = sU + lane;
+    const float* drow = sD + lane;
+    const int cta = n * (a.zb_tiles_x * a.zb_tiles_y) + blockIdx.x;
 
 #pragma unroll 1
     for (int fl = 0; fl < C::FPW; ++fl) {
@@ -191,41 +160,135 @@ bwd_bank(const BwdArgs a)
         for (int e = lane; e < KS * KS; e += 32) myK[e] = __ldg(a.k + fi * KS * KS + e);
         for (int e = lane; e < a.nrbf; e += 32) myWp[RBF_WPAD + e] = __ldg(a.w + fi * a.nrbf + e);
         __syncwarp();
-        rbf_build_table(myT, myWp, a.nrbf, a.rc, lane);
         float kr[KS][KS];
 #pragma unroll
         for (int p = 0; p < KS; ++p)
 #pragma unroll
             for (int q = 0; q < KS; ++q) kr[p][q] = myK[p * KS + q];
-        __syncwarp();
         const size_t plane = ioff * (size_t)a.nfilt + (size_t)fi * a.img_stride;
-        float* cpl_col = a.cpl + plane + (col_own ? xcol : 0);
-        float* vpl_col = a.vpl + plane + (col_own ? xcol : 0);
-        float za[KS], ba[KS], ha[KS];
+        float* cpl_col = a.cpl + plane + (col_in ? x : 0);
+        float* vpl_col = a.vpl + plane + (col_in ? x : 0);
+        float za[KS], ba[KS];
 #pragma unroll
-        for (int s = 0; s < KS; ++s) za[s] = ba[s] = ha[s] = 0.0f;
+        for (int s = 0; s < KS; ++s) za[s] = ba[s] = 0.0f;
 #pragma unroll 1
-        for (int m0 = 0; m0 < nsteps; m0 += KS)
-            bwd_walk_group<KS, C::UP>(urow, drow, hrow, kr, za, ba, ha, m0, zrow0, H, col_in,
-                                      col_own, wy0, wy1, 4 * R, nsteps, lane, myT, myHist,
-                                      a.nrbf, a.rc, cpl_col, vpl_col, a.pitch);
+        for (int g = 0; g < C::GROUPS; ++g)
+            zb_group<KS, C::UP>(urow, drow, kr, za, ba, g * KS, y0, H, TH, col_in, lane, myWp,
+                                myHist + lane, a.rc, cpl_col, vpl_col, a.pitch);
         __syncwarp();
         // per-tile dL/dw_i: sum the lanes' bins (skewed reads avoid bank conflicts)
         for (int j = lane; j < a.nrbf; j += 32) {
+            const float* hb = myHist + (j + 2 * RBF_WIN) * 32;
             float s = 0.0f;
 #pragma unroll 8
-            for (int l = 0; l < 32; ++l) s += myHist[j * 32 + ((l + j) & 31)];
+            for (int l = 0; l < 32; ++l) s += hb[(l + j) & 31];
             a.part_w[((size_t)cta * a.nfilt + fi) * a.nrbf + j] = s;
         }
         __syncwarp();
         for (int e = lane; e < C::HIST_FL; e += 32) myHist[e] = 0.0f;
         __syncwarp();
     }
+}
+
+// One group of KS walk steps of bwd_adj starting at step m0.  Step m takes c
+// row hy0 - R + m (cv[mm], this lane's column); h row hy0 - 2R + m completes
+// there and is added to the warp's buffer at hrow[m * 32].
+template <int KS>
+__device__ __forceinline__ void adj_group(const float (&cv)[KS], float* __restrict__ hrow,
+                                          const float (&kr)[KS][KS], float (&ha)[KS], int m0,
+                                          int mh_lo, int mh_hi, int lane)
+{
+    constexpr int R = KS / 2;
+#pragma unroll
+    for (int mm = 0; mm < KS; ++mm) {
+        const int m = m0 + mm;
+        float cw[KS];
+        gather_row<KS, 0, true>(cw, cv[mm], lane);   // cw[b] = c(row, x - R + b)
+        // h(q, x) += k[a][b] c(q - R + a, x - R + b): this c row feeds h rows
+        // q = row + R - a, slot (step + 2R - a) mod KS; slot mm completes (a = 2R)
+#pragma unroll
+        for (int b = 0; b < KS; ++b) {
+#pragma unroll
+            for (int q = 0; q < KS; ++q) {
+                const int s = (mm + 2 * R - q) % KS;
+                ha[s] = fmaf(kr[q][b], cw[b], ha[s]);
+            }
+        }
+        if (m >= mh_lo && m < mh_hi) hrow[m * 32] += ha[mm];
+        ha[mm] = 0.0f;
+    }
+}
+
+// grid (tiles_x * tiles_y, N), AdjCfg::NTHREADS threads.  Tiles, own regions
+// and the border fold as in the fused forward stage.
+template <int KS, int NK, int TH>
+__global__ void __launch_bounds__(AdjCfg<KS, NK, TH>::NTHREADS, 2)
+bwd_adj(const __grid_constant__ BwdArgs a)
+{
+    using C = AdjCfg<KS, NK, TH>;
+    constexpr int R = C::R;
+    constexpr int TW = C::TW;
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* myH = smem + warp * C::H_FL;   // h rows y0 - R .. y0 + TH + R - 1
+
+    const int n = blockIdx.y;
+    const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x - ty * a.tiles_x;
+    const int H = a.H, W = a.W;
+    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
+    const bool ext = (ty == 0) || (ty == a.tiles_y - 1);
+    const bool border = ext || (tx == 0) || (tx == a.tiles_x - 1);
+    const size_t ioff = (size_t)n * a.img_stride;
+    for (int e = lane; e < C::H_FL; e += 32) myH[e] = 0.0f;
+
+    const int hy0 = ext ? y0 - R : y0;           // first h row walked
+    const int nh = ext ? TH + 2 * R : TH;
+    const int nsteps = nh + 2 * R;               // c rows hy0 - R .. hy0 + nh + R - 1
+    const int ngroups = (nsteps + KS - 1) / KS;
+    const int xcol = x0 - R + lane;
+    const bool col_in = (unsigned)xcol < (unsigned)W;
+    // h row of step m is hy0 - 2R + m: buffer row hy0 - 2R + m - (y0 - R)
+    float* hrow = myH + (hy0 - R - y0) * 32 + lane;
+
+#pragma unroll 1
+    for (int fl = 0; fl < C::FPW; ++fl) {
+        const int fi = warp * C::FPW + fl;
+        float kr[KS][KS];
+#pragma unroll
+        for (int p = 0; p < KS; ++p)
+#pragma unroll
+            for (int q = 0; q < KS; ++q) kr[p][q] = __ldg(a.k + (fi * KS + p) * KS + q);
+        const float* cpl = a.cpl + ioff * (size_t)a.nfilt + (size_t)fi * a.img_stride +
+                           (col_in ? xcol : 0);
+        float ha[KS];
+#pragma unroll
+        for (int s = 0; s < KS; ++s) ha[s] = 0.0f;
+        // c rows of group g; the next group's loads are issued before the
+        // current group's arithmetic
+        auto load_group = [&](int g, float (&cv)[KS]) {
+#pragma unroll
+            for (int mm = 0; mm < KS; ++mm) {
+                const int m = g * KS + mm, r = hy0 - R + m;
+                cv[mm] = (col_in && (unsigned)r < (unsigned)H && m < nsteps)
+                             ? __ldcg(cpl + (size_t)r * a.pitch) : 0.0f;
+            }
+        };
+        float cv[KS];
+        load_group(0, cv);
+#pragma unroll 1
+        for (int g = 0; g < ngroups; ++g) {
+            float cn[KS];
+            load_group(g + 1, cn);
+            adj_group<KS>(cv, hrow, kr, ha, g * KS, 2 * R, nsteps, lane);
+#pragma unroll
+            for (int mm = 0; mm < KS; ++mm) cv[mm] = cn[mm];
+        }
+    }
     __syncthreads();
 
     // e_{t-1} = d + fold(sum over warps of h)
-    const float* sH0 = sW;
-    constexpr int WSTRIDE = C::H_FL + C::KW_FL + C::HIST_FL + C::TAB_FL;
+    const int wy0 = tile_split(ty, TH, H, a.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, a.tiles_y, R);
+    const int wx0 = tile_split(tx, TW, W, a.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, a.tiles_x, R);
     for (int idx = threadIdx.x; idx < TH * TW; idx += C::NTHREADS) {
         const int qy = y0 + idx / TW, qx = x0 + idx % TW;
         if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
@@ -245,39 +308,46 @@ bwd_bank(const BwdArgs a)
                 const int hi = sy[p] - (y0 - R), hj = sx[q] - (x0 - R);
                 float hs = 0.0f;
 #pragma unroll
-                for (int wq = 0; wq < C::NWARP; ++wq) hs += sH0[wq * WSTRIDE + hi * 32 + hj];
+                for (int wq = 0; wq < C::NWARP; ++wq) hs += smem[wq * C::H_FL + hi * 32 + hj];
                 g += hs;
             }
         }
-        const float dv = sD[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R)];
-        a.e_prev[ioff + (size_t)qy * a.pitch + qx] = dv + g;
+        const size_t o = ioff + (size_t)qy * a.pitch + qx;
+        a.e_prev[o] = a.d[o] + g;
     }
 }
 
-// grid (dk_tiles_x * dk_tiles_y, N), 4 warps.  Per warp and filter: lane =
-// pixel column, walk over the u/d rows of the tile plus R above and below,
-// with rolling windows of the 2R+1 c and v rows that meet each u/d row r:
-//   acc[a][b] += c(r - R + a) u(r, x + R - b) - v(r - R + a) d(r, x + R - b)
+// grid (dk_tiles_x * dk_tiles_y, N), 4 warps; tiles of 32 columns x TH rows
+// (TH + 2R a multiple of KS).  Per warp and filter: lane = pixel column, walk
+// over the u/d rows of the tile plus R above and below; step m takes u/d row
+// y0 - R + m and the 2R+1 c and v rows y0 + m - 2R + a (a = 0..2R) that meet it:
+//   acc[a][b] += c(y0 + m - 2R + a) u(y0 - R + m, x + R - b)
+//              - v(y0 + m - 2R + a) d(y0 - R + m, x + R - b)
 // (u, d symmetric-padded); rows and columns outside the tile or the image carry
-// c = v = 0, so every pixel's product is counted by exactly one tile.
-template <int KS, int NK>
-__global__ void __launch_bounds__(128) bwd_dk(const BwdArgs a)
+// c = v = 0, so every pixel's product is counted by exactly one tile.  The c
+// and v rows of a group of KS steps sit in registers (cur), with those of the
+// previous group (prev); the next group's loads are issued one group ahead.
+template <int KS, int NK, int TH>
+__global__ void __launch_bounds__(128) bwd_dk(const __grid_constant__ BwdArgs a)
 {
     constexpr int R = KS / 2;
     constexpr int NW = 4;
     constexpr int FPW = NK / NW;
     static_assert(NK % NW == 0, "");
-    constexpr int UHD = DK_TH + 2 * R, UWD = DK_TW + 2 * R;
-    __shared__ float sU[UHD * UWD];
-    __shared__ float sD[UHD * UWD];
+    constexpr int STEPS = TH + 2 * R;
+    static_assert(STEPS % KS == 0, "the walk must end on a whole group");
+    constexpr int NG = STEPS / KS;
+    constexpr int UWD = 32 + 2 * R;
+    __shared__ float sU[STEPS * UWD];
+    __shared__ float sD[STEPS * UWD];
     __shared__ float sRed[NW][KS * KS][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = blockIdx.y;
     const int ty = blockIdx.x / a.dk_tiles_x, tx = blockIdx.x - ty * a.dk_tiles_x;
-    const int y0 = ty * DK_TH, x0 = tx * DK_TW;
+    const int y0 = ty * TH, x0 = tx * 32;
     const int H = a.H, W = a.W;
     const size_t ioff = (size_t)n * a.img_stride;
-    for (int idx = threadIdx.x; idx < UHD * UWD; idx += 128) {
+    for (int idx = threadIdx.x; idx < STEPS * UWD; idx += 128) {
         const int i = idx / UWD, j = idx - i * UWD;
         const int yy = sym_idx(y0 - R + i, H), xx = sym_idx(x0 - R + j, W);
         const size_t o = ioff + (size_t)yy * a.pitch + xx;
@@ -287,51 +357,64 @@ __global__ void __launch_bounds__(128) bwd_dk(const BwdArgs a)
     __syncthreads();
     const int x = x0 + lane;
     const bool col_ok = x < W;
-    const int rows_here = min(DK_TH, H - y0);
+    const int rows_here = min(TH, H - y0);
     const int cta = n * (a.dk_tiles_x * a.dk_tiles_y) + blockIdx.x;
 #pragma unroll 1
     for (int fl = 0; fl < FPW; ++fl) {
         const int fi = warp * FPW + fl;
         const size_t plane = ioff * (size_t)a.nfilt + (size_t)fi * a.img_stride;
-        const float* cp = a.cpl + plane + (col_ok ? x : 0);
-        const float* vp = a.vpl + plane + (col_ok ? x : 0);
+        const float* cp = a.cpl + plane + (size_t)y0 * a.pitch + (col_ok ? x : 0);
+        const float* vp = a.vpl + plane + (size_t)y0 * a.pitch + (col_ok ? x : 0);
+        auto load_group = [&](int g, float (&cg)[KS], float (&vg)[KS]) {
+#pragma unroll
+            for (int mm = 0; mm < KS; ++mm) {
+                const int r = g * KS + mm;   // tile row
+                const bool ok = col_ok && r < rows_here;
+                cg[mm] = ok ? __ldcg(cp + (size_t)r * a.pitch) : 0.0f;
+                vg[mm] = ok ? __ldcg(vp + (size_t)r * a.pitch) : 0.0f;
+            }
+        };
         float acc[KS][KS];
 #pragma unroll
         for (int p = 0; p < KS; ++p)
 #pragma unroll
             for (int q = 0; q < KS; ++q) acc[p][q] = 0.0f;
-        // Step m handles u/d buffer row m (image row y0 - R + m).  The c/v rows
-        // that meet it are tile rows m - 2R + a, a = 0..2R: window slot a.
-        float cw[KS], vw[KS];
+        float cprev[KS], vprev[KS], ccur[KS], vcur[KS];
 #pragma unroll
-        for (int s = 0; s < KS; ++s) cw[s] = vw[s] = 0.0f;
+        for (int s = 0; s < KS; ++s) cprev[s] = vprev[s] = 0.0f;
+        load_group(0, ccur, vcur);
 #pragma unroll 1
-        for (int m = 0; m < DK_TH + 2 * R; ++m) {
+        for (int g = 0; g < NG; ++g) {
+            float cnext[KS], vnext[KS];
+            load_group(g + 1, cnext, vnext);
 #pragma unroll
-            for (int s = 0; s < KS - 1; ++s) {
-                cw[s] = cw[s + 1];
-                vw[s] = vw[s + 1];
+            for (int mm = 0; mm < KS; ++mm) {
+                const float* ur = sU + (g * KS + mm) * UWD + lane;
+                const float* dr = sD + (g * KS + mm) * UWD + lane;
+                float in[KS], dn[KS];
+#pragma unroll
+                for (int b = 0; b < KS; ++b) {
+                    in[b] = ur[2 * R - b];
+                    dn[b] = dr[2 * R - b];
+                }
+#pragma unroll
+                for (int p = 0; p < KS; ++p) {
+                    // c/v row m - 2R + p: slot mm - 2R + p of this group or the last
+                    const int sl = mm - 2 * R + p;
+                    const float cv = sl >= 0 ? ccur[sl] : cprev[sl + KS];
+                    const float vv = sl >= 0 ? vcur[sl] : vprev[sl + KS];
+#pragma unroll
+                    for (int q = 0; q < KS; ++q)
+                        acc[p][q] = fmaf(cv, in[q], fmaf(-vv, dn[q], acc[p][q]));
+                }
             }
-            float cn = 0.0f, vn = 0.0f;
-            if (col_ok && m < rows_here) {
-                cn = cp[(size_t)(y0 + m) * a.pitch];
-                vn = vp[(size_t)(y0 + m) * a.pitch];
+#pragma unroll
+            for (int s = 0; s < KS; ++s) {
+                cprev[s] = ccur[s];
+                vprev[s] = vcur[s];
+                ccur[s] = cnext[s];
+                vcur[s] = vnext[s];
             }
-            cw[KS - 1] = cn;
-            vw[KS - 1] = vn;
-            const float* ur = sU + m * UWD + lane;
-            const float* dr = sD + m * UWD + lane;
-            float in[KS], dn[KS];
-#pragma unroll
-            for (int b = 0; b < KS; ++b) {
-                in[b] = ur[2 * R - b];
-                dn[b] = dr[2 * R - b];
-            }
-#pragma unroll
-            for (int p = 0; p < KS; ++p)
-#pragma unroll
-                for (int q = 0; q < KS; ++q)
-                    acc[p][q] = fmaf(cw[p], in[q], fmaf(-vw[p], dn[q], acc[p][q]));
         }
         // reduce over the 32 lanes (columns) through shared memory
 #pragma unroll
@@ -350,15 +433,48 @@ __global__ void __launch_bounds__(128) bwd_dk(const BwdArgs a)
 }
 
 // Fixed-order sums of the per-tile partials into the gradients of one stage.
-// grid ceil(nparam / 256): thread e sums parameter e over all partial rows.
-__global__ void __launch_bounds__(256) bwd_reduce(const float* __restrict__ part, int nrows,
-                                                  int nparam, float* __restrict__ out)
+// grid (blocks, 3), 512 threads; blockIdx.y picks the partial set.  Sets of
+// 32 or more parameters: block x takes parameters 32x .. 32x + 31 (lane), and
+// warp w sums rows w, w + 16, ...; the 16 warp sums are then added in warp
+// order.  Smaller sets: block x takes parameter x, thread i sums rows i,
+// i + 512, ..., followed by a fixed pairwise tree.  Either way the order of
+// every addition is fixed by the launch shape alone.
+constexpr int RED_THREADS = 512;
+__global__ void __launch_bounds__(RED_THREADS) bwd_reduce(const __grid_constant__ RedArgs a)
 {
-    const int e = blockIdx.x * 256 + threadIdx.x;
-    if (e >= nparam) return;
-    float s = 0.0f;
-    for (int r = 0; r < nrows; ++r) s += part[(size_t)r * nparam + e];
-    out[e] = s;
+    const RedSet g = a.s[blockIdx.y];
+    __shared__ float red[RED_THREADS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NWR = RED_THREADS / 32;
+    if (g.nparam >= 32) {
+        const int e = blockIdx.x * 32 + lane;
+        if (blockIdx.x * 32 >= g.nparam) return;
+        float s = 0.0f;
+        if (e < g.nparam) {
+#pragma unroll 4
+            for (int r = warp; r < g.nrows; r += NWR) s += g.part[(size_t)r * g.nparam + e];
+        }
+        red[warp * 32 + lane] = s;
+        __syncthreads();
+        if (warp == 0 && e < g.nparam) {
+            float t = 0.0f;
+#pragma unroll
+            for (int w = 0; w < NWR; ++w) t += red[w * 32 + lane];
+            g.out[e] = t;
+        }
+    } else {
+        const int e = blockIdx.x;
+        if (e >= g.nparam) return;
+        float s = 0.0f;
+#pragma unroll 4
+        for (int r = tid; r < g.nrows; r += RED_THREADS) s += g.part[(size_t)r * g.nparam + e];
+        red[tid] = s;
+        for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+            __syncthreads();
+            if (tid < w) red[tid] += red[tid + w];
+        }
+        if (tid == 0) g.out[e] = red[0];
+    }
 }
 
 }  // namespace tnrd

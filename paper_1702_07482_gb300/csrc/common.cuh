@@ -187,6 +187,27 @@ __device__ __forceinline__ float rbf_phi_w(float z, const float* __restrict__ wp
     return w.pre * p;
 }
 
+// phi(z) and phi'(z) straight from the padded weights wp, as rbf_phi_dphi_tab
+// with the window coefficients w_j E[|m|] formed on the fly.
+__device__ __forceinline__ void rbf_phi_dphi_w(float z, const float* __restrict__ wp,
+                                               const RbfConst& rc, float& phi, float& dphi,
+                                               RbfWin2& win)
+{
+    win = rbf_win2(z, rc);
+    const float* wr = wp + win.row;
+    float p = wr[2 * RBF_WIN] * rc.E[RBF_WIN];
+    float dp = 0.0f;
+#pragma unroll
+    for (int n = 2 * RBF_WIN - 1; n >= 0; --n) {
+        const int m = n - RBF_WIN;
+        dp = fmaf(dp, win.q, p);
+        p = fmaf(p, win.q, wr[n] * rc.E[m < 0 ? -m : m]);
+    }
+    phi = win.pre * p;
+    const float m1 = win.pre * fmaf(-(float)RBF_WIN, p, win.q * dp);
+    dphi = -rc.inv_g2 * fmaf(win.s, phi, -rc.delta * m1);
+}
+
 // phi(z) from a coefficient table.
 __device__ __forceinline__ float rbf_phi_tab(float z, const float* __restrict__ tab,
                                              const RbfConst& rc)

@@ -39,10 +39,10 @@ cudaError_t tc_take_error(int* out);
 cudaError_t launch_batch_fwd(int ks, int nk, int th, const BatchArgs& a, int grid, cudaStream_t s);
 int batch_fwd_occupancy(int ks, int nk, int th, int nrbf);
 
-// Backward: tile height of bwd_bank (tiles are TH x (32 - 2R)), one stage's
-// prep + bank + filter-gradient launches, and the fixed-order partial reduce.
+// Backward: tile height of bwd_zb / bwd_adj, one stage's prep + zb + adj +
+// filter-gradient launches, and the fixed-order partial reduce (three sets).
 int bwd_tile_h(int ks);
 cudaError_t launch_bwd_stage(int ks, int nk, const BwdArgs& a, int N, cudaStream_t s);
-cudaError_t launch_bwd_reduce(const float* part, int nrows, int nparam, float* out, cudaStream_t s);
+cudaError_t launch_bwd_reduce(const RedArgs& r, cudaStream_t s);
 
 }  // namespace tnrd
