@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -140,6 +141,62 @@ int pick_fused_th(int ks, int nk, int N, int H, int W)
     return best_th;
 }
 
+// Fused forward kernel choice.  The one-column-per-lane kernel
+// (fused_stage_fwd) is the default.  When it cannot give every SM two CTAs
+// (a single small image), the column-pair kernel on two-CTA clusters
+// (fused_pair2_fwd, half of the filters per CTA) spreads the same work over
+// more CTAs; its tile height minimises (CTAs per SM, rounded up) x (walk
+// steps x filters per CTA).  TNRD_FUSED_KERNEL=lane|pair|pair2 and
+// TNRD_FUSED_TH override the choice (tuning and measurement).
+struct FusedChoice {
+    int pair = 0;     // 0: one column per lane; 1: column pairs
+    int th = 0;
+    int nsplit = 1;
+    int tw = 0;
+};
+
+FusedChoice pick_fused(int ks, int nk, int N, int H, int W)
+{
+    FusedChoice c;
+    int force = -1;   // -1 auto, 0 lane, 1 pair, 2 pair2
+    if (const char* env = std::getenv("TNRD_FUSED_KERNEL")) {
+        if (!std::strcmp(env, "lane")) force = 0;
+        else if (!std::strcmp(env, "pair")) force = 1;
+        else if (!std::strcmp(env, "pair2")) force = 2;
+    }
+    const int R = ks / 2;
+    int nsm = 148;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    c.th = pick_fused_th(ks, nk, N, H, W);
+    c.tw = 32 - 2 * R;
+    const long long lane_ctas = (long long)N * ((H + c.th - 1) / c.th) * ((W + c.tw - 1) / c.tw);
+    if (force == 0 || (force < 0 && lane_ctas >= 2LL * nsm)) return c;
+    const int ns = (force == 1) ? 1 : 2;
+    const int* list = tnrd::pair_th_list(ks);
+    int want_th = 0;
+    if (const char* env = std::getenv("TNRD_FUSED_TH")) want_th = std::atoi(env);
+    const int tw = 64 - 2 * R;
+    double best = 1e300;
+    c.pair = 1;
+    c.nsplit = ns;
+    c.tw = tw;
+    c.th = list[0];
+    for (const int* p = list; *p; ++p) {
+        const int th = *p;
+        if (want_th && th != want_th) continue;
+        const long long tiles = (long long)N * ((H + th - 1) / th) * ((W + tw - 1) / tw);
+        const long long per_sm = (tiles * ns + nsm - 1) / nsm;
+        const double cost = per_sm * (double)(th + 4 * R);
+        if (cost < best * 0.999) {
+            best = cost;
+            c.th = th;
+        }
+    }
+    return c;
+}
+
 struct FwdLayout {
     size_t pingpong = 0;   // offset of the ping-pong image batch
     size_t v = 0, g = 0;   // unfused response planes and adjoint plane
@@ -255,7 +312,7 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
     }
     const tnrd::RbfConst rc = make_rbf(p);
     const int ks = p->ksize, nk = p->nfilt;
-    const int th = (algo == TNRD_ALGO_FUSED) ? pick_fused_th(ks, nk, N, H, W) : 0;
+    const FusedChoice fc = (algo == TNRD_ALGO_FUSED) ? pick_fused(ks, nk, N, H, W) : FusedChoice{};
     int tc_nb = 2;
     if (const char* env = std::getenv("TNRD_TC_NB")) {   // tuning override
         const int v = std::atoi(env);
@@ -287,14 +344,15 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.H = H;
             a.W = W;
             a.pitch = pitch;
-            a.tiles_x = (W + (32 - 2 * (ks / 2)) - 1) / (32 - 2 * (ks / 2));
-            a.tiles_y = (H + th - 1) / th;
+            a.tiles_x = (W + fc.tw - 1) / fc.tw;
+            a.tiles_y = (H + fc.th - 1) / fc.th;
             a.k = kt;
             a.w = wt;
             a.lam = p->lambda + t;
             a.nrbf = p->nrbf;
             a.rc = rc;
-            e = tnrd::launch_fused_fwd(ks, nk, th, a, N, stream);
+            e = fc.pair ? tnrd::launch_pair_fwd(ks, nk, fc.th, fc.nsplit, a, N, stream)
+                        : tnrd::launch_fused_fwd(ks, nk, fc.th, a, N, stream);
         } else if (algo == TNRD_ALGO_TC_TF32) {
             tnrd::StageArgs a{};
             const int tw = 32 - 2 * (ks / 2), tth = tnrd::tc_tile_h(ks, tc_nb);

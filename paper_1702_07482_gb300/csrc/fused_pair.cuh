@@ -1,0 +1,319 @@
+// Fused FP32 forward stage of TRDMD (Eq. diffusionprocessfinal), column-pair
+// variant: u_t = prox(u_{t-1} - sum_i K_i^T phi_i(K_i u_{t-1})) in one kernel
+// per stage, with the filter responses kept in registers and only u_t
+// written to HBM (as fused_stage_fwd).
+//
+// Lane j owns the two z-columns c0 = x0 - R + 2j and c1 = c0 + 1, so a warp
+// covers 64 z-columns and the tile TW = 64 - 2R output columns.  Against one
+// column per lane this
+//   * reads the 2R + 2 u values of both columns as R + 1 float2 loads,
+//   * gathers the 2R + 2 neighbouring v values with 2R shuffles,
+//   * accumulates h as float2 rows,
+//   * and spends 2R of every 64 z-columns on the halo instead of 2R of 32.
+// Each warp walks down its columns once per filter (rolling z and h
+// accumulators as in fused_stage_fwd) and keeps h in a private buffer; the
+// epilogue sums the buffers, folds the border (exact transpose of the
+// symmetric-padded convolution) and applies the prox.
+//
+// NSPLIT = 2 runs one tile on a cluster of two CTAs, each with half of the
+// filters; the epilogue of each CTA covers half of the tile and adds the
+// other CTA's h buffers through distributed shared memory.  This doubles the
+// CTAs of small images (one 512 x 512 image is ~150 tiles for 152 SMs).
+#pragma once
+#include <cooperative_groups.h>
+#include "args.cuh"
+#include "fused_fwd.cuh"   // shfl_rel
+
+namespace tnrd {
+
+__host__ __device__ constexpr int pair_nwarp(int nk_cta)
+{
+    return nk_cta % 8 == 0 ? 8 : nk_cta % 6 == 0 ? 6 : nk_cta % 4 == 0 ? 4 : nk_cta % 2 == 0 ? 2 : 1;
+}
+
+template <int KS, int NK, int TH, int NSPLIT>
+struct PairCfg {
+    static constexpr int R = KS / 2;
+    static constexpr int TW = 64 - 2 * R;          // output columns per tile
+    static constexpr int NK_CTA = NK / NSPLIT;
+    static_assert(NK % NSPLIT == 0, "filters must split evenly over the cluster");
+    static constexpr int NWARP = pair_nwarp(NK_CTA);
+    static constexpr int NTHREADS = NWARP * 32;
+    static constexpr int FPW = NK_CTA / NWARP;
+    static constexpr int GROUPS_EXT = (TH + 6 * R + KS - 1) / KS;
+    static constexpr int GROUPS_INT = (TH + 4 * R + KS - 1) / KS;
+    static constexpr int UH_EXT = GROUPS_EXT * KS;
+    static constexpr int UH_INT = R + GROUPS_INT * KS;
+    static constexpr int UH = UH_EXT > UH_INT ? UH_EXT : UH_INT;   // u rows from y0 - 3R
+    static constexpr int UW = 64 + 2 * R;          // u cols from x0 - 2R
+    static constexpr int UP = (UW + 1) & ~1;       // even pitch: float2 row reads
+    static constexpr int U_FL = UH * UP;
+    static constexpr int H_FL = (TH + 2 * R) * 64; // h rows from y0 - R, two columns per lane
+    static constexpr int KPAD = (KS * KS + 3) & ~3;
+    static constexpr int WPADN = (MAX_NRBF + 2 * RBF_WPAD + 3) & ~3;
+    static constexpr int PW_FL = H_FL + KPAD + WPADN;
+    static constexpr int SMEM_FL = ((U_FL + 3) & ~3) + NWARP * PW_FL;
+    static constexpr size_t SMEM_BYTES = sizeof(float) * (size_t)SMEM_FL;
+};
+
+// vw[t] = v at column c0 - R + t (t = 0 .. 2R+1) from the (v0, v1) pairs of
+// lanes j + floor((t - R) / 2).
+template <int KS, int T, bool EDGE>
+__device__ __forceinline__ void gather_pair(float (&vw)[KS + 1], float v0, float v1, int lane)
+{
+    if constexpr (T < KS + 1) {
+        constexpr int R = KS / 2;
+        constexpr int d = T - R;
+        constexpr int D = d >= 0 ? d / 2 : -((1 - d) / 2);
+        constexpr int E = d - 2 * D;
+        vw[T] = shfl_rel<D, EDGE>(E ? v1 : v0, lane);
+        gather_pair<KS, T + 1, EDGE>(vw, v0, v1, lane);
+    }
+}
+
+// One group of KS walk steps (see walk_group of fused_stage_fwd for the
+// row bookkeeping); urow points at this lane's first u column (2j) of the
+// step-0 row, hrow at its float2 of the h row completed at step 0.
+template <int KS, int UP, bool INTERIOR>
+__device__ __forceinline__ void pair_group(const float* __restrict__ urow, float2* __restrict__ hrow,
+                                           const float (&kr)[KS][KS], float (&za0)[KS],
+                                           float (&za1)[KS], float (&ha0)[KS], float (&ha1)[KS],
+                                           int m0, int zrow0, int H, bool col_in0, bool col_in1,
+                                           int mz_lo, int mh_lo, int mh_hi, int lane,
+                                           const float* __restrict__ wp, const RbfConst& rc)
+{
+    constexpr int R = KS / 2;
+#pragma unroll
+    for (int mm = 0; mm < KS; ++mm) {
+        const int m = m0 + mm;
+        const float2* row = reinterpret_cast<const float2*>(urow + m * UP);
+        float in[2 * R + 2];   // in[t] = u(row, c0 - R + t)
+#pragma unroll
+        for (int t2 = 0; t2 <= R; ++t2) {
+            const float2 p = row[t2];
+            in[2 * t2] = p.x;
+            in[2 * t2 + 1] = p.y;
+        }
+        // z(c) = sum_{a,b} k[a][b] u(i + R - a, c + R - b): the row feeds slots (step + a) mod KS
+#pragma unroll
+        for (int b = 0; b < KS; ++b) {
+#pragma unroll
+            for (int a = 0; a < KS; ++a) {
+                const int s = (mm + a) % KS;
+                za0[s] = fmaf(kr[a][b], in[2 * R - b], za0[s]);
+                za1[s] = fmaf(kr[a][b], in[2 * R + 1 - b], za1[s]);
+            }
+        }
+        const float z0 = za0[mm], z1 = za1[mm];
+        za0[mm] = 0.0f;
+        za1[mm] = 0.0f;
+        float v0 = rbf_phi_w(z0, wp, rc);
+        float v1 = rbf_phi_w(z1, wp, rc);
+        if constexpr (!INTERIOR) {
+            const int zi = zrow0 + m;
+            const bool row_ok = (m >= mz_lo) && ((unsigned)zi < (unsigned)H);
+            v0 = (row_ok && col_in0) ? v0 : 0.0f;
+            v1 = (row_ok && col_in1) ? v1 : 0.0f;
+        }
+        float vw[KS + 1];
+        gather_pair<KS, 0, !INTERIOR>(vw, v0, v1, lane);
+        // h(c) = sum_{a,b} k[a][b] v(i - R + a, c - R + b): slots (step - a) mod KS
+#pragma unroll
+        for (int b = 0; b < KS; ++b) {
+#pragma unroll
+            for (int a = 0; a < KS; ++a) {
+                const int s = (mm - a + 2 * KS) % KS;
+                ha0[s] = fmaf(kr[a][b], vw[b], ha0[s]);
+                ha1[s] = fmaf(kr[a][b], vw[b + 1], ha1[s]);
+            }
+        }
+        const int sf = (mm - 2 * R + 2 * KS) % KS;
+        if (m >= mh_lo && m < mh_hi) {
+            float2 h = hrow[m * 32];
+            h.x += ha0[sf];
+            h.y += ha1[sf];
+            hrow[m * 32] = h;
+        }
+        ha0[sf] = 0.0f;
+        ha1[sf] = 0.0f;
+    }
+}
+
+// One stage on one tile.  rank selects the CTA's half of the filters and of
+// the epilogue when NSPLIT = 2 (the two CTAs of a cluster share the tile);
+// remote_h is then the other CTA's h buffers (distributed shared memory).
+// Loads of u_{t-1} go through L2 (ld.global.cg).
+template <int KS, int NK, int TH, int NSPLIT>
+__device__ __forceinline__ void pair_tile_walk(const TileJob& j, float* smem, int rank)
+{
+    using C = PairCfg<KS, NK, TH, NSPLIT>;
+    constexpr int R = C::R;
+    constexpr int TW = C::TW;
+    float* sU = smem;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* myH = smem + ((C::U_FL + 3) & ~3) + warp * C::PW_FL;
+    float* myK = myH + C::H_FL;
+    float* myW = myK + C::KPAD;
+    const int ty = j.ty, tx = j.tx;
+    const int H = j.H, W = j.W;
+    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
+    const bool ext = (ty == 0) || (ty == j.tiles_y - 1);
+    const bool border = ext || (tx == 0) || (tx == j.tiles_x - 1);
+    const RbfConst& rc = *j.rc;
+
+    for (int idx = threadIdx.x; idx < C::UH * C::UW; idx += C::NTHREADS) {
+        const int i = idx / C::UW, jj = idx - i * C::UW;
+        const int yy = sym_idx(y0 - 3 * R + i, H), xx = sym_idx(x0 - 2 * R + jj, W);
+        sU[i * C::UP + jj] = __ldcg(j.u_in + (size_t)yy * j.pitch + xx);
+    }
+    for (int e = lane; e < C::H_FL; e += 32) myH[e] = 0.0f;
+    for (int e = lane; e < C::WPADN; e += 32) myW[e] = 0.0f;
+    __syncthreads();
+
+    const int hy0 = ext ? y0 - R : y0;
+    const int nh = ext ? TH + 2 * R : TH;
+    const int nsteps = nh + 4 * R;
+    const int ub0 = ext ? 0 : R;
+    const float* urow = sU + ub0 * C::UP + 2 * lane;
+    float2* hrow = reinterpret_cast<float2*>(myH) + (hy0 - 4 * R - (y0 - R)) * 32 + lane;
+    const int zrow0 = hy0 - 3 * R;
+    const int c0 = x0 - R + 2 * lane;
+    const bool col_in0 = (unsigned)c0 < (unsigned)W;
+    const bool col_in1 = (unsigned)(c0 + 1) < (unsigned)W;
+
+#pragma unroll 1
+    for (int fl = 0; fl < C::FPW; ++fl) {
+        const int fi = rank * C::NK_CTA + warp * C::FPW + fl;
+        for (int e = lane; e < KS * KS; e += 32) myK[e] = __ldg(j.k + fi * KS * KS + e);
+        for (int e = lane; e < j.nrbf; e += 32) myW[RBF_WPAD + e] = __ldg(j.w + fi * j.nrbf + e);
+        __syncwarp();
+        float kr[KS][KS];
+#pragma unroll
+        for (int p = 0; p < KS; ++p)
+#pragma unroll
+            for (int q = 0; q < KS; ++q) kr[p][q] = myK[p * KS + q];
+        float za0[KS], za1[KS], ha0[KS], ha1[KS];
+#pragma unroll
+        for (int s = 0; s < KS; ++s) za0[s] = za1[s] = ha0[s] = ha1[s] = 0.0f;
+        if (!border) {
+#pragma unroll 1
+            for (int m0 = 0; m0 < nsteps; m0 += KS)
+                pair_group<KS, C::UP, true>(urow, hrow, kr, za0, za1, ha0, ha1, m0, zrow0, H,
+                                            col_in0, col_in1, 2 * R, 4 * R, nsteps, lane, myW, rc);
+        } else {
+#pragma unroll 1
+            for (int m0 = 0; m0 < nsteps; m0 += KS)
+                pair_group<KS, C::UP, false>(urow, hrow, kr, za0, za1, ha0, ha1, m0, zrow0, H,
+                                             col_in0, col_in1, 2 * R, 4 * R, nsteps, lane, myW, rc);
+        }
+        __syncwarp();
+    }
+}
+
+// Epilogue over the tile's own pixels idx = first, first + step, ...:
+// g = fold(sum of the h buffers), u_t = prox(u_{t-1} - g).
+template <int KS, int NK, int TH, int NSPLIT>
+__device__ __forceinline__ void pair_tile_epilogue(const TileJob& j, const float* smem,
+                                                   const float* remote, int first, int step)
+{
+    using C = PairCfg<KS, NK, TH, NSPLIT>;
+    constexpr int R = C::R;
+    constexpr int TW = C::TW;
+    const float* sU = smem;
+    const float* sH = smem + ((C::U_FL + 3) & ~3);
+    const int ty = j.ty, tx = j.tx;
+    const int H = j.H, W = j.W;
+    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
+    const bool ext = (ty == 0) || (ty == j.tiles_y - 1);
+    const bool border = ext || (tx == 0) || (tx == j.tiles_x - 1);
+    const float lam = __ldg(j.lam);
+    const int wy0 = tile_split(ty, TH, H, j.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, j.tiles_y, R);
+    const int wx0 = tile_split(tx, TW, W, j.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, j.tiles_x, R);
+    for (int idx = first; idx < TH * TW; idx += step) {
+        const int qy = y0 + idx / TW, qx = x0 + idx % TW;
+        if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
+        int sy[2], sx[2];
+        int nsy = 1, nsx = 1;
+        sy[0] = qy;
+        sx[0] = qx;
+        if (border) {
+            if (qy < R) sy[nsy++] = -1 - qy;
+            else if (qy >= H - R) sy[nsy++] = 2 * H - 1 - qy;
+            if (qx < R) sx[nsx++] = -1 - qx;
+            else if (qx >= W - R) sx[nsx++] = 2 * W - 1 - qx;
+        }
+        float g = 0.0f;
+        for (int p = 0; p < nsy; ++p) {
+            for (int q = 0; q < nsx; ++q) {
+                const int o = (sy[p] - (y0 - R)) * 64 + sx[q] - (x0 - R);
+                float hs = 0.0f;
+#pragma unroll
+                for (int wq = 0; wq < C::NWARP; ++wq) hs += sH[wq * C::PW_FL + o];
+                if constexpr (NSPLIT == 2) {
+#pragma unroll
+                    for (int wq = 0; wq < C::NWARP; ++wq) hs += remote[wq * C::PW_FL + o];
+                }
+                g += hs;
+            }
+        }
+        const float up = sU[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R)];
+        const float fv = __ldg(j.f + (size_t)qy * j.pitch + qx);
+        j.u_out[(size_t)qy * j.pitch + qx] = prox_idiv(up - g, fv, lam);
+    }
+}
+
+__device__ __forceinline__ TileJob pair_job(const StageArgs& a, int tile)
+{
+    const int n = blockIdx.y;
+    TileJob j;
+    j.u_in = a.u_in + (size_t)n * a.img_stride;
+    j.u_out = a.u_out + (size_t)n * a.img_stride;
+    j.f = a.f + (size_t)n * a.img_stride;
+    j.H = a.H;
+    j.W = a.W;
+    j.pitch = a.pitch;
+    j.tiles_x = a.tiles_x;
+    j.tiles_y = a.tiles_y;
+    j.ty = tile / a.tiles_x;
+    j.tx = tile - j.ty * a.tiles_x;
+    j.k = a.k;
+    j.w = a.w;
+    j.lam = a.lam;
+    j.nrbf = a.nrbf;
+    j.rc = &a.rc;
+    return j;
+}
+
+// One CTA per tile; grid (tiles_x * tiles_y, N).
+template <int KS, int NK, int TH>
+__global__ void __launch_bounds__(PairCfg<KS, NK, TH, 1>::NTHREADS, 2)
+fused_pair_fwd(const __grid_constant__ StageArgs a)
+{
+    extern __shared__ __align__(16) float smem[];
+    const TileJob j = pair_job(a, blockIdx.x);
+    pair_tile_walk<KS, NK, TH, 1>(j, smem, 0);
+    __syncthreads();
+    pair_tile_epilogue<KS, NK, TH, 1>(j, smem, nullptr, threadIdx.x,
+                                      PairCfg<KS, NK, TH, 1>::NTHREADS);
+}
+
+// A cluster of two CTAs per tile; grid (2 * tiles_x * tiles_y, N).
+template <int KS, int NK, int TH>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairCfg<KS, NK, TH, 2>::NTHREADS, 2)
+fused_pair2_fwd(const __grid_constant__ StageArgs a)
+{
+    namespace cg = cooperative_groups;
+    using C = PairCfg<KS, NK, TH, 2>;
+    extern __shared__ __align__(16) float smem[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const TileJob j = pair_job(a, blockIdx.x >> 1);
+    pair_tile_walk<KS, NK, TH, 2>(j, smem, rank);
+    cl.sync();   // both CTAs' h buffers complete and visible in the cluster
+    const float* remote = cl.map_shared_rank(smem, rank ^ 1) + ((C::U_FL + 3) & ~3);
+    pair_tile_epilogue<KS, NK, TH, 2>(j, smem, remote, rank * C::NTHREADS + threadIdx.x,
+                                      2 * C::NTHREADS);
+    cl.sync();   // keep this CTA's shared memory alive until the other has read it
+}
+
+}  // namespace tnrd

@@ -35,6 +35,12 @@ int tc_tile_h(int ks, int nb);
 cudaError_t launch_tc_fwd(int ks, int nk, int nb, const StageArgs& a, int N, cudaStream_t s);
 cudaError_t tc_take_error(int* out);
 
+// Column-pair fused forward (two z-columns per lane, TW = 64 - 2R); nsplit 2
+// runs each tile on a cluster of two CTAs with half of the filters each.
+const int* pair_th_list(int ks);
+cudaError_t launch_pair_fwd(int ks, int nk, int th, int nsplit, const StageArgs& a, int N,
+                            cudaStream_t s);
+
 // Persistent batched forward.
 cudaError_t launch_batch_fwd(int ks, int nk, int th, const BatchArgs& a, int grid, cudaStream_t s);
 int batch_fwd_occupancy(int ks, int nk, int th, int nrbf);

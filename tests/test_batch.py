@@ -52,7 +52,9 @@ def test_batch_matches_per_image_forward_bit_for_bit():
     plan.forward(stream)
     torch.cuda.synchronize()
     assert plan.status() == 0
+    # the persistent kernel walks tiles of the one-column-per-lane fused kernel
     os.environ["TNRD_FUSED_TH"] = str(plan.tile_height)
+    os.environ["TNRD_FUSED_KERNEL"] = "lane"
     try:
         for (H, W, L, s), ft, ut in zip(SIZES, fts, uts):
             ref = ops.forward(models[s], ft.unsqueeze(0), W=W)[0]
@@ -60,6 +62,7 @@ def test_batch_matches_per_image_forward_bit_for_bit():
             assert torch.equal(ut[:, :W], ref[:, :W])
     finally:
         del os.environ["TNRD_FUSED_TH"]
+        del os.environ["TNRD_FUSED_KERNEL"]
 
 
 def test_batch_matches_oracle_and_replays():
