@@ -9,14 +9,15 @@ collective on the data path): weak scaling.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload fwd512|fwd512_unfused|small128|batched|train|
-                              mixed_tf32|mixed_fp32]
+                              mixed_tf32|mixed_bf16|mixed_fp32]
 
 The other workloads (one GPU) measure the rest of the table with the same
 contract: fwd512_unfused (three kernels per stage), small128 (1 x 128^2,
 5x5x24), batched (64 images of 256-1024 px per side, four parameter sets, one
 persistent launch per step), train (32 x 180^2 crops, forward + backward),
-mixed_tf32 / mixed_fp32 (16 x 2048^2, L = 2, T = 8, tensor-core TF32 vs plain
-FP32; the line adds the path's error against the FP64 oracle).
+mixed_tf32 / mixed_bf16 / mixed_fp32 (16 x 2048^2, L = 2, T = 8, tensor-core
+TF32 and BF16 vs plain FP32; the line adds the path's error against the FP64
+oracle).
 
 Prints ONE JSON line (rank 0).  `value` is Mpixel/s over all ranks with the
 inputs resident in HBM (L2 flushed between steps by a 256 MiB write, outside
@@ -418,7 +419,8 @@ class Mixed(Workload):
         from paper_1702_07482_gb300 import binding as B
         from paper_1702_07482_gb300 import ops
         self.T, self.n, self.S, self.algo = T_, n, S, algo
-        self.dtype = "tf32 operands, f32 accumulate" if algo == "tf32" else "f32"
+        self.dtype = {"tf32": "tf32 operands, f32 accumulate",
+                      "bf16": "bf16 operands, f32 accumulate"}.get(algo, "f32")
         self.p = _p32(synth.params(T_, KS, NK, seed=synth.seed_for(cfg, 0, "params")))
         self.m = ops.Model.create(self.p.filters, self.p.rbf_w, self.p.lam, device=dev)
         self.prm = self.m.params()
@@ -440,11 +442,17 @@ class Mixed(Workload):
         self.launches = T_
         self.flops = float(self.px) * T_ * FLOPS_PER_PX_STAGE
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE
-        self.kernel = ("tc_stage_fwd<7,48,2> (tcgen05 TF32 filter bank and adjoint, FP32 phi/prox)"
-                       if algo == "tf32" else "fused_stage_fwd<7,48,TH> (FP32)")
+        self.kernel = {"tf32": "tc_stage_fwd<7,48,2,tf32> (tcgen05 TF32 filter bank and adjoint, "
+                               "FP32 phi/prox)",
+                       "bf16": "tc_stage_fwd<7,48,2,bf16> (tcgen05 BF16 filter bank and adjoint, "
+                               "FP32 phi/prox)"}.get(algo, "fused_stage_fwd<7,48,TH> (FP32)")
+        prec = {"tf32": "filter bank and adjoint on tensor cores (TF32 operands, FP32 accumulate), "
+                        "phi and prox FP32",
+                "bf16": "filter bank and adjoint on tensor cores (BF16 operands, FP32 accumulate), "
+                        "phi and prox FP32"}.get(algo, "plain FP32 fused stage kernel")
         self.h2d = self.d2h = int(self.f_host.numel() * 4)
         self.config = {"workload": f"TRDMD forward, {n} x {S}x{S}, L=2, 7x7x48, 63 RBF, T={T_}, "
-                                   f"{'filter bank and adjoint on tensor cores (TF32 operands, FP32 accumulate), phi and prox FP32' if algo == 'tf32' else 'plain FP32 fused stage kernel'}",
+                                   f"{prec}",
                        "images": n, "H": S, "W": S, "ksize": KS, "nfilt": NK, "nrbf": 63, "T": T_,
                        "looks": 2, "precision": algo,
                        "l2": f"inputs ({self.h2d / 2 ** 20:.0f} MiB) larger than L2"}
@@ -508,6 +516,8 @@ def make_workload(name, dev):
         return Train(dev)
     if name == "mixed_tf32":
         return Mixed(dev, algo="tf32")
+    if name == "mixed_bf16":
+        return Mixed(dev, algo="bf16")
     if name == "mixed_fp32":
         return Mixed(dev, algo="fp32")
     raise ValueError(name)
@@ -659,7 +669,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fwd512",
                     choices=["fwd512", "fwd512_unfused", "small128", "batched", "train",
-                             "mixed_tf32", "mixed_fp32"])
+                             "mixed_tf32", "mixed_bf16", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -60,7 +60,9 @@ typedef enum {
  * accumulation, phi and the prox in FP32.  TNRD_ALGO_TC_TF32: the filter bank
  * and the adjoint run as tcgen05 implicit GEMMs with TF32 operands (u, the
  * filters and phi's outputs rounded to TF32, 10-bit mantissa); its error
- * against the FP64 result is larger than the FP32 paths' (see the tests). */
+ * against the FP64 result is larger than the FP32 paths' (see the tests).
+ * TNRD_ALGO_TC_BF16: the same GEMMs with BF16 operands (8-bit mantissa, round
+ * to nearest even) and FP32 accumulation; error larger again. */
 typedef enum {
     TNRD_ALGO_FUSED = 0,      /* one kernel per stage, responses kept on chip      */
     TNRD_ALGO_UNFUSED = 1,    /* three kernels per stage, N_k response planes in HBM */

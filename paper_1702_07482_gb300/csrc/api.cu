@@ -289,7 +289,8 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
     if (st != TNRD_OK) return st;
     st = check_images(N, H, W, pitch, p->ksize);
     if (st != TNRD_OK) return st;
-    if (algo != TNRD_ALGO_FUSED && algo != TNRD_ALGO_UNFUSED && algo != TNRD_ALGO_TC_TF32)
+    if (algo != TNRD_ALGO_FUSED && algo != TNRD_ALGO_UNFUSED && algo != TNRD_ALGO_TC_TF32 &&
+        algo != TNRD_ALGO_TC_BF16)
         return fail(TNRD_ERR_UNSUPPORTED, "algo %d not available in tnrd_forward", (int)algo);
     if (N == 0) return TNRD_OK;
     if (!f || !u) return fail(TNRD_ERR_INVALID_ARG, "null image pointer");
@@ -353,7 +354,7 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.rc = rc;
             e = fc.pair ? tnrd::launch_pair_fwd(ks, nk, fc.th, fc.nsplit, a, N, stream)
                         : tnrd::launch_fused_fwd(ks, nk, fc.th, a, N, stream);
-        } else if (algo == TNRD_ALGO_TC_TF32) {
+        } else if (algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16) {
             tnrd::StageArgs a{};
             const int tw = 32 - 2 * (ks / 2), tth = tnrd::tc_tile_h(ks, tc_nb);
             a.u_in = in;
@@ -370,7 +371,7 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.lam = p->lambda + t;
             a.nrbf = p->nrbf;
             a.rc = rc;
-            e = tnrd::launch_tc_fwd(ks, nk, tc_nb, a, N, stream);
+            e = tnrd::launch_tc_fwd(ks, nk, tc_nb, algo == TNRD_ALGO_TC_BF16, a, N, stream);
         } else {
             tnrd::UnfArgs a{};
             a.u_in = in;

@@ -225,28 +225,37 @@ struct BatchArgs {
 // Tensor-core stage (TNRD_ALGO_TC_TF32): filter bank and adjoint as implicit
 // GEMMs on tcgen05, phi and the prox on the CUDA cores.
 // ---------------------------------------------------------------------------
-template <int KS, int NK, int NB>
+template <int KS, int NK, int NB, bool BF>
 struct TcCfg {
     static constexpr int R = KS / 2;
     static constexpr int TW = 32 - 2 * R;        // output columns per tile
     static constexpr int ZR = 16 * NB;           // z rows per tile (NB blocks of 16)
     static constexpr int TH = ZR - 2 * R;        // output rows per tile
-    static constexpr int NPAD = (NK + 15) / 16 * 16;   // N of the filter-bank GEMM
-    static constexpr int NKP = (NK + 7) / 8 * 8;       // K of the adjoint GEMM
+    static constexpr int ESZ = BF ? 2 : 4;       // bytes per operand element
+    static constexpr int KMMA = BF ? 16 : 8;     // K of one MMA (32 bytes)
+    static constexpr int KCORE = BF ? 8 : 4;     // K elements of one core matrix row (16 bytes)
+    static constexpr int NPAD = (NK + 15) / 16 * 16;                 // N of the filter-bank GEMM
+    static constexpr int NKP = (NK + KMMA - 1) / KMMA * KMMA;        // K of the adjoint GEMM
     static constexpr int NT = (KS * KS + 15) / 16 * 16;  // N of the adjoint GEMM (taps)
     static_assert(NPAD <= 64 && NT <= 64, "TMEM columns: z at 0, Y at 64");
     static constexpr int UROWS = ZR + 2 * R;     // u rows from y0 - 2R
-    static constexpr int UPITCH = 36;            // floats per u row of a residue copy
+    // u operand row of one residue class r, in bytes:
+    //  TF32: a copy shifted by r columns, 36 floats (A core row m = floats 4m..4m+3);
+    //  BF16: 10 chunks of 8 values, chunk c = u columns 4c + r .. 4c + r + 7
+    //        (A core row m = chunk m; the second K core, taps 8..15, is chunk m + 2)
+    static constexpr int UPITCH = 36;            // TF32 floats per row
+    static constexpr int UCHUNKS = 10;           // BF16 chunks per row
+    static constexpr int UROWB = BF ? UCHUNKS * 16 : UPITCH * 4;
     static constexpr int HROWS = ZR + 2 * R;     // h rows from y0 - 2R
     static constexpr int HPITCH = 41;            // h columns from x0 - 2R (41 = 1 mod 4: no bank conflicts)
     static constexpr int WPADN = MAX_NRBF + 2 * RBF_WPAD;
     static constexpr int NTHREADS = 128;
     static constexpr size_t al(size_t x) { return (x + 127) / 128 * 128; }
     static constexpr size_t OFF_U = 0;
-    static constexpr size_t OFF_BZ = al(OFF_U + 4ull * 4 * UROWS * UPITCH);
-    static constexpr size_t OFF_KM = al(OFF_BZ + 4ull * KS * NPAD * 8);
-    static constexpr size_t OFF_V = al(OFF_KM + 4ull * NT * NKP);
-    static constexpr size_t OFF_W = al(OFF_V + 4ull * 128 * NKP);
+    static constexpr size_t OFF_BZ = al(OFF_U + 4ull * UROWS * UROWB);
+    static constexpr size_t OFF_KM = al(OFF_BZ + (size_t)ESZ * KS * NPAD * KMMA);
+    static constexpr size_t OFF_V = al(OFF_KM + (size_t)ESZ * NT * NKP);
+    static constexpr size_t OFF_W = al(OFF_V + (size_t)ESZ * 128 * NKP);
     static constexpr size_t OFF_H = al(OFF_W + 4ull * NK * WPADN);
     static constexpr size_t OFF_MISC = al(OFF_H + 4ull * 4 * HROWS * HPITCH);
     static constexpr size_t SMEM_BYTES = OFF_MISC + 128;

@@ -32,7 +32,8 @@ cudaError_t launch_unfused_fwd(int ks, const UnfArgs& a, int N, cudaStream_t s);
 // Tensor-core forward stage: tile height for NB row blocks, launcher, and the
 // device error word (read and cleared).
 int tc_tile_h(int ks, int nb);
-cudaError_t launch_tc_fwd(int ks, int nk, int nb, const StageArgs& a, int N, cudaStream_t s);
+cudaError_t launch_tc_fwd(int ks, int nk, int nb, bool bf16, const StageArgs& a, int N,
+                          cudaStream_t s);
 cudaError_t tc_take_error(int* out);
 
 // Column-pair fused forward (two z-columns per lane, TW = 64 - 2R); nsplit 2

@@ -6,15 +6,15 @@ namespace tnrd {
 
 namespace {
 
-template <int KS, int NK, int NB>
+template <int KS, int NK, int NB, bool BF>
 cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
 {
-    using C = TcCfg<KS, NK, NB>;
-    cudaError_t e = cudaFuncSetAttribute(tc_stage_fwd<KS, NK, NB>,
+    using C = TcCfg<KS, NK, NB, BF>;
+    cudaError_t e = cudaFuncSetAttribute(tc_stage_fwd<KS, NK, NB, BF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    tc_stage_fwd<KS, NK, NB><<<dim3(a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(a);
+    tc_stage_fwd<KS, NK, NB, BF><<<dim3(a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -25,9 +25,12 @@ cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
 
 int tc_tile_h(int ks, int nb) { return 16 * nb - 2 * (ks / 2); }
 
-cudaError_t launch_tc_fwd(int ks, int nk, int nb, const StageArgs& a, int N, cudaStream_t s)
+cudaError_t launch_tc_fwd(int ks, int nk, int nb, bool bf16, const StageArgs& a, int N,
+                          cudaStream_t s)
 {
-#define X(K, NN, B) if (ks == K && nk == NN && nb == B) return launch_one<K, NN, B>(a, N, s);
+#define X(K, NN, B)                                                                  \
+    if (ks == K && nk == NN && nb == B)                                              \
+        return bf16 ? launch_one<K, NN, B, true>(a, N, s) : launch_one<K, NN, B, false>(a, N, s);
     TNRD_TC_CASES(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -18,6 +18,14 @@
 // (leading offset 16 B, overlapping the first); the next 8-pixel group is the
 // next image row (stride offset = the copy's row pitch).  Kernel row a is one
 // MMA of K = 8 with the start row shifted by a; taps b' >= ksize are zero in B.
+//
+// TNRD_ALGO_TC_BF16 (BF = true) runs the same tile and groups with BF16
+// operands (kind::f16, K = 16 per MMA, FP32 accumulation).  A BF16 core-matrix
+// row is 8 values, so residue r of u is kept as overlapping chunks of 8:
+// chunk c of a row holds u columns 4c + r .. 4c + r + 7.  Core row m is chunk
+// m (pixel column r + 4m, taps 0..7) and the second K core (taps 8..15) is
+// chunk m + 2, 32 bytes on.  V and the adjoint's filter matrix are BF16 too;
+// phi, the scatter, the fold and the prox stay FP32.
 #pragma once
 #include "args.cuh"
 #include "tc_ptx.cuh"
@@ -29,10 +37,10 @@ namespace tnrd {
 // header (the library is built without relocatable device code).
 __device__ int g_tc_error = 0;
 
-template <int KS, int NK, int NB>
+template <int KS, int NK, int NB, bool BF>
 __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ StageArgs a)
 {
-    using C = TcCfg<KS, NK, NB>;
+    using C = TcCfg<KS, NK, NB, BF>;
     constexpr int R = C::R, TW = C::TW, TH = C::TH;
     constexpr long long WAIT_LIMIT = 1ll << 31;   // SM cycles, about one second
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -55,32 +63,67 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
     const float* uin = a.u_in + (size_t)n * a.img_stride;
 
     // ---- stage operands in shared memory ----------------------------------
-    constexpr int UCOPY = C::UROWS * C::UPITCH;
-    for (int idx = tid; idx < 4 * UCOPY; idx += 128) {
-        const int r = idx / UCOPY, rem = idx - r * UCOPY;
-        const int i = rem / C::UPITCH, j = rem - i * C::UPITCH;
-        const int yy = sym_idx(y0 - 2 * R + i, H), xx = sym_idx(x0 - 2 * R + j + r, W);
-        sU[idx] = tc::to_tf32(__ldcg(uin + (size_t)yy * a.pitch + xx));
-    }
-    // B of the filter bank, per kernel row ka: B[nn][b'] = k_nn[ka][KS-1-b'],
-    // K-major core matrices [nn/8][b'/4][nn%8][b'%4]
-    for (int e = tid; e < KS * C::NPAD * 8; e += 128) {
-        const int ka = e / (C::NPAD * 8), rem = e - ka * (C::NPAD * 8);
-        const int nn = rem / 8, k = rem - nn * 8;
-        const float v = (nn < NK && k < KS) ? __ldg(a.k + (nn * KS + ka) * KS + (KS - 1 - k)) : 0.0f;
-        sBz[ka * C::NPAD * 8 + ((nn / 8) * 2 + k / 4) * 32 + (nn % 8) * 4 + (k % 4)] = tc::to_tf32(v);
-    }
-    // B of the adjoint GEMM: B[tap][i] = k_i[tap], core matrices [i/4][tap/8][tap%8][i%4]
-    for (int e = tid; e < C::NT * C::NKP; e += 128) {
-        const int tap = e / C::NKP, i = e - tap * C::NKP;
-        const float v = (tap < KS * KS && i < NK) ? __ldg(a.k + i * KS * KS + tap) : 0.0f;
-        sKm[((i / 4) * (C::NT / 8) + tap / 8) * 32 + (tap % 8) * 4 + (i % 4)] = tc::to_tf32(v);
+    if constexpr (!BF) {
+        constexpr int UCOPY = C::UROWS * C::UPITCH;
+        for (int idx = tid; idx < 4 * UCOPY; idx += 128) {
+            const int r = idx / UCOPY, rem = idx - r * UCOPY;
+            const int i = rem / C::UPITCH, j = rem - i * C::UPITCH;
+            const int yy = sym_idx(y0 - 2 * R + i, H), xx = sym_idx(x0 - 2 * R + j + r, W);
+            sU[idx] = tc::to_tf32(__ldcg(uin + (size_t)yy * a.pitch + xx));
+        }
+        // B of the filter bank, per kernel row ka: B[nn][b'] = k_nn[ka][KS-1-b'],
+        // K-major core matrices [nn/8][b'/4][nn%8][b'%4]
+        for (int e = tid; e < KS * C::NPAD * 8; e += 128) {
+            const int ka = e / (C::NPAD * 8), rem = e - ka * (C::NPAD * 8);
+            const int nn = rem / 8, k = rem - nn * 8;
+            const float v = (nn < NK && k < KS) ? __ldg(a.k + (nn * KS + ka) * KS + (KS - 1 - k)) : 0.0f;
+            sBz[ka * C::NPAD * 8 + ((nn / 8) * 2 + k / 4) * 32 + (nn % 8) * 4 + (k % 4)] = tc::to_tf32(v);
+        }
+        // B of the adjoint GEMM: B[tap][i] = k_i[tap], core matrices [i/4][tap/8][tap%8][i%4]
+        for (int e = tid; e < C::NT * C::NKP; e += 128) {
+            const int tap = e / C::NKP, i = e - tap * C::NKP;
+            const float v = (tap < KS * KS && i < NK) ? __ldg(a.k + i * KS * KS + tap) : 0.0f;
+            sKm[((i / 4) * (C::NT / 8) + tap / 8) * 32 + (tap % 8) * 4 + (i % 4)] = tc::to_tf32(v);
+        }
+    } else {
+        // u chunks, two values per 32-bit store: [r][row][chunk][8]
+        uint32_t* sU2 = reinterpret_cast<uint32_t*>(sU);
+        constexpr int PAIRS = 4 * C::UROWS * C::UCHUNKS * 4;
+        for (int idx = tid; idx < PAIRS; idx += 128) {
+            const int e2 = idx & 3, c = (idx >> 2) % C::UCHUNKS, ri = (idx >> 2) / C::UCHUNKS;
+            const int r = ri / C::UROWS, i = ri - r * C::UROWS;
+            const int yy = sym_idx(y0 - 2 * R + i, H);
+            const int x = x0 - 2 * R + 4 * c + r + 2 * e2;
+            const float* ur = uin + (size_t)yy * a.pitch;
+            sU2[idx] = tc::pack_bf16x2(__ldcg(ur + sym_idx(x, W)), __ldcg(ur + sym_idx(x + 1, W)));
+        }
+        // B of the filter bank, per kernel row ka: B[nn][b'] = k_nn[ka][KS-1-b'] (b' < 16),
+        // core matrices [nn/8][b'/8][nn%8][b'%8]
+        uint32_t* sBz2 = reinterpret_cast<uint32_t*>(sBz);
+        for (int e = tid; e < KS * C::NPAD * 8; e += 128) {
+            const int ka = e / (C::NPAD * 8), rem = e - ka * (C::NPAD * 8);
+            const int nn = rem / 8, k = 2 * (rem - nn * 8);
+            const float v0 = (nn < NK && k < KS) ? __ldg(a.k + (nn * KS + ka) * KS + (KS - 1 - k)) : 0.0f;
+            const float v1 = (nn < NK && k + 1 < KS) ? __ldg(a.k + (nn * KS + ka) * KS + (KS - 2 - k)) : 0.0f;
+            sBz2[(ka * C::NPAD * 16 + ((nn / 8) * 2 + k / 8) * 64 + (nn % 8) * 8 + (k % 8)) / 2] =
+                tc::pack_bf16x2(v0, v1);
+        }
+        // B of the adjoint GEMM: B[tap][i] = k_i[tap], core matrices [i/8][tap/8][tap%8][i%8]
+        uint32_t* sKm2 = reinterpret_cast<uint32_t*>(sKm);
+        for (int e = tid; e < C::NT * C::NKP / 2; e += 128) {
+            const int tap = e / (C::NKP / 2), i = 2 * (e - tap * (C::NKP / 2));
+            const bool tok = tap < KS * KS;
+            const float v0 = (tok && i < NK) ? __ldg(a.k + i * KS * KS + tap) : 0.0f;
+            const float v1 = (tok && i + 1 < NK) ? __ldg(a.k + (i + 1) * KS * KS + tap) : 0.0f;
+            sKm2[(((i / 8) * (C::NT / 8) + tap / 8) * 64 + (tap % 8) * 8 + (i % 8)) / 2] =
+                tc::pack_bf16x2(v0, v1);
+        }
     }
     for (int e = tid; e < NK * C::WPADN; e += 128) {
         const int i = e / C::WPADN, jj = e - i * C::WPADN - RBF_WPAD;
         sW[e] = (jj >= 0 && jj < a.nrbf) ? __ldg(a.w + i * a.nrbf + jj) : 0.0f;
     }
-    for (int e = tid; e < 128 * C::NKP; e += 128) sV[e] = 0.0f;
+    for (int e = tid; e < C::ESZ * 128 * C::NKP / 4; e += 128) sV[e] = 0.0f;
     for (int e = tid; e < 4 * C::HROWS * C::HPITCH; e += 128) sH[e] = 0.0f;
     if (tid == 0) {
         tc::mbar_init(mbz + 0, 1);
@@ -96,8 +139,9 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
     // TMEM columns: z of even groups at 0, z of odd groups at 64, Y at 128
     const uint32_t tyv = tmem + 128;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-    constexpr uint32_t ID_Z = tc::idesc(tc::FMT_TF32, 128, C::NPAD);
-    constexpr uint32_t ID_Y = tc::idesc(tc::FMT_TF32, 128, C::NT);
+    constexpr uint32_t FMT = BF ? tc::FMT_BF16 : tc::FMT_TF32;
+    constexpr uint32_t ID_Z = tc::idesc(FMT, 128, C::NPAD);
+    constexpr uint32_t ID_Y = tc::idesc(FMT, 128, C::NT);
     constexpr uint32_t LBO_KM = (C::NT / 8) * 128;
     const RbfConst& rc = a.rc;
 
@@ -107,16 +151,17 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
     int ok = 1;
     constexpr int NG = 4 * NB;                  // groups (row block, residue) per tile
 
-    // z = K u of group gi into TMEM buffer zb: one K = 8 MMA per kernel row
+    // z = K u of group gi into TMEM buffer zb: one MMA (K = 32 bytes) per kernel row
     auto issue_z = [&](int gi, int zb) {
         const int nb = gi >> 2, r = gi & 3;
-        const float* ur = sU + r * UCOPY;
+        const uint32_t ur = tc::smem_u32(sU) + (uint32_t)(r * C::UROWS * C::UROWB);
 #pragma unroll
         for (int ka = 0; ka < KS; ++ka) {
-            const uint64_t da = tc::sdesc(tc::smem_u32(ur + (16 * nb + 2 * R - ka) * C::UPITCH), 16,
-                                          C::UPITCH * 4);
-            const uint64_t db = tc::sdesc(tc::smem_u32(sBz + ka * C::NPAD * 8), 128, 256);
-            tc::mma_tf32(tmem + 64u * zb, da, db, ID_Z, ka > 0);
+            const uint64_t da = tc::sdesc(ur + (uint32_t)((16 * nb + 2 * R - ka) * C::UROWB),
+                                          BF ? 32 : 16, C::UROWB);
+            const uint64_t db = tc::sdesc(tc::smem_u32(sBz) + (uint32_t)(ka * C::NPAD * 32), 128, 256);
+            if constexpr (BF) tc::mma_f16(tmem + 64u * zb, da, db, ID_Z, ka > 0);
+            else tc::mma_tf32(tmem + 64u * zb, da, db, ID_Z, ka > 0);
         }
         tc::commit(mbz + zb);
     };
@@ -149,12 +194,20 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
                     const float ph = rbf_phi_w(z[q], sW + (i < NK ? i : 0) * C::WPADN, rc);
                     v[q] = (i < NK && inside) ? ph : 0.0f;
                 }
-                // A layout [filter/4][g][mp][filter%4]: core matrices of 8 positions x 4 filters
-                float4* d0 = reinterpret_cast<float4*>(sV + ((c8 / 4) * 16 + g) * 32 + mp * 4);
-                *d0 = make_float4(tc::to_tf32(v[0]), tc::to_tf32(v[1]), tc::to_tf32(v[2]), tc::to_tf32(v[3]));
-                if (c8 + 4 < C::NKP) {
-                    float4* d1 = reinterpret_cast<float4*>(sV + ((c8 / 4 + 1) * 16 + g) * 32 + mp * 4);
-                    *d1 = make_float4(tc::to_tf32(v[4]), tc::to_tf32(v[5]), tc::to_tf32(v[6]), tc::to_tf32(v[7]));
+                if constexpr (!BF) {
+                    // A layout [filter/4][g][mp][filter%4]: core matrices of 8 positions x 4 filters
+                    float4* d0 = reinterpret_cast<float4*>(sV + ((c8 / 4) * 16 + g) * 32 + mp * 4);
+                    *d0 = make_float4(tc::to_tf32(v[0]), tc::to_tf32(v[1]), tc::to_tf32(v[2]), tc::to_tf32(v[3]));
+                    if (c8 + 4 < C::NKP) {
+                        float4* d1 = reinterpret_cast<float4*>(sV + ((c8 / 4 + 1) * 16 + g) * 32 + mp * 4);
+                        *d1 = make_float4(tc::to_tf32(v[4]), tc::to_tf32(v[5]), tc::to_tf32(v[6]), tc::to_tf32(v[7]));
+                    }
+                } else {
+                    // A layout [filter/8][g][mp][filter%8]: core matrices of 8 positions x 8 filters
+                    uint4* d0 = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(sV) +
+                                                         ((c8 / 8) * 16 + g) * 128 + mp * 16);
+                    *d0 = make_uint4(tc::pack_bf16x2(v[0], v[1]), tc::pack_bf16x2(v[2], v[3]),
+                                     tc::pack_bf16x2(v[4], v[5]), tc::pack_bf16x2(v[6], v[7]));
                 }
             }
         }
@@ -165,11 +218,14 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
         // ---- Y = V Kmat ----------------------------------------------------------
         if (ok) {
             if (tid == 0) {
+                // one MMA per two K cores (8 filters TF32, 16 filters BF16): 4 KB of V
+                // and 2 LBO_KM of the filter matrix apart
 #pragma unroll
-                for (int s = 0; s < C::NKP / 8; ++s) {
-                    const uint64_t da = tc::sdesc(tc::smem_u32(sV + s * 2 * (16 * 32)), 16 * 128, 128);
-                    const uint64_t db = tc::sdesc(tc::smem_u32(sKm + s * 2 * (LBO_KM / 4)), LBO_KM, 128);
-                    tc::mma_tf32(tyv, da, db, ID_Y, s > 0);
+                for (int s = 0; s < C::NKP / C::KMMA; ++s) {
+                    const uint64_t da = tc::sdesc(tc::smem_u32(sV) + (uint32_t)(s * 4096), 16 * 128, 128);
+                    const uint64_t db = tc::sdesc(tc::smem_u32(sKm) + (uint32_t)(s * 2 * LBO_KM), LBO_KM, 128);
+                    if constexpr (BF) tc::mma_f16(tyv, da, db, ID_Y, s > 0);
+                    else tc::mma_tf32(tyv, da, db, ID_Y, s > 0);
                 }
                 tc::commit(mby);
             }
@@ -181,6 +237,13 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
         // ---- scatter: h(p - off(tap)) += Y[p][tap] into this warp's partial ------
         // (tcgen05.ld is warp-collective: every lane loads; lanes outside the
         // image have v = 0, hence Y = 0, and add zeros at in-range indices)
+        // Two lanes of a warp, (g, mp) and (g', mp'), update the same h element
+        // through taps (a, b) and (a', b') when g - a = g' - a' and
+        // 4 mp - b = 4 mp' - b', i.e. only for taps with different kernel rows,
+        // or with the same row and b - b' = +-4.  Taps of one row with b in
+        // [0, 4) or in [4, 8) never collide, so a warp barrier (which also
+        // orders the lanes' shared-memory accesses) before each such run keeps
+        // every read-modify-write of h whole.
         if (ok) {
             const int base = (16 * nb + g + 2 * R) * C::HPITCH + (r + 4 * mp + 2 * R);
 #pragma unroll
@@ -190,9 +253,13 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int t = c8 + q;
-                    if (t < KS * KS) myh[base - (t / KS) * C::HPITCH - (t % KS)] += y[q];
+                    if (t < KS * KS) {
+                        if ((t % KS) % 4 == 0) __syncwarp();
+                        myh[base - (t / KS) * C::HPITCH - (t % KS)] += y[q];
+                    }
                 }
             }
+            __syncwarp();
         }
         tc::fence_before();
         __syncthreads();

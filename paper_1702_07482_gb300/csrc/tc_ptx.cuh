@@ -130,5 +130,14 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(y);
 }
 
+// Two fp32 values -> packed bf16x2 (round to nearest even); lo lands in the
+// lower 16 bits, i.e. at the lower address when stored.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    uint32_t y;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(y) : "f"(hi), "f"(lo));
+    return y;
+}
+
 }  // namespace tc
 }  // namespace tnrd
