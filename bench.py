@@ -62,24 +62,27 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# DRAM bytes (read + write) per launch of the stage kernel at this workload,
-# from one ncu capture (profiles/fused_stage_fwd_7x7x48_512x512.md), valid only
-# for the kernel sources it was taken on (their hash is checked at run time).
-_TRAFFIC = {"sources_sha256_16": "20c231ed885ecf70", "bytes_per_launch": 2205440}
+# DRAM bytes (read + write) per launch of the fused stage kernel at the 512 x 512
+# workload, from one ncu capture (profiles/fused_pair2_fwd_7x7x48_512x512.md),
+# valid only for the kernel that capture measured and the sources it was taken
+# on (the kernel name and the sources' hash are checked at run time).
+_TRAFFIC = {"kernel": "fused_pair2_fwd<7,48,37> tiles 37x58", "sources_sha256_16": "5d25d82e7bfff84b",
+            "bytes_per_launch": 2215936}
 
 
 def _kernel_sources_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("fused_fwd.cuh", "common.cuh", "args.cuh"):
+    for f in ("fused_fwd.cuh", "fused_pair.cuh", "common.cuh", "args.cuh"):
         with open(os.path.join(ROOT, "paper_1702_07482_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _measured_traffic():
+def _measured_traffic(kernel: str):
     try:
-        if _kernel_sources_hash() == _TRAFFIC["sources_sha256_16"]:
+        if (kernel == _TRAFFIC["kernel"] and
+                _kernel_sources_hash() == _TRAFFIC["sources_sha256_16"]):
             return _TRAFFIC["bytes_per_launch"]
     except OSError:
         pass
@@ -230,10 +233,9 @@ class Fwd(Workload):
         fl = 2 * nk * ks * ks * 2 + 2 * nk * 63 + 12
         self.flops = float(H * W) * T_ * fl
         self.flops_per_px_stage = fl
-        self.kernel = f"fused_stage_fwd<{ks},{nk},TH>" if algo == "fused" else \
-            f"unf_bank_phi + unf_adjoint + unf_prox <{ks}>"
+        self.kernel = binding.tnrd_forward_kernel(self.prm, 1, H, W, self.algo)
         self.h2d = self.d2h = int(self.f_host.numel() * 4)
-        self.traffic = _measured_traffic() if (algo == "fused" and H == 512 and ks == 7) else None
+        self.traffic = _measured_traffic(self.kernel) if (algo == "fused" and H == 512) else None
         self.config = {"workload": f"TRDMD forward, 1 x {H}x{W} per GPU, {ks}x{ks}x{nk}, 63 RBF, "
                                    f"T={T_}, L={L}, {algo} FP32 stage kernel" +
                                    ("" if algo == "fused" else "s"),
@@ -365,7 +367,8 @@ class Train(Workload):
         self.launches = T_ + T_ * 5   # forward stages; prep, zb, adj, dk, reduce per stage
         self.flops = float(self.px) * T_ * (FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE)
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE
-        self.kernel = "fused_stage_fwd + bwd_prep/bwd_zb/bwd_adj/bwd_dk/bwd_reduce <7,48>"
+        self.kernel = (B.tnrd_forward_kernel(self.m.params(), n, S, S, B.ALGO["fused"]) +
+                       " + bwd_prep/bwd_zb/bwd_adj/bwd_dk/bwd_reduce <7,48>")
         self.h2d = int((self.f_host.numel() + self.c_host.numel()) * 4)
         self.d2h = int(self.g_host.numel() * 4)
         self.config = {"workload": f"TRDMD training step (forward + backward), {n} crops of "
@@ -442,10 +445,9 @@ class Mixed(Workload):
         self.launches = T_
         self.flops = float(self.px) * T_ * FLOPS_PER_PX_STAGE
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE
-        self.kernel = {"tf32": "tc_stage_fwd<7,48,2,tf32> (tcgen05 TF32 filter bank and adjoint, "
-                               "FP32 phi/prox)",
-                       "bf16": "tc_stage_fwd<7,48,2,bf16> (tcgen05 BF16 filter bank and adjoint, "
-                               "FP32 phi/prox)"}.get(algo, "fused_stage_fwd<7,48,TH> (FP32)")
+        self.kernel = B.tnrd_forward_kernel(self.prm, n, S, S, self.code) + \
+            {"tf32": " (tcgen05 TF32 filter bank and adjoint, FP32 phi/prox)",
+             "bf16": " (tcgen05 BF16 filter bank and adjoint, FP32 phi/prox)"}.get(algo, " (FP32)")
         prec = {"tf32": "filter bank and adjoint on tensor cores (TF32 operands, FP32 accumulate), "
                         "phi and prox FP32",
                 "bf16": "filter bank and adjoint on tensor cores (BF16 operands, FP32 accumulate), "

@@ -102,6 +102,14 @@ TNRD_API tnrd_status tnrd_forward(const tnrd_params* params, int N, int H, int W
                          const float* f, float* u, int keep_stages, tnrd_algo algo,
                          void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
+/* Describes the stage kernel tnrd_forward would launch for this shape and
+ * algo (kernel name and tile geometry), as a NUL-terminated string of at most
+ * len - 1 characters written to buf.  Host-only: launches nothing.  Returns
+ * TNRD_ERR_INVALID_ARG for a null or empty buf, otherwise the status
+ * tnrd_forward's parameter checks would return. */
+TNRD_API tnrd_status tnrd_forward_kernel(const tnrd_params* params, int N, int H, int W,
+                                         tnrd_algo algo, char* buf, size_t len);
+
 /* Gradients of a loss L through the cascade (Sec. 3.2, Eq. iterstep), for the
  * images of a batch summed (the loss of Eq. learning sums over samples).
  *   u_stages  [T+1][N][H][pitch] from tnrd_forward(keep_stages = 1)

@@ -25,7 +25,8 @@ OP_FORWARD, OP_BACKWARD = 0, 1
 EXPORTS = ["tnrd_workspace_size", "tnrd_forward", "tnrd_backward", "tnrd_plan_create",
            "tnrd_batch_forward", "tnrd_plan_status", "tnrd_plan_set_wait_limit",
            "tnrd_plan_tile_height", "tnrd_plan_destroy",
-           "tnrd_forward_noalloc", "tnrd_device_status", "tnrd_last_error", "tnrd_version"]
+           "tnrd_forward_noalloc", "tnrd_forward_kernel", "tnrd_device_status", "tnrd_last_error",
+           "tnrd_version"]
 
 # Largest N * H * pitch (floats) tnrd_forward_noalloc accepts (TNRD_NOALLOC_MAX_FLOATS).
 NOALLOC_MAX_FLOATS = 1 << 22
@@ -87,6 +88,8 @@ def load(path: str = LIB_PATH):
         L.tnrd_plan_destroy.argtypes = [P]
         L.tnrd_forward_noalloc.restype = i
         L.tnrd_forward_noalloc.argtypes = [pp, i, i, i, i, P, P, P]
+        L.tnrd_forward_kernel.restype = i
+        L.tnrd_forward_kernel.argtypes = [pp, i, i, i, i, ctypes.c_char_p, sz]
         L.tnrd_device_status.restype = i
         L.tnrd_device_status.argtypes = []
         L.tnrd_last_error.restype = ctypes.c_char_p
@@ -189,6 +192,13 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def tnrd_forward_kernel(params, N: int, H: int, W: int, algo: int) -> str:
+    """Name and tile geometry of the stage kernel tnrd_forward would launch."""
+    buf = ctypes.create_string_buffer(160)
+    check(load().tnrd_forward_kernel(ctypes.byref(params), N, H, W, algo, buf, len(buf)))
+    return buf.value.decode()
 
 
 def tnrd_device_status() -> int:

@@ -281,6 +281,39 @@ size_t tnrd_workspace_size(tnrd_op op, const tnrd_params* params, int N, int H, 
     return 0;
 }
 
+tnrd_status tnrd_forward_kernel(const tnrd_params* p, int N, int H, int W, tnrd_algo algo,
+                                char* buf, size_t len)
+{
+    if (!buf || len == 0) return fail(TNRD_ERR_INVALID_ARG, "null or empty buffer");
+    buf[0] = '\0';
+    tnrd_status st = check_params(p);
+    if (st != TNRD_OK) return st;
+    st = check_images(N, H, W, (W + 3) & ~3, p->ksize);
+    if (st != TNRD_OK) return st;
+    const int ks = p->ksize, nk = p->nfilt, R = ks / 2;
+    if (algo == TNRD_ALGO_FUSED) {
+        const FusedChoice c = pick_fused(ks, nk, N, H, W);
+        if (c.pair)
+            std::snprintf(buf, len, "%s<%d,%d,%d> tiles %dx%d", c.nsplit == 2 ? "fused_pair2_fwd" : "fused_pair_fwd",
+                          ks, nk, c.th, c.th, c.tw);
+        else
+            std::snprintf(buf, len, "fused_stage_fwd<%d,%d,%d> tiles %dx%d", ks, nk, c.th, c.th, c.tw);
+    } else if (algo == TNRD_ALGO_UNFUSED) {
+        std::snprintf(buf, len, "unf_bank_phi + unf_adjoint + unf_prox <%d,%d>", ks, nk);
+    } else if (algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16) {
+        int nb = 2;
+        if (const char* env = std::getenv("TNRD_TC_NB")) {
+            const int v = std::atoi(env);
+            if (v == 2 || v == 3) nb = v;
+        }
+        std::snprintf(buf, len, "tc_stage_fwd<%d,%d,%d,%s> tiles %dx%d", ks, nk, nb,
+                      algo == TNRD_ALGO_TC_BF16 ? "bf16" : "tf32", tnrd::tc_tile_h(ks, nb), 32 - 2 * R);
+    } else {
+        return fail(TNRD_ERR_INVALID_ARG, "unknown algo");
+    }
+    return TNRD_OK;
+}
+
 tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
                          const float* f, float* u, int keep_stages, tnrd_algo algo,
                          void* workspace, size_t workspace_bytes, cudaStream_t stream)

@@ -109,3 +109,19 @@ def test_plan_create_rejects_bad_batches_before_touching_the_device(lib):
     two = (B.tnrd_params * 2)(p, p2)
     assert lib.tnrd_plan_create(ctypes.byref(h), arr, 1, two, 2, 0, 0, None) == 1
     assert not h.value
+
+
+def test_forward_kernel_query_host_only():
+    """tnrd_forward_kernel names a kernel for every algo without a GPU and
+    rejects what tnrd_forward rejects."""
+    import synth
+    from paper_1702_07482_gb300 import binding as B
+    from paper_1702_07482_gb300 import ops
+    p = synth.params(2, 7, 48, seed=3)
+    m = ops.Model.create(p.filters, p.rbf_w, p.lam, device="cpu")
+    prm = m.params()
+    assert B.tnrd_forward_kernel(prm, 1, 64, 64, B.ALGO["unfused"]).startswith("unf_bank_phi")
+    assert "tf32" in B.tnrd_forward_kernel(prm, 1, 64, 64, B.ALGO["tf32"])
+    assert "bf16" in B.tnrd_forward_kernel(prm, 1, 64, 64, B.ALGO["bf16"])
+    with pytest.raises(B.TnrdError):
+        B.tnrd_forward_kernel(prm, 1, 5, 64, B.ALGO["fused"])   # H < ksize
