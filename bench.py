@@ -9,12 +9,13 @@ collective on the data path): weak scaling.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload fwd512|fwd512_unfused|small128|batched|train|
-                              mixed_tf32|mixed_bf16|mixed_fp32]
+                              fit|mixed_tf32|mixed_bf16|mixed_fp32]
 
 The other workloads (one GPU) measure the rest of the table with the same
 contract: fwd512_unfused (three kernels per stage), small128 (1 x 128^2,
 5x5x24), batched (64 images of 256-1024 px per side, four parameter sets, one
 persistent launch per step), train (32 x 180^2 crops, forward + backward),
+fit (one Adam iteration of joint training on the same crops),
 mixed_tf32 / mixed_bf16 / mixed_fp32 (16 x 2048^2, L = 2, T = 8, tensor-core
 TF32 and BF16 vs plain FP32; the line adds the path's error against the FP64
 oracle).
@@ -411,6 +412,41 @@ class Train(Workload):
                           f"T={self.T} stages ({dt:.1f} s)"}
 
 
+class Fit(Train):
+    """One Adam iteration of joint training (Sec. 3.2) on the training-step
+    batch: forward, backward, zero-mean filter projection and the update of
+    filters, RBF weights and beta = log lambda."""
+
+    def __init__(self, dev):
+        super().__init__(dev)
+        import torch
+        from paper_1702_07482_gb300 import train
+        self.tp = train.Params.from_model(self.p.filters, self.p.rbf_w, self.p.lam, device=dev)
+        self.opt = torch.optim.Adam(self.tp.tensors(), lr=1e-3)
+        self.f_img = self.f_dev[..., :self.S]
+        self.c_img = self.c_dev[..., :self.S]
+        self.loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+        self.d2h = 4
+        self.kernel = self.kernel + " + torch Adam on the parameters"
+        self.config = dict(self.config)
+        self.config["workload"] = (f"TRDMD joint training iteration (Adam, lr 1e-3): forward + "
+                                   f"backward + update, {self.n} crops of {self.S}x{self.S}, L=1, "
+                                   f"7x7x48, 63 RBF, T={self.T}, loss 1/2|u_T - clean|^2")
+
+    def step(self):
+        from paper_1702_07482_gb300 import train
+        self.opt.zero_grad(set_to_none=False)
+        self.loss = train.loss_sum(train.cascade(self.tp, self.f_img), self.c_img)
+        self.loss.backward()
+        self.opt.step()
+
+    def e2e(self):
+        self.f_dev.copy_(self.f_host, non_blocking=True)
+        self.c_dev.copy_(self.c_host, non_blocking=True)
+        self.step()
+        self.loss_host.copy_(self.loss.detach().reshape(1), non_blocking=True)
+
+
 class Mixed(Workload):
     """16 images of 2048 x 2048, L = 2, 7x7x48, T = 8, as one batch."""
 
@@ -516,6 +552,8 @@ def make_workload(name, dev):
         return Batched(dev)
     if name == "train":
         return Train(dev)
+    if name == "fit":
+        return Fit(dev)
     if name == "mixed_tf32":
         return Mixed(dev, algo="tf32")
     if name == "mixed_bf16":
@@ -671,7 +709,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fwd512",
                     choices=["fwd512", "fwd512_unfused", "small128", "batched", "train",
-                             "mixed_tf32", "mixed_bf16", "mixed_fp32"])
+                             "fit", "mixed_tf32", "mixed_bf16", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

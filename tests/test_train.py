@@ -1,0 +1,76 @@
+"""Training loop (Sec. 3.2): greedy stage-wise, then joint, with Adam or
+L-BFGS on top of the library's forward and backward kernels."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+
+def _problem(n=6, S=48, T=2, ks=5, nk=24, cfg=210, device="cuda"):
+    p = synth.params(T, ks, nk, seed=synth.seed_for(cfg, 0, "params"), w_sigma=0.02)
+    pairs = [synth.single_image(S, S, 4, cfg, index=i) for i in range(n)]
+    clean = torch.tensor(np.stack([c for c, _ in pairs]), dtype=torch.float32, device=device)
+    f = torch.tensor(np.stack([f for _, f in pairs]), dtype=torch.float32, device=device)
+    return p, f, clean
+
+
+def test_parameterisation_on_cpu():
+    """Zero-mean filters and lambda = exp(beta) hold by construction, and the
+    projection's gradient is the projected gradient."""
+    from paper_1702_07482_gb300 import train
+    p, _, _ = _problem(n=1, device="cpu")
+    tp = train.Params.from_model(p.filters, p.rbf_w, p.lam, device="cpu")
+    k = tp.filters()
+    assert torch.allclose(k.sum(dim=(-2, -1)), torch.zeros(k.shape[:2]), atol=1e-5)
+    assert torch.allclose(tp.lam(), torch.tensor(p.lam, dtype=torch.float32))
+    g = torch.randn_like(k)
+    (k * g).sum().backward()
+    proj = g - g.mean(dim=(-2, -1), keepdim=True)
+    assert torch.allclose(tp.theta.grad, proj, atol=1e-6)
+    with pytest.raises(ValueError):
+        train.Params.from_model(p.filters, p.rbf_w, np.zeros_like(p.lam), device="cpu")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("optimizer,lr,frac", [("adam", 3e-2, 0.6), ("lbfgs", 1.0, 0.1)])
+def test_greedy_then_joint_decreases_loss(optimizer, lr, frac):
+    """6 greedy iterations per stage and 8 joint ones on 6 crops of 48 x 48
+    (L = 4, 5x5x24, T = 2) must bring the per-pixel MSE below `frac` times the
+    noisy input's (measured: Adam 0.38, L-BFGS 0.017)."""
+    from paper_1702_07482_gb300 import binding, build, train
+    build.build()
+    binding.load()
+    p, f, clean = _problem()
+    tp = train.Params.from_model(p.filters, p.rbf_w, p.lam)
+    hist = train.fit(tp, f, clean, greedy_steps=6, joint_steps=8, optimizer=optimizer, lr=lr)
+    by = {}
+    for tag, it, mse in hist:
+        by.setdefault(tag, []).append(mse)
+    assert set(by) == {"greedy1", "greedy2", "joint"}
+    for tag, v in by.items():
+        assert np.all(np.isfinite(v)), (tag, v)
+        assert min(v[1:]) < v[0], (tag, v)          # every phase improves on its start
+    with torch.no_grad():
+        final = float(train.loss_sum(train.cascade(tp, f), clean)) / clean.numel() * 2
+    noisy = float(((f - clean) ** 2).mean())
+    assert final < frac * noisy, (final, noisy, by)
+    k = tp.filters().detach()
+    assert float(k.sum(dim=(-2, -1)).abs().max()) < 1e-4
+    assert bool(torch.all(tp.lam() > 0))
+
+
+@pytest.mark.gpu
+def test_greedy_phase_leaves_other_stages_alone():
+    from paper_1702_07482_gb300 import binding, build, train
+    build.build()
+    binding.load()
+    p, f, clean = _problem(n=2, S=40, T=3)
+    tp = train.Params.from_model(p.filters, p.rbf_w, p.lam)
+    before = [t.detach().clone() for t in tp.tensors()]
+    mask = torch.tensor([False, True, False], device="cuda")
+    train._run(tp, f, clean, 2, 3, "adam", 1e-2, mask)
+    after = tp.tensors()
+    for b, a in zip(before, after):
+        assert torch.equal(b[0], a[0].detach()) and torch.equal(b[2], a[2].detach())
+        assert not torch.equal(b[1], a[1].detach())
