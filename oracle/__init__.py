@@ -64,6 +64,10 @@ def lib():
                 "orc_forward": (None, [P, i, i, i, P, P, P, i, i, i, d, d, d, P]),
                 "orc_backward": (None, [P, i, i, i, P, P, P, i, i, i, d, d, d,
                                         P, P, P, P, P, P]),
+                "orc_stage_mode": (None, [P, P, i, i, i, P, P, P, i, i, i, d, d, d, i, d, P, P]),
+                "orc_forward_mode": (None, [P, i, i, i, P, P, P, i, i, i, d, d, d, i, d, P]),
+                "orc_backward_mode": (None, [P, i, i, i, P, P, P, i, i, i, d, d, d, i, d,
+                                             P, P, P, P, P, P]),
                 "orc_set_threads": (None, [i]),
                 "orc_get_threads": (i, []),
             }
@@ -159,6 +163,12 @@ def _pargs(p):
     return (k, w, lam), (pk, pw, pl)
 
 
+def _mode(p):
+    """Data term of the model: 0 I-divergence prox (default), 1 TNRD Gaussian
+    reaction, 2 explicit step with projection (floor p.proj_c)."""
+    return int(getattr(p, "dterm", 0)), float(getattr(p, "proj_c", 1.0))
+
+
 def stage(u_prev, f, p, t):
     """One stage (0-based t): returns (u_next, u_tilde)."""
     u_prev, pu = _c(u_prev)
@@ -167,9 +177,10 @@ def stage(u_prev, f, p, t):
     H, W = u_prev.shape
     un = np.empty_like(u_prev)
     ut = np.empty_like(u_prev)
-    lib().orc_stage(pu, pf, H, W, int(t), pk, pw, pl, p.nk, p.ks, p.nrbf,
-                    p.mu0, p.delta, p.gamma, un.ctypes.data_as(ctypes.c_void_p),
-                    ut.ctypes.data_as(ctypes.c_void_p))
+    mode, c = _mode(p)
+    lib().orc_stage_mode(pu, pf, H, W, int(t), pk, pw, pl, p.nk, p.ks, p.nrbf,
+                         p.mu0, p.delta, p.gamma, mode, c, un.ctypes.data_as(ctypes.c_void_p),
+                         ut.ctypes.data_as(ctypes.c_void_p))
     return un, ut
 
 
@@ -179,8 +190,9 @@ def forward(f, p):
     keep, (pk, pw, pl) = _pargs(p)
     H, W = f.shape
     out = np.empty((p.T + 1, H, W), dtype=np.float64)
-    lib().orc_forward(pf, H, W, p.T, pk, pw, pl, p.nk, p.ks, p.nrbf,
-                      p.mu0, p.delta, p.gamma, out.ctypes.data_as(ctypes.c_void_p))
+    mode, c = _mode(p)
+    lib().orc_forward_mode(pf, H, W, p.T, pk, pw, pl, p.nk, p.ks, p.nrbf,
+                           p.mu0, p.delta, p.gamma, mode, c, out.ctypes.data_as(ctypes.c_void_p))
     return out
 
 
@@ -196,8 +208,10 @@ def backward(f, p, u_all, e_T):
     gw = np.empty(p.rbf_w.shape)
     gl = np.empty(p.lam.shape)
     vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-    lib().orc_backward(pf, H, W, p.T, pk, pw, pl, p.nk, p.ks, p.nrbf,
-                       p.mu0, p.delta, p.gamma, pua, pe, vp(e0), vp(gk), vp(gw), vp(gl))
+    mode, c = _mode(p)
+    lib().orc_backward_mode(pf, H, W, p.T, pk, pw, pl, p.nk, p.ks, p.nrbf,
+                            p.mu0, p.delta, p.gamma, mode, c, pua, pe, vp(e0), vp(gk), vp(gw),
+                            vp(gl))
     return e0, gk, gw, gl
 
 

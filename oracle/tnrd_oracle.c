@@ -155,21 +155,67 @@ double orc_prox_dlam(double ut, double f, double lam)
     return t1 - (ut + S) / (a * a);
 }
 
-void orc_stage(const double* u_prev, const double* f, int H, int W, int t,
-               const double* k, const double* w, const double* lam,
-               int nk, int ks, int nrbf, double mu0, double delta, double gamma,
-               double* u_next, double* ut_out)
+/* Reaction term psi(u) of the explicit data-term steps and its derivative:
+ *   ORC_GAUSS: psi = lam (u - f),                 psi' = lam
+ *   ORC_PROJ:  psi = (lam / u) (1 - f^2 / u^2),   psi' = -lam / u^2 + 3 lam f^2 / u^4
+ * (the gradient of lam/2 |u - f|^2, resp. of lam <log u + f^2 / (2 u^2), 1>). */
+static double orc_psi(int mode, double u, double f, double lam)
+{
+    if (mode == ORC_GAUSS) return lam * (u - f);
+    if (mode == ORC_PROJ) return (lam / u) * (1.0 - (f * f) / (u * u));
+    return 0.0;
+}
+
+static double orc_dpsi(int mode, double u, double f, double lam)
+{
+    if (mode == ORC_GAUSS) return lam;
+    if (mode == ORC_PROJ) return -lam / (u * u) + 3.0 * lam * f * f / (u * u * u * u);
+    return 0.0;
+}
+
+void orc_stage_mode(const double* u_prev, const double* f, int H, int W, int t,
+                    const double* k, const double* w, const double* lam,
+                    int nk, int ks, int nrbf, double mu0, double delta, double gamma,
+                    int mode, double c, double* u_next, double* ut_out)
 {
     const long n = (long)H * W;
     double* g = (double*)malloc(sizeof(double) * n);
     double* ut = (double*)malloc(sizeof(double) * n);
     orc_diffusion(u_prev, H, W, k + (long)t * nk * ks * ks, w + (long)t * nk * nrbf,
                   nk, ks, nrbf, mu0, delta, gamma, g);
-    for (long p = 0; p < n; ++p) ut[p] = u_prev[p] - g[p];
-    orc_prox_vec(ut, f, n, lam[t], u_next);
+    for (long p = 0; p < n; ++p)
+        ut[p] = u_prev[p] - g[p] - orc_psi(mode, u_prev[p], f[p], lam[t]);
+    if (mode == ORC_IDIV) {
+        orc_prox_vec(ut, f, n, lam[t], u_next);
+    } else if (mode == ORC_GAUSS) {
+        memcpy(u_next, ut, sizeof(double) * n);
+    } else {
+        for (long p = 0; p < n; ++p) u_next[p] = ut[p] > c ? ut[p] : c;
+    }
     if (ut_out) memcpy(ut_out, ut, sizeof(double) * n);
     free(g);
     free(ut);
+}
+
+void orc_stage(const double* u_prev, const double* f, int H, int W, int t,
+               const double* k, const double* w, const double* lam,
+               int nk, int ks, int nrbf, double mu0, double delta, double gamma,
+               double* u_next, double* ut_out)
+{
+    orc_stage_mode(u_prev, f, H, W, t, k, w, lam, nk, ks, nrbf, mu0, delta, gamma,
+                   ORC_IDIV, 0.0, u_next, ut_out);
+}
+
+void orc_forward_mode(const double* f, int H, int W, int T,
+                      const double* k, const double* w, const double* lam,
+                      int nk, int ks, int nrbf, double mu0, double delta, double gamma,
+                      int mode, double c, double* u_all)
+{
+    const long n = (long)H * W;
+    memcpy(u_all, f, sizeof(double) * n);
+    for (int t = 0; t < T; ++t)
+        orc_stage_mode(u_all + t * n, f, H, W, t, k, w, lam, nk, ks, nrbf, mu0, delta, gamma,
+                       mode, c, u_all + (t + 1) * n, NULL);
 }
 
 void orc_forward(const double* f, int H, int W, int T,
@@ -177,29 +223,28 @@ void orc_forward(const double* f, int H, int W, int T,
                  int nk, int ks, int nrbf, double mu0, double delta, double gamma,
                  double* u_all)
 {
-    const long n = (long)H * W;
-    memcpy(u_all, f, sizeof(double) * n);
-    for (int t = 0; t < T; ++t)
-        orc_stage(u_all + t * n, f, H, W, t, k, w, lam, nk, ks, nrbf, mu0, delta, gamma,
-                  u_all + (t + 1) * n, NULL);
+    orc_forward_mode(f, H, W, T, k, w, lam, nk, ks, nrbf, mu0, delta, gamma, ORC_IDIV, 0.0,
+                     u_all);
 }
 
 /* Back-propagation through the cascade (Eq. iterstep), stage by stage from T
- * down to 1.  For stage t with e = dL/du_t:
- *   d      = y .* e                                       (Eqs. derv1, derv2)
- *   dlam_t = sum_p x_p e_p                                (Eq. derv4)
+ * down to 1.  For stage t with e = dL/du_t, u~ = u - diffusion(u) - psi(u) and
+ * u_t = P(u~) (P the prox, the identity or max(., c)):
+ *   s      = P'(u~): y of Eq. derv2 / 1 / [u~ > c]
+ *   d      = s .* e                                       (Eqs. derv1, derv2)
+ *   dlam_t = sum_p e_p du_t/dlam: x of Eq. derv4 / -(u - f) d / -(psi/lam) d
  *   b_i    = K_i d
  *   dw_ij  = -sum_p b_i(p) G_j(z_i(p))                    (phi_i linear in w_i)
  *   c_i    = -phi_i'(z_i) .* b_i
  *   dk_i   = sum_p c_i(p) * dz_i(p)/dk_i - v_i(p) * d(K_i d)(p)/dk_i ... both
  *            written out as the shifted products of the padded images
- *   dL/du_{t-1} = d + sum_i K_i^T c_i                     (Eq. derv1-1)
+ *   dL/du_{t-1} = (1 - psi'(u)) d + sum_i K_i^T c_i       (Eq. derv1-1)
  */
-void orc_backward(const double* f, int H, int W, int T,
-                  const double* k, const double* w, const double* lam,
-                  int nk, int ks, int nrbf, double mu0, double delta, double gamma,
-                  const double* u_all, const double* e_T,
-                  double* e_0, double* gk, double* gw, double* glam)
+void orc_backward_mode(const double* f, int H, int W, int T,
+                       const double* k, const double* w, const double* lam,
+                       int nk, int ks, int nrbf, double mu0, double delta, double gamma,
+                       int mode, double cproj, const double* u_all, const double* e_T,
+                       double* e_0, double* gk, double* gw, double* glam)
 {
     const long n = (long)H * W;
     const int r = ks / 2;
@@ -220,14 +265,22 @@ void orc_backward(const double* f, int H, int W, int T,
         const double* kt_ = k + (long)t * nk * ks * ks;
         const double* wt_ = w + (long)t * nk * nrbf;
         /* recompute u~ of this stage */
-        orc_stage(u, f, H, W, t, k, w, lam, nk, ks, nrbf, mu0, delta, gamma, unext, ut);
+        orc_stage_mode(u, f, H, W, t, k, w, lam, nk, ks, nrbf, mu0, delta, gamma, mode, cproj,
+                       unext, ut);
         double sl = 0.0;
         for (long p = 0; p < n; ++p) {
-            d[p] = orc_prox_du(ut[p], f[p], lam[t]) * e[p];
-            sl += orc_prox_dlam(ut[p], f[p], lam[t]) * e[p];
+            if (mode == ORC_IDIV) {
+                d[p] = orc_prox_du(ut[p], f[p], lam[t]) * e[p];
+                sl += orc_prox_dlam(ut[p], f[p], lam[t]) * e[p];
+            } else {
+                const double s = (mode == ORC_GAUSS) ? 1.0 : (ut[p] > cproj ? 1.0 : 0.0);
+                d[p] = s * e[p];
+                /* psi is linear in lam: du~/dlam = -psi / lam */
+                sl += -(orc_psi(mode, u[p], f[p], 1.0)) * d[p];
+            }
+            e_prev[p] = (1.0 - orc_dpsi(mode, u[p], f[p], lam[t])) * d[p];
         }
         glam[t] = sl;
-        memcpy(e_prev, d, sizeof(double) * n);
         for (int i = 0; i < nk; ++i) {
             const double* ki = kt_ + (long)i * ks * ks;
             const double* wi = wt_ + (long)i * nrbf;
@@ -263,6 +316,16 @@ void orc_backward(const double* f, int H, int W, int T,
     if (e_0) memcpy(e_0, e, sizeof(double) * n);
     free(e); free(e_prev); free(ut); free(unext); free(d); free(z); free(v);
     free(b); free(c); free(kt);
+}
+
+void orc_backward(const double* f, int H, int W, int T,
+                  const double* k, const double* w, const double* lam,
+                  int nk, int ks, int nrbf, double mu0, double delta, double gamma,
+                  const double* u_all, const double* e_T,
+                  double* e_0, double* gk, double* gw, double* glam)
+{
+    orc_backward_mode(f, H, W, T, k, w, lam, nk, ks, nrbf, mu0, delta, gamma, ORC_IDIV, 0.0,
+                      u_all, e_T, e_0, gk, gw, glam);
 }
 
 void orc_set_threads(int n)

@@ -13,6 +13,8 @@
  *     u_t  = (u~ + sqrt(u~^2 + 8 (1+2 lam) lam f^2)) / (2 (1+2 lam))   (Eq. subproblemGIdiv)
  *   cascade (Eq. diffusion): u_0 = f, t = 1..T.
  *   gradients (Sec. 3.2, Eqs. derv1, derv1-1, derv2, derv4, iterstep).
+ *   the same stage with the TNRD Gaussian-denoising reaction term (Sec. 2.2.1)
+ *   and with the explicit data-term step plus projection (Eq. diffusion_backP).
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - "*" is true 2-D convolution; boundary is half-sample symmetric padding
@@ -64,14 +66,41 @@ void orc_prox_vec(const double* ut, const double* f, long n, double lam, double*
 double orc_prox_du(double ut, double f, double lam);
 double orc_prox_dlam(double ut, double f, double lam);
 
+/* Data terms of a stage (the reaction force):
+ *   ORC_IDIV  0: despeckling, u_t = prox of G = lam <u^2 - 2 f^2 log u, 1>
+ *                at u~ = u_{t-1} - diffusion (Eqs. diffusionprocessfinal,
+ *                subproblemGIdiv);
+ *   ORC_GAUSS 1: TNRD Gaussian denoising, G = 0, D = lam/2 |u - f|^2 (Sec. 2.2.1,
+ *                A = identity): u_t = u_{t-1} - diffusion - lam (u_{t-1} - f);
+ *   ORC_PROJ  2: the explicit despeckling step with projection, Eq.
+ *                diffusion_backP: u~ = u_{t-1} - diffusion
+ *                - (lam / u_{t-1}) (1 - f^2 / u_{t-1}^2), u_t = max(u~, c). */
+enum { ORC_IDIV = 0, ORC_GAUSS = 1, ORC_PROJ = 2 };
+
+/* One stage t (0-based) of the model with data term `mode` (c: the projection
+ * floor of ORC_PROJ, unused otherwise).  ut_out (nullable) receives u~. */
+void orc_stage_mode(const double* u_prev, const double* f, int H, int W, int t,
+                    const double* k, const double* w, const double* lam,
+                    int nk, int ks, int nrbf, double mu0, double delta, double gamma,
+                    int mode, double c, double* u_next, double* ut_out);
+void orc_forward_mode(const double* f, int H, int W, int T,
+                      const double* k, const double* w, const double* lam,
+                      int nk, int ks, int nrbf, double mu0, double delta, double gamma,
+                      int mode, double c, double* u_all);
+void orc_backward_mode(const double* f, int H, int W, int T,
+                       const double* k, const double* w, const double* lam,
+                       int nk, int ks, int nrbf, double mu0, double delta, double gamma,
+                       int mode, double c, const double* u_all, const double* e_T,
+                       double* e_0, double* gk, double* gw, double* glam);
+
 /* One stage t (0-based) of the model: u_next = prox(u_prev - diffusion).
- * ut_out (nullable) receives u~. */
+ * ut_out (nullable) receives u~.  (orc_stage_mode with ORC_IDIV.) */
 void orc_stage(const double* u_prev, const double* f, int H, int W, int t,
                const double* k, const double* w, const double* lam,
                int nk, int ks, int nrbf, double mu0, double delta, double gamma,
                double* u_next, double* ut_out);
 
-/* T stages from u_0 = f; u_all receives u_0..u_T, [T+1][H][W]. */
+/* T stages from u_0 = f; u_all receives u_0..u_T, [T+1][H][W].  (ORC_IDIV.) */
 void orc_forward(const double* f, int H, int W, int T,
                  const double* k, const double* w, const double* lam,
                  int nk, int ks, int nrbf, double mu0, double delta, double gamma,
@@ -79,7 +108,7 @@ void orc_forward(const double* f, int H, int W, int T,
 
 /* Gradients of a loss L given e_T = dL/du_T (one image), by Eq. iterstep.
  * Outputs are overwritten: e_0 = dL/du_0 [H][W] (nullable), gk [T][nk][ks][ks],
- * gw [T][nk][nrbf], glam [T].  Requires lam_t > 0. */
+ * gw [T][nk][nrbf], glam [T].  Requires lam_t > 0.  (ORC_IDIV.) */
 void orc_backward(const double* f, int H, int W, int T,
                   const double* k, const double* w, const double* lam,
                   int nk, int ks, int nrbf, double mu0, double delta, double gamma,

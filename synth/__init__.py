@@ -79,6 +79,8 @@ class Params:
     mu0: float = RBF_MU0
     delta: float = RBF_DELTA
     gamma: float = RBF_GAMMA
+    dterm: int = 0          # data term: 0 despeckling prox, 1 Gaussian, 2 projection
+    proj_c: float = 1.0     # floor of the projection variant
 
     @property
     def T(self) -> int:
@@ -98,7 +100,8 @@ class Params:
 
     def astype(self, dt) -> "Params":
         return Params(self.filters.astype(dt), self.rbf_w.astype(dt),
-                      self.lam.astype(dt), self.mu0, self.delta, self.gamma)
+                      self.lam.astype(dt), self.mu0, self.delta, self.gamma, self.dterm,
+                      self.proj_c)
 
 
 def params(T: int, ks: int, nk: int, seed: int, nrbf: int = RBF_N,

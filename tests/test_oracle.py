@@ -373,3 +373,128 @@ def test_gradients_match_finite_differences():
 
         fd = (4.0 * central(h / 2) - central(h)) / 3.0
         assert e0[y, x] == pytest.approx(fd, rel=1e-6, abs=1e-6 * np.abs(e0).max())
+
+
+# --------------------------------------------------------------------------
+# the other data terms: TNRD's Gaussian-denoising reaction (Sec. 2.2.1) and the
+# explicit despeckling step with projection (Eq. diffusion_backP)
+# --------------------------------------------------------------------------
+
+def _energy_with_data(uu, p, f, mode):
+    """E(u) = sum_i sum_p rho_i((K_i u)_p) + D(u) (Eq. foemodel), rho_i the erf
+    penalty whose derivative is phi_i, D = lam/2 |u - f|^2 (Gaussian) or
+    lam <log u + f^2 / (2 u^2), 1> (the data term whose gradient Eq.
+    diffusion_backP subtracts)."""
+    k, w, lam = p.filters[0], p.rbf_w[0], p.lam[0]
+    mu = MU0 + DELTA * np.arange(p.nrbf)
+    e = 0.0
+    for i in range(p.nk):
+        z = oracle.conv(uu, k[i])[..., None]
+        e += np.sum(w[i] * GAMMA * np.sqrt(np.pi / 2)
+                    * scipy.special.erf((z - mu) / (np.sqrt(2) * GAMMA)))
+    if mode == 1:
+        e += 0.5 * lam * np.sum((uu - f) ** 2)
+    else:
+        e += lam * np.sum(np.log(uu) + f ** 2 / (2 * uu ** 2))
+    return e
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_explicit_stage_is_gradient_step_of_its_energy(mode):
+    """u~ = u - grad E(u) with E's gradient by central differences, border
+    pixels included; the Gaussian stage returns u~ itself."""
+    p = _small_model(T=1, ks=5, nk=3, seed=31)
+    p.dterm = mode
+    H, W = 9, 11
+    u = synth.random_field((H, W), 32, 40, 220)
+    f = synth.random_field((H, W), 33, 30, 250)
+    un, ut = oracle.stage(u, f, p, 0)
+    h = 1e-3
+    for (y, x) in [(0, 0), (0, 5), (1, 1), (4, 5), (8, 10), (8, 0), (3, 10), (2, 2)]:
+        up, um = u.copy(), u.copy()
+        up[y, x] += h
+        um[y, x] -= h
+        fd = (_energy_with_data(up, p, f, mode) - _energy_with_data(um, p, f, mode)) / (2 * h)
+        assert u[y, x] - ut[y, x] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+    if mode == 1:
+        np.testing.assert_array_equal(un, ut)
+
+
+def test_projection_floors_at_c():
+    """Eq. diffusion_backP: u_t = max(u~, c); pixels driven below c stop at c."""
+    p = _small_model(T=1, ks=3, nk=4, seed=34)
+    p.dterm, p.proj_c = 2, 1.0
+    p.rbf_w *= 40.0                                    # a strong diffusion force
+    H, W = 12, 12
+    u = synth.random_field((H, W), 35, 0.5, 30)
+    f = synth.random_field((H, W), 36, 0.5, 30)
+    un, ut = oracle.stage(u, f, p, 0)
+    below = ut < p.proj_c
+    assert below.any() and (~below).any()
+    np.testing.assert_array_equal(un[below], p.proj_c)
+    np.testing.assert_array_equal(un[~below], ut[~below])
+    # the floor moves with c
+    p.proj_c = 5.0
+    un5, ut5 = oracle.stage(u, f, p, 0)
+    np.testing.assert_array_equal(ut5, ut)
+    assert un5.min() == 5.0
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_explicit_modes_gradients_match_finite_differences(mode):
+    """Every filter, RBF weight and lambda gradient and input-pixel gradients of
+    the Gaussian and projection cascades (T = 2, 3x3x4, 24x24) against
+    Richardson-extrapolated central differences.  Intensities are shifted to
+    >= 20 so that no pixel sits at the projection's kink."""
+    p = _small_model(T=2, ks=3, nk=4, seed=37)
+    p.rbf_w *= 3.0
+    p.dterm = mode
+    p.lam = np.array([0.05, 0.1]) if mode == 1 else np.array([2.0, 3.0])
+    clean, f = synth.single_image(24, 24, 8, cfg=94)
+    clean, f = clean + 20.0, f + 20.0
+    u_all = oracle.forward(f, p)
+    for t in range(p.T):
+        _, ut = oracle.stage(u_all[t], f, p, t)
+        assert np.abs(ut - p.proj_c).min() > 1.0
+    eT = u_all[-1] - clean
+    e0, gk, gw, gl = oracle.backward(f, p, u_all, eT)
+    gscale = {"k": np.abs(gk).max(), "w": np.abs(gw).max(), "lam": np.abs(gl).max()}
+
+    def check(arr, grad, hrel, name, idx_list):
+        for idx in idx_list:
+            old = arr[idx]
+            h = hrel * max(1.0, abs(old))
+
+            def central(hh):
+                arr[idx] = old + hh
+                lp = _loss(f, p, clean)
+                arr[idx] = old - hh
+                lm = _loss(f, p, clean)
+                arr[idx] = old
+                return (lp - lm) / (2 * hh)
+
+            fd = (4.0 * central(h / 2) - central(h)) / 3.0
+            assert abs(grad[idx] - fd) <= 1e-6 * max(abs(fd), 1e-3 * gscale[name]), \
+                (name, idx, grad[idx], fd)
+
+    check(p.filters, gk, 1e-4, "k", list(np.ndindex(p.filters.shape)))
+    check(p.rbf_w, gw, 1e-2, "w", list(np.ndindex(p.rbf_w.shape))[::3])
+    check(p.lam, gl, 1e-4, "lam", list(np.ndindex(p.lam.shape)))
+
+    def loss_u0(u0):
+        u = u0
+        for t in range(p.T):
+            u, _ = oracle.stage(u, f, p, t)
+        return 0.5 * np.sum((u - clean) ** 2)
+
+    for (y, x) in [(0, 0), (0, 23), (23, 0), (23, 23), (0, 11), (12, 12), (5, 17)]:
+        h = 1e-4 * max(1.0, abs(f[y, x]))
+
+        def central(hh):
+            up, um = f.copy(), f.copy()
+            up[y, x] += hh
+            um[y, x] -= hh
+            return (loss_u0(up) - loss_u0(um)) / (2 * hh)
+
+        fd = (4.0 * central(h / 2) - central(h)) / 3.0
+        assert e0[y, x] == pytest.approx(fd, rel=1e-6, abs=1e-6 * np.abs(e0).max())
