@@ -9,13 +9,16 @@ collective on the data path): weak scaling.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload fwd512|fwd512_unfused|small128|batched|train|
-                              fit|mixed_tf32|mixed_bf16|mixed_fp32]
+                              fit|fwd512_gauss|fwd512_proj|mixed_tf32|
+                              mixed_bf16|mixed_fp32]
 
 The other workloads (one GPU) measure the rest of the table with the same
 contract: fwd512_unfused (three kernels per stage), small128 (1 x 128^2,
 5x5x24), batched (64 images of 256-1024 px per side, four parameter sets, one
 persistent launch per step), train (32 x 180^2 crops, forward + backward),
-fit (one Adam iteration of joint training on the same crops),
+fit (one Adam iteration of joint training on the same crops), fwd512_gauss /
+fwd512_proj (the 512^2 forward with TNRD's Gaussian-denoising reaction term on
+sigma = 25 noise, and with the explicit step plus projection),
 mixed_tf32 / mixed_bf16 / mixed_fp32 (16 x 2048^2, L = 2, T = 8, tensor-core
 TF32 and BF16 vs plain FP32; the line adds the path's error against the FP64
 oracle).
@@ -206,7 +209,8 @@ def _rows_rate(fn, rows0, target_s, max_rows):
 
 
 class Fwd(Workload):
-    def __init__(self, dev, H=512, W=512, ks=KS, nk=NK, T_=T, algo="fused", cfg=CFG_ID):
+    def __init__(self, dev, H=512, W=512, ks=KS, nk=NK, T_=T, algo="fused", cfg=CFG_ID,
+                 data_term=0):
         super().__init__(dev)
         import numpy as np
         import torch
@@ -214,9 +218,17 @@ class Fwd(Workload):
         from paper_1702_07482_gb300 import binding, ops
         self.Hh, self.Ww, self.T = H, W, T_
         self.p = _p32(synth.params(T_, ks, nk, seed=synth.seed_for(cfg, 0, "params")))
-        _, f = synth.single_image(H, W, L, cfg, index=0)
+        self.p.dterm = data_term
+        if data_term == 1:
+            # TNRD Gaussian denoising: additive N(0, 25^2) noise, small reaction weights
+            self.p.lam = 0.1 * np.arange(1, T_ + 1, dtype=np.float64)
+            clean = synth.clean_image(H, W, synth.seed_for(cfg, 0, "image"))
+            f = synth.gaussian_noise(clean, 25.0, synth.seed_for(cfg, 0, "noise"))
+        else:
+            _, f = synth.single_image(H, W, L, cfg, index=0)
         self.f = f.astype(np.float32).astype(np.float64)
-        m = ops.Model.create(self.p.filters, self.p.rbf_w, self.p.lam, device=dev)
+        m = ops.Model.create(self.p.filters, self.p.rbf_w, self.p.lam, device=dev,
+                             data_term=data_term, proj_c=1.0)
         self.prm = m.params()
         self.model = m
         self.P = ops.pitch_for(W)
@@ -236,12 +248,17 @@ class Fwd(Workload):
         self.flops_per_px_stage = fl
         self.kernel = binding.tnrd_forward_kernel(self.prm, 1, H, W, self.algo)
         self.h2d = self.d2h = int(self.f_host.numel() * 4)
-        self.traffic = _measured_traffic(self.kernel) if (algo == "fused" and H == 512) else None
+        self.traffic = (_measured_traffic(self.kernel)
+                        if (algo == "fused" and H == 512 and data_term == 0) else None)
+        noise = {0: f"L={L}", 1: "Gaussian sigma=25", 2: f"L={L}"}[data_term]
+        dterm = {0: "", 1: ", TNRD Gaussian-denoising reaction (Sec. 2.2.1)",
+                 2: ", explicit step with projection max(u, 1) (Eq. diffusion_backP)"}[data_term]
         self.config = {"workload": f"TRDMD forward, 1 x {H}x{W} per GPU, {ks}x{ks}x{nk}, 63 RBF, "
-                                   f"T={T_}, L={L}, {algo} FP32 stage kernel" +
-                                   ("" if algo == "fused" else "s"),
+                                   f"T={T_}, {noise}, {algo} FP32 stage kernel" +
+                                   ("" if algo == "fused" else "s") + dterm,
                        "H": H, "W": W, "images_per_gpu": 1, "ksize": ks, "nfilt": nk,
-                       "nrbf": 63, "T": T_, "looks": L,
+                       "nrbf": 63, "T": T_, "looks": L if data_term != 1 else None,
+                       "data_term": ["idiv", "gauss", "proj"][data_term],
                        "l2": "flushed between steps (256 MiB write outside the events)"}
 
     def step(self):
@@ -546,6 +563,10 @@ def make_workload(name, dev):
         return Fwd(dev)
     if name == "fwd512_unfused":
         return Fwd(dev, algo="unfused")
+    if name == "fwd512_gauss":
+        return Fwd(dev, data_term=1)
+    if name == "fwd512_proj":
+        return Fwd(dev, data_term=2)
     if name == "small128":
         return Fwd(dev, H=128, W=128, ks=5, nk=24, cfg=1)
     if name == "batched":
@@ -709,7 +730,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fwd512",
                     choices=["fwd512", "fwd512_unfused", "small128", "batched", "train",
-                             "fit", "mixed_tf32", "mixed_bf16", "mixed_fp32"])
+                             "fit", "fwd512_gauss", "fwd512_proj", "mixed_tf32", "mixed_bf16",
+                             "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

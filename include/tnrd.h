@@ -70,6 +70,22 @@ typedef enum {
     TNRD_ALGO_TC_BF16 = 3
 } tnrd_algo;
 
+/* Data term (reaction force) of every stage of a model.  With
+ * u~ = u_{t-1} - sum_i K_i^T phi_i(K_i u_{t-1}):
+ *   TNRD_DATA_IDIV  despeckling (Eq. diffusionprocessfinal): u_t = prox of
+ *                   G = lam <u^2 - 2 f^2 log u, 1> at u~ (Eq. subproblemGIdiv);
+ *   TNRD_DATA_GAUSS TNRD Gaussian denoising (Sec. 2.2.1, G = 0, A = I):
+ *                   u_t = u~ - lam (u_{t-1} - f);
+ *   TNRD_DATA_PROJ  explicit despeckling step with projection (Eq.
+ *                   diffusion_backP): u_t = max(u~ - (lam / u_{t-1})
+ *                   (1 - f^2 / u_{t-1}^2), proj_c); requires f > 0.
+ * A zero-initialised tnrd_params selects TNRD_DATA_IDIV. */
+typedef enum {
+    TNRD_DATA_IDIV = 0,
+    TNRD_DATA_GAUSS = 1,
+    TNRD_DATA_PROJ = 2
+} tnrd_data_term;
+
 /* Parameters of a T-stage model (Sec. 3.2: Theta_t = {lam_t, phi_i^t, k_i^t}). */
 typedef struct {
     int T;                  /* number of stages, >= 1                              */
@@ -82,6 +98,8 @@ typedef struct {
     const float* filters;   /* device [T][nfilt][ksize][ksize], k[a][b] row-major  */
     const float* rbf_w;     /* device [T][nfilt][nrbf]                             */
     const float* lambda;    /* device [T], lam_t >= 0 (> 0 for tnrd_backward)      */
+    int data_term;          /* tnrd_data_term; 0 (despeckling prox) when zeroed     */
+    float proj_c;           /* projection floor c > 0 of TNRD_DATA_PROJ (paper: 1)  */
 } tnrd_params;
 
 typedef enum { TNRD_OP_FORWARD = 0, TNRD_OP_BACKWARD = 1 } tnrd_op;

@@ -43,7 +43,12 @@ class tnrd_params(ctypes.Structure):
                 ("nrbf", ctypes.c_int), ("rbf_mu0", ctypes.c_float),
                 ("rbf_delta", ctypes.c_float), ("rbf_gamma", ctypes.c_float),
                 ("filters", ctypes.c_void_p), ("rbf_w", ctypes.c_void_p),
-                ("lambda_", ctypes.c_void_p)]
+                ("lambda_", ctypes.c_void_p), ("data_term", ctypes.c_int),
+                ("proj_c", ctypes.c_float)]
+
+
+# tnrd_data_term
+DATA_TERM = {"idiv": 0, "gauss": 1, "proj": 2}
 
 
 class tnrd_image(ctypes.Structure):
@@ -125,6 +130,8 @@ def make_params(model) -> tnrd_params:
     p.filters = model.filters.data_ptr()
     p.rbf_w = model.rbf_w.data_ptr()
     p.lambda_ = model.lam.data_ptr()
+    p.data_term = int(getattr(model, "data_term", 0))
+    p.proj_c = float(getattr(model, "proj_c", 1.0))
     return p
 
 

@@ -71,6 +71,11 @@ tnrd_status check_params(const tnrd_params* p)
                     "(delta = %g, gamma = %g)", p->rbf_delta, p->rbf_gamma);
     if (!p->filters || !p->rbf_w || !p->lambda)
         return fail(TNRD_ERR_INVALID_ARG, "null parameter array");
+    if (p->data_term != TNRD_DATA_IDIV && p->data_term != TNRD_DATA_GAUSS &&
+        p->data_term != TNRD_DATA_PROJ)
+        return fail(TNRD_ERR_INVALID_ARG, "data_term = %d is not a tnrd_data_term", p->data_term);
+    if (p->data_term == TNRD_DATA_PROJ && !(p->proj_c > 0.0f && std::isfinite(p->proj_c)))
+        return fail(TNRD_ERR_INVALID_ARG, "proj_c = %g must be a positive number", p->proj_c);
     return TNRD_OK;
 }
 
@@ -223,7 +228,7 @@ FwdLayout fwd_layout(const tnrd_params* p, int N, int H, int pitch, int keep, tn
 }
 
 struct BwdLayout {
-    size_t d = 0, e0 = 0, e1 = 0, c = 0, v = 0, pw = 0, pk = 0, pl = 0, total = 0;
+    size_t d = 0, did = 0, e0 = 0, e1 = 0, c = 0, v = 0, pw = 0, pk = 0, pl = 0, total = 0;
     int zb_tiles_x = 0, zb_tiles_y = 0, tiles_x = 0, tiles_y = 0, dk_tiles_x = 0,
         dk_tiles_y = 0, prep_blocks = 0;
 };
@@ -243,6 +248,7 @@ BwdLayout bwd_layout(const tnrd_params* p, int N, int H, int W, int pitch)
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
     L.d = take(batch);
+    if (p->data_term != TNRD_DATA_IDIV) L.did = take(batch);
     L.e0 = take(batch);
     L.e1 = take(batch);
     L.c = take(batch * (size_t)p->nfilt);
@@ -384,6 +390,8 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.w = wt;
             a.lam = p->lambda + t;
             a.nrbf = p->nrbf;
+            a.dterm = p->data_term;
+            a.proj_c = p->proj_c;
             a.rc = rc;
             e = fc.pair ? tnrd::launch_pair_fwd(ks, nk, fc.th, fc.nsplit, a, N, stream)
                         : tnrd::launch_fused_fwd(ks, nk, fc.th, a, N, stream);
@@ -403,6 +411,8 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.w = wt;
             a.lam = p->lambda + t;
             a.nrbf = p->nrbf;
+            a.dterm = p->data_term;
+            a.proj_c = p->proj_c;
             a.rc = rc;
             e = tnrd::launch_tc_fwd(ks, nk, tc_nb, algo == TNRD_ALGO_TC_BF16, a, N, stream);
         } else {
@@ -421,6 +431,8 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.w = wt;
             a.lam = p->lambda + t;
             a.nrbf = p->nrbf;
+            a.dterm = p->data_term;
+            a.proj_c = p->proj_c;
             a.rc = rc;
             e = tnrd::launch_unfused_fwd(ks, a, N, stream);
         }
@@ -466,6 +478,7 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
     tnrd::BwdArgs a{};
     a.f = f;
     a.d = (float*)(ws + L.d);
+    a.d_id = (p->data_term != TNRD_DATA_IDIV) ? (float*)(ws + L.did) : a.d;
     a.cpl = (float*)(ws + L.c);
     a.vpl = (float*)(ws + L.v);
     a.part_w = (float*)(ws + L.pw);
@@ -484,6 +497,8 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
     a.prep_blocks = L.prep_blocks;
     a.nfilt = nk;
     a.nrbf = nrbf;
+    a.dterm = p->data_term;
+    a.proj_c = p->proj_c;
     a.rc = make_rbf(p);
 
     for (int t = T - 1; t >= 0; --t) {
@@ -671,6 +686,8 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
         bs[s].k = sets[s].filters;
         bs[s].w = sets[s].rbf_w;
         bs[s].lam = sets[s].lambda;
+        bs[s].dterm = sets[s].data_term;
+        bs[s].proj_c = sets[s].proj_c;
         bs[s].rc = make_rbf(&sets[s]);
     }
     const long long limit = 2000000000LL;

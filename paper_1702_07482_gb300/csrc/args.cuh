@@ -16,6 +16,8 @@ struct StageArgs {
     const float* w;        // [nfilt][nrbf] of this stage
     const float* lam;      // &lambda[t]
     int nrbf;
+    int dterm;             // tnrd_data_term of the model
+    float proj_c;          // projection floor (dterm 2)
     RbfConst rc;
 };
 
@@ -30,6 +32,8 @@ struct TileJob {
     const float* w;
     const float* lam;
     int nrbf;
+    int dterm;
+    float proj_c;
     const RbfConst* rc;
 };
 
@@ -98,6 +102,8 @@ struct UnfArgs {
     const float* w;        // [nfilt][nrbf]
     const float* lam;
     int nrbf;
+    int dterm;
+    float proj_c;
     RbfConst rc;
 };
 
@@ -117,7 +123,8 @@ struct BwdArgs {
     const float* u_cur;    // u_t       [N][H][pitch]
     const float* f;        //           [N][H][pitch]
     const float* e_cur;    // dL/du_t   [N][H][pitch]
-    float* d;              // y .* e    [N][H][pitch]
+    float* d;              // s .* e    [N][H][pitch] (s = du_t/du~; y for dterm 0)
+    float* d_id;           // (1 - psi') d [N][H][pitch]: identity path (dterm != 0)
     float* e_prev;         // dL/du_{t-1} [N][H][pitch]
     float* cpl;            // c planes  [N][nfilt][H][pitch]
     float* vpl;            // v planes  [N][nfilt][H][pitch]
@@ -134,6 +141,8 @@ struct BwdArgs {
     const float* w;
     const float* lam;
     int nfilt, nrbf;
+    int dterm;
+    float proj_c;
     RbfConst rc;
 };
 
@@ -205,6 +214,8 @@ struct BatchSet {
     const float* k;    // [T][nfilt][ks][ks]
     const float* w;    // [T][nfilt][nrbf]
     const float* lam;  // [T]
+    int dterm;         // tnrd_data_term of this parameter set
+    float proj_c;
     RbfConst rc;
 };
 

@@ -92,6 +92,8 @@ batch_persistent_fwd(const __grid_constant__ BatchArgs a)
             j.w = ps.w + (size_t)t * NK * a.nrbf;
             j.lam = ps.lam + t;
             j.nrbf = a.nrbf;
+            j.dterm = ps.dterm;
+            j.proj_c = ps.proj_c;
             j.rc = &ps.rc;
             stage_tile<KS, NK, TH>(j, smem);   // ends with a CTA barrier after the stores
             if (threadIdx.x == 0) {

@@ -22,7 +22,15 @@
 
 namespace tnrd {
 
-// grid (prep_blocks, N), 256 threads
+// grid (prep_blocks, N), 256 threads.  Per pixel, with s = du_t/du~ and psi the
+// explicit data term's reaction (zero for the prox), writes d = s e, for the
+// explicit data terms also the identity-path cotangent d_id = (1 - psi'(u)) d,
+// and sums e du_t/dlam per block:
+//   dterm 0: s = y, du_t/dlam = x (Eqs. derv2, derv4; from u_t as above);
+//   dterm 1: s = 1, psi = lam (u - f), psi' = lam, du_t/dlam = -(u - f);
+//   dterm 2: s = [u_t > c] (u_t = max(u~, c); derivative 0 at the floor),
+//            psi = lam (u - f)(u + f) / u^3, psi' = lam (3 f^2 - u^2) / u^4,
+//            du_t/dlam = -s psi / lam.
 __global__ void __launch_bounds__(256) bwd_prep(const BwdArgs a)
 {
     const int n = blockIdx.y;
@@ -33,17 +41,35 @@ __global__ void __launch_bounds__(256) bwd_prep(const BwdArgs a)
         const size_t o = (size_t)n * a.img_stride + (size_t)y * a.pitch + x;
         const float lam = __ldg(a.lam);
         const float u = a.u_cur[o], fv = a.f[o], e = a.e_cur[o];
-        const float av = fmaf(2.0f, lam, 1.0f);
-        float yv = 0.0f, xv = 0.0f;
-        if (u > 0.0f) {
-            const float f2 = fv * fv;
-            const float r = 2.0f * lam * f2 / u;
-            const float S = fmaf(av, u, r);
-            yv = u / S;
-            xv = (2.0f / av) * (f2 * fmaf(4.0f, lam, 1.0f) / S - u);
+        if (a.dterm == 0) {
+            const float av = fmaf(2.0f, lam, 1.0f);
+            float yv = 0.0f, xv = 0.0f;
+            if (u > 0.0f) {
+                const float f2 = fv * fv;
+                const float r = 2.0f * lam * f2 / u;
+                const float S = fmaf(av, u, r);
+                yv = u / S;
+                xv = (2.0f / av) * (f2 * fmaf(4.0f, lam, 1.0f) / S - u);
+            }
+            a.d[o] = yv * e;
+            xe = xv * e;
+        } else {
+            const float up = a.u_prev[o];
+            float dv, dpsi, dlam;
+            if (a.dterm == 1) {
+                dv = e;
+                dpsi = lam;
+                dlam = -(up - fv);
+            } else {
+                dv = (u > a.proj_c) ? e : 0.0f;
+                const float u2 = up * up;
+                dpsi = lam * (3.0f * fv * fv - u2) / (u2 * u2);
+                dlam = -((up - fv) * (up + fv)) / (u2 * up);
+            }
+            a.d[o] = dv;
+            a.d_id[o] = (1.0f - dpsi) * dv;
+            xe = dlam * dv;
         }
-        a.d[o] = yv * e;
-        xe = xv * e;
     }
     // deterministic block sum: warp shuffles, then warp 0 over the 8 warp sums
     __shared__ float ws[8];
@@ -313,7 +339,7 @@ bwd_adj(const __grid_constant__ BwdArgs a)
             }
         }
         const size_t o = ioff + (size_t)qy * a.pitch + qx;
-        a.e_prev[o] = a.d[o] + g;
+        a.e_prev[o] = a.d_id[o] + g;
     }
 }
 

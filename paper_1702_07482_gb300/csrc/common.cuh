@@ -240,4 +240,20 @@ __device__ __forceinline__ float prox_idiv(float ut, float f, float lam)
     return (ut >= 0.0f) ? (ut + S) / (2.0f * a) : (4.0f * lam * f2) / (S - ut);
 }
 
+// Stage output from u_{t-1} = up, the diffusion force g, f and lam, for the
+// data terms of tnrd_data_term (mode):
+//   0: prox of the I-divergence term at u~ = up - g (Eq. subproblemGIdiv);
+//   1: TNRD Gaussian denoising, u~ - lam (up - f) (Sec. 2.2.1, G = 0);
+//   2: max(u~ - psi, c), psi = (lam / up) (1 - f^2 / up^2) (Eq. diffusion_backP),
+//      written lam (up - f)(up + f) / up^3 to avoid the cancellation in 1 - f^2/up^2.
+__device__ __forceinline__ float stage_out(float up, float g, float f, float lam, int mode,
+                                           float c)
+{
+    const float ut = up - g;
+    if (mode == 0) return prox_idiv(ut, f, lam);
+    if (mode == 1) return fmaf(-lam, up - f, ut);
+    const float psi = lam * ((up - f) * (up + f)) / (up * up * up);
+    return fmaxf(ut - psi, c);
+}
+
 }  // namespace tnrd

@@ -219,7 +219,7 @@ __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
         }
         const float up = sU[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R)];
         const float fv = __ldg(j.f + (size_t)qy * j.pitch + qx);
-        j.u_out[(size_t)qy * j.pitch + qx] = prox_idiv(up - g, fv, lam);
+        j.u_out[(size_t)qy * j.pitch + qx] = stage_out(up, g, fv, lam, j.dterm, j.proj_c);
     }
     __syncthreads();
 }
@@ -245,6 +245,8 @@ fused_stage_fwd(const __grid_constant__ StageArgs a)
     j.w = a.w;
     j.lam = a.lam;
     j.nrbf = a.nrbf;
+    j.dterm = a.dterm;
+    j.proj_c = a.proj_c;
     j.rc = &a.rc;
     stage_tile<KS, NK, TH>(j, smem);
 }

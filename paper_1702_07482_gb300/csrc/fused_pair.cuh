@@ -258,7 +258,7 @@ __device__ __forceinline__ void pair_tile_epilogue(const TileJob& j, const float
         }
         const float up = sU[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R)];
         const float fv = __ldg(j.f + (size_t)qy * j.pitch + qx);
-        j.u_out[(size_t)qy * j.pitch + qx] = prox_idiv(up - g, fv, lam);
+        j.u_out[(size_t)qy * j.pitch + qx] = stage_out(up, g, fv, lam, j.dterm, j.proj_c);
     }
 }
 
@@ -280,6 +280,8 @@ __device__ __forceinline__ TileJob pair_job(const StageArgs& a, int tile)
     j.w = a.w;
     j.lam = a.lam;
     j.nrbf = a.nrbf;
+    j.dterm = a.dterm;
+    j.proj_c = a.proj_c;
     j.rc = &a.rc;
     return j;
 }

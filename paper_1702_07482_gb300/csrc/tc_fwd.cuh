@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
             }
             const float up = __ldcg(uin + (size_t)qy * a.pitch + qx);
             const float fv = __ldg(fimg + (size_t)qy * a.pitch + qx);
-            uout[(size_t)qy * a.pitch + qx] = prox_idiv(up - gsum, fv, lam);
+            uout[(size_t)qy * a.pitch + qx] = stage_out(up, gsum, fv, lam, a.dterm, a.proj_c);
         }
     } else if (tid == 0) {
         atomicExch(&g_tc_error, 4);

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) unf_prox(const UnfArgs a)
     if (p >= a.H * a.W) return;
     const int y = p / a.W, x = p - y * a.W;
     const size_t o = (size_t)n * a.img_stride + (size_t)y * a.pitch + x;
-    a.u_out[o] = prox_idiv(a.u_in[o] - a.g[o], a.f[o], __ldg(a.lam));
+    a.u_out[o] = stage_out(a.u_in[o], a.g[o], a.f[o], __ldg(a.lam), a.dterm, a.proj_c);
 }
 
 }  // namespace tnrd

@@ -18,7 +18,9 @@ class Model:
     """Parameters of a T-stage TRDMD model, held as device float32 tensors.
 
     filters [T][nfilt][ks][ks], rbf_w [T][nfilt][nrbf], lam [T] (lambda_t >= 0);
-    RBF centres mu_j = mu0 + j * delta, width gamma.
+    RBF centres mu_j = mu0 + j * delta, width gamma; data_term 0 (despeckling
+    prox), 1 (TNRD Gaussian reaction) or 2 (explicit step with projection at
+    proj_c), as tnrd_data_term.
     """
     filters: torch.Tensor
     rbf_w: torch.Tensor
@@ -26,11 +28,15 @@ class Model:
     mu0: float = -310.0
     delta: float = 10.0
     gamma: float = 10.0
+    data_term: int = 0
+    proj_c: float = 1.0
 
     @staticmethod
-    def create(filters, rbf_w, lam, mu0=-310.0, delta=10.0, gamma=10.0, device="cuda"):
+    def create(filters, rbf_w, lam, mu0=-310.0, delta=10.0, gamma=10.0, device="cuda",
+               data_term=0, proj_c=1.0):
         t = lambda a: torch.as_tensor(a, dtype=torch.float32, device=device).contiguous()
-        return Model(t(filters), t(rbf_w), t(lam), float(mu0), float(delta), float(gamma))
+        return Model(t(filters), t(rbf_w), t(lam), float(mu0), float(delta), float(gamma),
+                     int(data_term), float(proj_c))
 
     @property
     def T(self):

@@ -36,15 +36,19 @@ class Params:
     mu0: float = -310.0
     delta: float = 10.0
     gamma: float = 10.0
+    data_term: int = 0       # tnrd_data_term of the model
+    proj_c: float = 1.0
 
     @staticmethod
-    def from_model(filters, rbf_w, lam, mu0=-310.0, delta=10.0, gamma=10.0, device="cuda"):
+    def from_model(filters, rbf_w, lam, mu0=-310.0, delta=10.0, gamma=10.0, device="cuda",
+                   data_term=0, proj_c=1.0):
         t = lambda a: torch.as_tensor(a, dtype=torch.float32, device=device).clone().contiguous()
         lam_t = t(lam)
         if torch.any(lam_t <= 0):
             raise ValueError("lambda must be positive (lambda = exp(beta))")
         return Params(t(filters).requires_grad_(), t(rbf_w).requires_grad_(),
-                      lam_t.log().requires_grad_(), float(mu0), float(delta), float(gamma))
+                      lam_t.log().requires_grad_(), float(mu0), float(delta), float(gamma),
+                      int(data_term), float(proj_c))
 
     @property
     def T(self) -> int:
@@ -78,7 +82,8 @@ def cascade(p: Params, f: torch.Tensor, stages: int | None = None) -> torch.Tens
     """u_t after the first `stages` stages (all T by default), differentiable."""
     sl = slice(0, p.T if stages is None else stages)
     return autograd.trdmd(f, p.filters(sl).contiguous(), p.weights(sl).contiguous(),
-                          p.lam(sl).contiguous(), p.mu0, p.delta, p.gamma)
+                          p.lam(sl).contiguous(), p.mu0, p.delta, p.gamma, p.data_term,
+                          p.proj_c)
 
 
 def _make_opt(tensors, optimizer: str, lr: float):

@@ -63,6 +63,12 @@ def clean_image(H: int, W: int, seed: int) -> np.ndarray:
     return np.clip(img, 1.0, 255.0)
 
 
+def gaussian_noise(clean: np.ndarray, sigma: float, seed: int) -> np.ndarray:
+    """Noisy observation f = clean + n, n ~ N(0, sigma^2) i.i.d. (the Gaussian
+    denoising task of TNRD)."""
+    return clean + _rng(seed).normal(0.0, float(sigma), size=clean.shape)
+
+
 def speckle(clean: np.ndarray, L: float, seed: int) -> np.ndarray:
     """Noisy observation f = clean * n, n ~ Gamma(L, 1/L) i.i.d."""
     g = _rng(seed)

@@ -125,3 +125,21 @@ def test_forward_kernel_query_host_only():
     assert "bf16" in B.tnrd_forward_kernel(prm, 1, 64, 64, B.ALGO["bf16"])
     with pytest.raises(B.TnrdError):
         B.tnrd_forward_kernel(prm, 1, 5, 64, B.ALGO["fused"])   # H < ksize
+
+
+def test_data_term_validation_host_only():
+    """An unknown data term, or the projection without a positive floor, is
+    rejected before any launch."""
+    import synth
+    from paper_1702_07482_gb300 import binding as B
+    from paper_1702_07482_gb300 import ops
+    p = synth.params(1, 7, 48, seed=4)
+    prm = ops.Model.create(p.filters, p.rbf_w, p.lam, device="cpu").params()
+    for dt, c, ok in ((0, 0.0, True), (1, 0.0, True), (2, 1.0, True), (2, 0.0, False),
+                      (2, float("nan"), False), (3, 1.0, False), (-1, 1.0, False)):
+        prm.data_term, prm.proj_c = dt, c
+        if ok:
+            assert B.tnrd_forward_kernel(prm, 1, 20, 20, 0)
+        else:
+            with pytest.raises(B.TnrdError):
+                B.tnrd_forward_kernel(prm, 1, 20, 20, 0)
