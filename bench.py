@@ -9,8 +9,8 @@ collective on the data path): weak scaling.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload fwd512|fwd512_unfused|small128|batched|train|
-                              fit|fwd512_gauss|fwd512_proj|mixed_tf32|
-                              mixed_bf16|mixed_fp32]
+                              fit|fwd512_gauss|fwd512_proj|quality|
+                              mixed_tf32|mixed_bf16|mixed_fp32]
 
 The other workloads (one GPU) measure the rest of the table with the same
 contract: fwd512_unfused (three kernels per stage), small128 (1 x 128^2,
@@ -18,7 +18,8 @@ contract: fwd512_unfused (three kernels per stage), small128 (1 x 128^2,
 persistent launch per step), train (32 x 180^2 crops, forward + backward),
 fit (one Adam iteration of joint training on the same crops), fwd512_gauss /
 fwd512_proj (the 512^2 forward with TNRD's Gaussian-denoising reaction term on
-sigma = 25 noise, and with the explicit step plus projection),
+sigma = 25 noise, and with the explicit step plus projection), quality (the
+Sec. 4 quality indexes of 16 x 2048^2 image triplets; HBM roofline),
 mixed_tf32 / mixed_bf16 / mixed_fp32 (16 x 2048^2, L = 2, T = 8, tensor-core
 TF32 and BF16 vs plain FP32; the line adds the path's error against the FP64
 oracle).
@@ -464,6 +465,68 @@ class Fit(Train):
         self.loss_host.copy_(self.loss.detach().reshape(1), non_blocking=True)
 
 
+class Quality(Workload):
+    """Quality indexes of Sec. 4 (PSNR, MSSIM, EC, RI_M, RI_V, C) of 16 images of
+    2048 x 2048 (reference, despeckled-like result, L = 2 speckled input)."""
+
+    def __init__(self, dev, n=16, S=2048, cfg=5):
+        super().__init__(dev)
+        import numpy as np
+        import torch
+        import synth
+        from paper_1702_07482_gb300 import binding as B
+        self.n, self.S = n, S
+        hosts = [torch.empty((n, S, S), dtype=torch.float32).pin_memory() for _ in range(3)]
+        g = np.random.Generator(np.random.PCG64(synth.seed_for(cfg, 0, "params") + 9))
+        for i in range(n):
+            clean, f = synth.single_image(S, S, 2, cfg, index=i)
+            img = np.maximum(clean * (1.0 + 0.05 * g.standard_normal(clean.shape)), 0.5)
+            hosts[0][i] = torch.from_numpy(clean.astype(np.float32))
+            hosts[1][i] = torch.from_numpy(img.astype(np.float32))
+            hosts[2][i] = torch.from_numpy(f.astype(np.float32))
+            if i == 0:
+                self.sample = [h[0].numpy().astype(np.float64) for h in hosts]
+        self.hosts = hosts
+        self.devs = [h.to(dev) for h in hosts]
+        self.out = torch.empty((n, B.QUALITY_COUNT), dtype=torch.float64, device=dev)
+        self.out_host = torch.empty_like(self.out, device="cpu").pin_memory()
+        self.ws_bytes = B.tnrd_quality_workspace_size(n, S, S)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.sp = torch.cuda.current_stream(dev).cuda_stream
+        self.px = n * S * S
+        self.launches = 2
+        self.flops = 0.0
+        self.bytes_per_px = 12            # read reference, result and noisy input once
+        self.kernel = "quality_partials + quality_finish"
+        self.h2d = int(3 * n * S * S * 4)
+        self.d2h = int(self.out.numel() * 8)
+        self.config = {"workload": f"quality indexes of Sec. 4 (PSNR, MSSIM 11x11 Gaussian, "
+                                   f"Laplacian edge correlation, ratio-image mean/variance, "
+                                   f"coefficient of variation), {n} x {S}x{S}",
+                       "images": n, "H": S, "W": S,
+                       "l2": f"inputs ({self.h2d / 2 ** 20:.0f} MiB) larger than L2"}
+
+    def step(self):
+        from paper_1702_07482_gb300 import binding as B
+        B.tnrd_quality(self.devs[0], self.devs[1], self.devs[2], self.n, self.S, self.S, self.S,
+                       255.0, self.out, self.ws, self.ws_bytes, self.sp)
+
+    def e2e(self):
+        for d, h in zip(self.devs, self.hosts):
+            d.copy_(h, non_blocking=True)
+        self.step()
+        self.out_host.copy_(self.out, non_blocking=True)
+
+    def cpu_baseline(self):
+        from oracle import quality as Q
+        r = 256
+        t0 = time.perf_counter()
+        Q.indexes(*(a[:r, :r] for a in self.sample))
+        dt = time.perf_counter() - t0
+        return {"value": r * r / dt / 1e6, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+                "sample": f"all six indexes of a {r}x{r} crop of image 0 ({dt:.1f} s)"}
+
+
 class Mixed(Workload):
     """16 images of 2048 x 2048, L = 2, 7x7x48, T = 8, as one batch."""
 
@@ -563,6 +626,8 @@ def make_workload(name, dev):
         return Fwd(dev)
     if name == "fwd512_unfused":
         return Fwd(dev, algo="unfused")
+    if name == "quality":
+        return Quality(dev)
     if name == "fwd512_gauss":
         return Fwd(dev, data_term=1)
     if name == "fwd512_proj":
@@ -696,16 +761,27 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": getattr(wl, "dtype", "f32"), "data": "synthetic",
             "config": wl.config,
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
-                         "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                         "traffic": wl.traffic,
-                         "kernel": wl.kernel,
-                         "launches_per_step": wl.launches,
-                         "achieved_basis": "algorithmic flops per step / step time (the step's "
-                                           "launches run back to back on one stream)",
-                         "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x "
-                                        f"{sm_max:.0f} MHz ({src} sm_max_mhz)",
-                         "flops_per_px_stage": wl.flops_per_px_stage},
+            "roofline": ({"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
+                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
+                          "traffic": wl.traffic,
+                          "kernel": wl.kernel,
+                          "launches_per_step": wl.launches,
+                          "achieved_basis": "algorithmic flops per step / step time (the "
+                                            "step's launches run back to back on one stream)",
+                          "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x "
+                                         f"{sm_max:.0f} MHz ({src} sm_max_mhz)",
+                          "flops_per_px_stage": wl.flops_per_px_stage}
+                         if not getattr(wl, "bytes_per_px", 0) else
+                         {"bound": "hbm",
+                          "achieved": wl.px * wl.bytes_per_px / (ms / 1e3) / 1e9,
+                          "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                          "frac": wl.px * wl.bytes_per_px / (ms / 1e3) / 1e9
+                          / float(peaks.get("hbm_gbs", 6800.0)),
+                          "traffic": wl.traffic, "kernel": wl.kernel,
+                          "launches_per_step": wl.launches,
+                          "achieved_basis": f"algorithmic bytes ({wl.bytes_per_px} B/pixel) "
+                                            "per step / step time",
+                          "peak_source": f"{src} hbm_gbs"}),
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": wl.h2d,
                     "d2h_bytes_per_step": wl.d2h},
@@ -730,8 +806,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fwd512",
                     choices=["fwd512", "fwd512_unfused", "small128", "batched", "train",
-                             "fit", "fwd512_gauss", "fwd512_proj", "mixed_tf32", "mixed_bf16",
-                             "mixed_fp32"])
+                             "fit", "fwd512_gauss", "fwd512_proj", "quality", "mixed_tf32",
+                             "mixed_bf16", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -198,6 +198,28 @@ TNRD_API int tnrd_plan_tile_height(const tnrd_plan* plan);
 /* Frees the plan's device memory and graph (synchronous). */
 TNRD_API void tnrd_plan_destroy(tnrd_plan* plan);
 
+/* Quality indexes of Sec. 4 for N images of H x W (pitch in floats), FP64
+ * results in out (device, [N][TNRD_QUALITY_COUNT] doubles, in this order):
+ *   psnr    10 log10(peak^2 / mean (ref - img)^2)
+ *   mssim   mean SSIM over the 11 x 11 windows inside the image (Gaussian
+ *           weights, sigma 1.5, summing to 1; C1 = (0.01 peak)^2,
+ *           C2 = (0.03 peak)^2; windowed variance E[x^2] - mean^2); NaN when
+ *           H or W < 11
+ *   ec      correlation coefficient of the 3 x 3 Laplacians [0 1 0; 1 -4 1; 0 1 0]
+ *           of ref and img (half-sample symmetric borders)
+ *   ri_mean, ri_var   mean and population variance of the ratio image noisy / img
+ *   cv      population standard deviation over mean of img
+ * ref (nullable: psnr, mssim and ec are NaN) and img are [N][H][pitch]; noisy
+ * (nullable: ri_mean and ri_var are NaN) likewise, with img > 0 where it is
+ * given.  peak is the intensity range (255 on the [0, 255] scale).  The sums
+ * are FP64 in a fixed order (repeatable bits).  Workspace: at least
+ * tnrd_quality_workspace_size(N, H, W) bytes. */
+#define TNRD_QUALITY_COUNT 6
+TNRD_API size_t tnrd_quality_workspace_size(int N, int H, int W);
+TNRD_API tnrd_status tnrd_quality(const float* ref, const float* img, const float* noisy, int N,
+                                  int H, int W, int pitch, float peak, double* out,
+                                  void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
 /* Largest batch (N * H * pitch floats) that tnrd_forward_noalloc accepts:
  * 4 Mi floats = 16 MiB, e.g. one 2048 x 2048 image or four 1024 x 1024. */
 #define TNRD_NOALLOC_MAX_FLOATS (1u << 22)

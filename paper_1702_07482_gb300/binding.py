@@ -25,8 +25,8 @@ OP_FORWARD, OP_BACKWARD = 0, 1
 EXPORTS = ["tnrd_workspace_size", "tnrd_forward", "tnrd_backward", "tnrd_plan_create",
            "tnrd_batch_forward", "tnrd_plan_status", "tnrd_plan_set_wait_limit",
            "tnrd_plan_tile_height", "tnrd_plan_destroy",
-           "tnrd_forward_noalloc", "tnrd_forward_kernel", "tnrd_device_status", "tnrd_last_error",
-           "tnrd_version"]
+           "tnrd_forward_noalloc", "tnrd_forward_kernel", "tnrd_quality_workspace_size",
+           "tnrd_quality", "tnrd_device_status", "tnrd_last_error", "tnrd_version"]
 
 # Largest N * H * pitch (floats) tnrd_forward_noalloc accepts (TNRD_NOALLOC_MAX_FLOATS).
 NOALLOC_MAX_FLOATS = 1 << 22
@@ -95,6 +95,10 @@ def load(path: str = LIB_PATH):
         L.tnrd_forward_noalloc.argtypes = [pp, i, i, i, i, P, P, P]
         L.tnrd_forward_kernel.restype = i
         L.tnrd_forward_kernel.argtypes = [pp, i, i, i, i, ctypes.c_char_p, sz]
+        L.tnrd_quality_workspace_size.restype = sz
+        L.tnrd_quality_workspace_size.argtypes = [i, i, i]
+        L.tnrd_quality.restype = i
+        L.tnrd_quality.argtypes = [P, P, P, i, i, i, i, ctypes.c_float, P, P, sz, P]
         L.tnrd_device_status.restype = i
         L.tnrd_device_status.argtypes = []
         L.tnrd_last_error.restype = ctypes.c_char_p
@@ -206,6 +210,22 @@ def tnrd_forward_kernel(params, N: int, H: int, W: int, algo: int) -> str:
     buf = ctypes.create_string_buffer(160)
     check(load().tnrd_forward_kernel(ctypes.byref(params), N, H, W, algo, buf, len(buf)))
     return buf.value.decode()
+
+
+QUALITY_NAMES = ("psnr", "mssim", "ec", "ri_mean", "ri_var", "cv")
+QUALITY_COUNT = len(QUALITY_NAMES)   # TNRD_QUALITY_COUNT
+
+
+def tnrd_quality_workspace_size(N: int, H: int, W: int) -> int:
+    return int(load().tnrd_quality_workspace_size(N, H, W))
+
+
+def tnrd_quality(ref, img, noisy, N, H, W, pitch, peak, out, workspace, workspace_bytes,
+                 stream) -> None:
+    """Quality indexes into out (device [N][6] float64); ref / noisy may be None."""
+    check(load().tnrd_quality(_ptr(ref), _ptr(img), _ptr(noisy), N, H, W, pitch, float(peak),
+                              _ptr(out), _ptr(workspace), int(workspace_bytes),
+                              ctypes.c_void_p(stream)))
 
 
 def tnrd_device_status() -> int:

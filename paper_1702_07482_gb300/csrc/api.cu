@@ -526,6 +526,59 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Quality indexes.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+size_t tnrd_quality_workspace_size(int N, int H, int W)
+{
+    if (N < 1 || H < 1 || W < 1) return 0;
+    return sizeof(double) * (size_t)N * tnrd::quality_tiles(H, W) * tnrd::QSUMS;
+}
+
+tnrd_status tnrd_quality(const float* ref, const float* img, const float* noisy, int N, int H,
+                         int W, int pitch, float peak, double* out, void* workspace,
+                         size_t workspace_bytes, cudaStream_t stream)
+{
+    if (N < 1 || H < 1 || W < 1 || pitch < W)
+        return fail(TNRD_ERR_INVALID_ARG, "quality: N, H, W >= 1 and pitch >= W required");
+    if ((long long)H * (long long)pitch >= (1LL << 31) || N > 65535)
+        return fail(TNRD_ERR_INVALID_ARG, "quality: images too large");
+    if (!img || !out) return fail(TNRD_ERR_INVALID_ARG, "quality: null img or out");
+    if (!(peak > 0.0f) || !std::isfinite(peak))
+        return fail(TNRD_ERR_INVALID_ARG, "quality: peak must be a positive number");
+    const size_t need = tnrd_quality_workspace_size(N, H, W);
+    if (!workspace || workspace_bytes < need)
+        return fail(TNRD_ERR_WORKSPACE, "quality: workspace of %zu bytes needed", need);
+    tnrd::QualityArgs a{};
+    a.ref = ref;
+    a.img = img;
+    a.noisy = noisy;
+    a.img_stride = (long long)H * pitch;
+    a.H = H;
+    a.W = W;
+    a.pitch = pitch;
+    a.tiles_x = (W + 31) / 32;
+    a.tiles_y = (H + 31) / 32;
+    a.peak = peak;
+    a.part = (double*)workspace;
+    a.out = out;
+    double g[11], sum = 0.0;
+    for (int b = 0; b < 11; ++b) {
+        const double d = b - 5;
+        g[b] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
+        sum += g[b];
+    }
+    for (int b = 0; b < 11; ++b) a.g1[b] = (float)(g[b] / sum);
+    for (int r = 0; r < 11; ++r)
+        for (int b = 0; b < 11; ++b) a.g2[r * 11 + b] = (float)(g[r] * g[b] / (sum * sum));
+    const cudaError_t e = tnrd::launch_quality(a, N, stream);
+    return e == cudaSuccess ? TNRD_OK : cuda_fail(e, "quality launch");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // Batched forward: plans.
 // ---------------------------------------------------------------------------
 struct tnrd_plan {

@@ -187,6 +187,31 @@ struct AdjCfg {
     static constexpr size_t SMEM_BYTES = sizeof(float) * (size_t)NWARP * H_FL;
 };
 
+// Quality indexes (tnrd_quality): per-tile FP64 partial sums, then the indexes.
+enum QualitySum {
+    Q_SE = 0,      // sum (x - y)^2
+    Q_SSIM,        // sum of the SSIM of the tile's windows
+    Q_LA, Q_LB,    // sums of the Laplacians of x and y
+    Q_LAA, Q_LBB, Q_LAB,
+    Q_R, Q_RR,     // sums of f / y and its square
+    Q_SY, Q_SYY,   // sums of y and y^2
+    QSUMS
+};
+constexpr int QOUT = 6;   // psnr, mssim, ec, ri_mean, ri_var, cv
+struct QualityArgs {
+    const float* ref;      // [N][H][pitch] or null
+    const float* img;      // [N][H][pitch] despeckled
+    const float* noisy;    // [N][H][pitch] or null
+    long long img_stride;
+    int H, W, pitch;
+    int tiles_x, tiles_y;
+    float peak;
+    double* part;          // [N][tiles][QSUMS]
+    double* out;           // [N][QOUT]
+    float g1[11];          // normalised 1-D SSIM window, sigma = 1.5
+    float g2[121];         // its outer product (the 2-D window), row-major
+};
+
 // Gradient reduction: up to three (partials, rows, parameters, output) sets in
 // one launch, blockIdx.y selecting the set.
 struct RedSet {

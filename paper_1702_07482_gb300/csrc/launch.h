@@ -52,4 +52,8 @@ int bwd_tile_h(int ks);
 cudaError_t launch_bwd_stage(int ks, int nk, const BwdArgs& a, int N, cudaStream_t s);
 cudaError_t launch_bwd_reduce(const RedArgs& r, cudaStream_t s);
 
+// Quality indexes: tiles per image, and the partials + finish launches.
+int quality_tiles(int H, int W);
+cudaError_t launch_quality(const QualityArgs& a, int N, cudaStream_t s);
+
 }  // namespace tnrd

@@ -133,3 +133,27 @@ def backward(model: Model, f: torch.Tensor, u_stages: torch.Tensor, grad_uT: tor
     B.tnrd_backward(p, N, H, W, P, f, u_stages, grad_uT, g_u0, g_k, g_w, g_l,
                     B.ALGO["fused"], workspace, ws_bytes, stream)
     return g_u0, g_k, g_w, g_l
+
+
+def quality(img: torch.Tensor, ref: torch.Tensor | None = None, noisy: torch.Tensor | None = None,
+            peak: float = 255.0, W: int | None = None) -> torch.Tensor:
+    """Quality indexes of Sec. 4 (tnrd_quality) of images [N][H][W] (or pitched
+    [N][H][pitch] with W given): a float64 CUDA tensor [N][6] whose columns are
+    binding.QUALITY_NAMES (psnr, mssim, ec, ri_mean, ri_var, cv).  ref and
+    noisy are optional (their indexes are NaN without them)."""
+    if img.dim() == 2:
+        img = img.unsqueeze(0)
+        ref = None if ref is None else ref.unsqueeze(0)
+        noisy = None if noisy is None else noisy.unsqueeze(0)
+    W = img.shape[-1] if W is None else W
+    imgp = img if (W is not None and img.shape[-1] % 4 == 0) else to_pitched(img)
+    pitch = imgp.shape[-1]
+    pad = lambda t: None if t is None else (t if t.shape[-1] == pitch else to_pitched(t))
+    refp, noisyp = pad(ref), pad(noisy)
+    N, H = imgp.shape[0], imgp.shape[1]
+    out = torch.empty((N, B.QUALITY_COUNT), dtype=torch.float64, device=img.device)
+    nb = B.tnrd_quality_workspace_size(N, H, W)
+    ws = torch.empty(nb, dtype=torch.uint8, device=img.device)
+    B.tnrd_quality(refp, imgp.contiguous(), noisyp, N, H, W, pitch, peak, out, ws, nb,
+                   torch.cuda.current_stream(img.device).cuda_stream)
+    return out
