@@ -367,7 +367,8 @@ class Train(Workload):
         from paper_1702_07482_gb300 import ops
         self.T, self.n, self.S = T_, n, S
         self.p = _p32(synth.params(T_, KS, NK, seed=synth.seed_for(cfg, 0, "params")))
-        pairs = [synth.single_image(S, S, 1, cfg, index=i) for i in range(n)]
+        rank = int(os.environ.get("RANK", "0"))      # each rank its own crops (weak scaling)
+        pairs = [synth.single_image(S, S, 1, cfg, index=rank * n + i) for i in range(n)]
         self.clean = np.stack([c for c, _ in pairs]).astype(np.float32)
         self.f = np.stack([f for _, f in pairs]).astype(np.float32)
         self.m = ops.Model.create(self.p.filters, self.p.rbf_w, self.p.lam, device=dev)
@@ -433,7 +434,9 @@ class Train(Workload):
 class Fit(Train):
     """One Adam iteration of joint training (Sec. 3.2) on the training-step
     batch: forward, backward, zero-mean filter projection and the update of
-    filters, RBF weights and beta = log lambda."""
+    filters, RBF weights and beta = log lambda.  With N GPUs every rank trains
+    on its own 32 crops and the gradients are summed over the ranks (one
+    all-reduce per step): weak scaling."""
 
     def __init__(self, dev):
         super().__init__(dev)
@@ -453,9 +456,11 @@ class Fit(Train):
 
     def step(self):
         from paper_1702_07482_gb300 import train
+        from paper_1702_07482_gb300.shard import allreduce_gradients
         self.opt.zero_grad(set_to_none=False)
         self.loss = train.loss_sum(train.cascade(self.tp, self.f_img), self.c_img)
         self.loss.backward()
+        allreduce_gradients(self.tp.tensors())   # data-parallel ranks (no-op on one GPU)
         self.opt.step()
 
     def e2e(self):
@@ -695,10 +700,11 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1 and args.workload != "fwd512":
+    if world > 1 and args.workload not in ("fwd512", "fit"):
         if rank == 0:
             print(json.dumps({"workload": args.workload,
-                              "unavailable": "multi-GPU runs use the default fwd512 workload"}))
+                              "unavailable": "multi-GPU runs use the fwd512 (independent images) "
+                                             "or fit (data-parallel training) workloads"}))
         return 0
     if world > 1:
         dist.init_process_group("nccl")

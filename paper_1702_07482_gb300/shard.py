@@ -2,7 +2,10 @@
 
 The despeckling path has no exchange between images, so a multi-GPU run
 splits the batch and needs no collective on the data path; the only
-collective is the timing reduction of the benchmark.
+collective of inference is the timing reduction of the benchmark.  Data-
+parallel training (Sec. 3.2, the loss of Eq. learning summed over samples)
+has one real exchange per step: the sum of the ranks' parameter gradients
+(allreduce_gradients).
 """
 from __future__ import annotations
 
@@ -35,3 +38,24 @@ def global_rate(pixels_local: float, ms_local: float, group=None):
         dist.all_reduce(ms, op=dist.ReduceOp.MAX, group=group)
         return float(px[0]) / (float(ms[0]) / 1e3) / 1e6, float(ms[0])
     return pixels_local / (ms_local / 1e3) / 1e6, ms_local
+
+
+def allreduce_gradients(tensors, group=None) -> None:
+    """Sums the .grad of every tensor over the ranks, in place (one flat
+    all-reduce of T (N_k k^2 + N_k N_rbf + 1) values).  With each rank's loss
+    summing its own samples, the result is the gradient of the whole batch's
+    loss, identical on every rank.  No-op without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return
+    grads = [t.grad for t in tensors if t.grad is not None]
+    if not grads:
+        return
+    flat = torch.cat([g.reshape(-1) for g in grads])
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    off = 0
+    for g in grads:
+        n = g.numel()
+        g.copy_(flat[off:off + n].view_as(g))
+        off += n

@@ -16,7 +16,9 @@ optimiser loop:
 
 Optimisers: torch's Adam or L-BFGS (the paper's choice for TNRD-type models).
 Every forward and backward stage runs in libtnrd.so; torch only updates the
-few thousand parameters.
+few thousand parameters.  Under torch.distributed each rank passes its own
+crops, and the parameter gradients are summed over the ranks after every
+backward (one all-reduce), so all ranks take the same step.
 """
 from __future__ import annotations
 
@@ -25,6 +27,7 @@ import dataclasses
 import torch
 
 from . import autograd
+from .shard import allreduce_gradients
 
 
 @dataclasses.dataclass
@@ -106,6 +109,7 @@ def _run(p: Params, f, clean, stages: int, steps: int, optimizer: str, lr: float
         opt.zero_grad(set_to_none=False)
         loss = loss_sum(cascade(p, f, stages), clean)
         loss.backward()
+        allreduce_gradients(p.tensors())     # data-parallel ranks: sum of the batch's gradients
         if trainable_mask is not None:
             with torch.no_grad():
                 for g in (p.theta.grad, p.w.grad, p.beta.grad):

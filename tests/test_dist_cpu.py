@@ -3,6 +3,7 @@ whole-job rate reduction that bench.py uses with one process per GPU."""
 import os
 import socket
 
+import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -62,3 +63,53 @@ def test_two_rank_rate_uses_all_pixels_and_slowest_rank():
     for _, _, rate, ms_max in out:
         assert ms_max == 15.0
         assert rate == pytest.approx(total / 15e-3 / 1e6)
+
+
+def _grad_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    from paper_1702_07482_gb300.shard import allreduce_gradients
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # three parameter tensors shaped as one 3x3x4, T = 2 model; rank-dependent gradients
+    shapes = [(2, 4, 3, 3), (2, 4, 63), (2,)]
+    ts = []
+    for k, sh in enumerate(shapes):
+        t = torch.zeros(sh, requires_grad=True)
+        t.grad = torch.full(sh, float(rank + 1)) * (k + 1) + torch.arange(t.numel()).view(sh)
+        ts.append(t)
+    allreduce_gradients(ts)
+    q.put((rank, [t.grad.clone() for t in ts]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_gradient_allreduce_sums_and_agrees():
+    """The data-parallel exchange of training: after allreduce_gradients every
+    rank holds the sum of both ranks' gradients, bit for bit the same."""
+    import torch
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_grad_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    shapes = [(2, 4, 3, 3), (2, 4, 63), (2,)]
+    for k, sh in enumerate(shapes):
+        n = int(np.prod(sh))
+        want = (1 + 2) * (k + 1) + 2 * torch.arange(n).view(sh).float()
+        assert torch.equal(out[0][k], want) and torch.equal(out[1][k], want)
+
+
+def test_allreduce_is_noop_without_process_group():
+    import torch
+    from paper_1702_07482_gb300.shard import allreduce_gradients
+    t = torch.zeros(3, requires_grad=True)
+    t.grad = torch.tensor([1.0, 2.0, 3.0])
+    allreduce_gradients([t])
+    assert torch.equal(t.grad, torch.tensor([1.0, 2.0, 3.0]))
