@@ -61,7 +61,10 @@ __device__ __forceinline__ void gather_row(float (&vw)[KS], float v, int lane)
 // INTERIOR: the tile touches no image border, so every z of a valid step is
 // inside the image and no v needs masking (partial z rows of the first 2R
 // steps only reach h rows above the tile, which are never stored).
-template <int KS, int UP, bool INTERIOR>
+// FIRST: the group of steps 0 .. KS-1, whose first 2R steps only prime the z
+// accumulators -- their phi, shuffles and h updates would reach no stored h
+// row, so they are left out (the stored values are the same bits).
+template <int KS, int UP, bool INTERIOR, bool FIRST = false>
 __device__ __forceinline__ void walk_group(const float* __restrict__ urow, float* __restrict__ hrow,
                                            const float (&kr)[KS][KS], float (&za)[KS],
                                            float (&ha)[KS], int m0, int zrow0, int H, bool col_in,
@@ -87,6 +90,9 @@ __device__ __forceinline__ void walk_group(const float* __restrict__ urow, float
         }
         const float z = za[mm];
         za[mm] = 0.0f;
+        if constexpr (FIRST) {
+            if (mm < 2 * R) continue;
+        }
         float v = rbf_phi_tab(z, tab, rc);
         if constexpr (!INTERIOR) {
             const int zi = zrow0 + m;
@@ -176,13 +182,17 @@ __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
 #pragma unroll
         for (int s = 0; s < KS; ++s) za[s] = ha[s] = 0.0f;
         if (!border) {
+            walk_group<KS, C::UP, true, true>(urow, hrow, kr, za, ha, 0, zrow0, H, col_in, 2 * R,
+                                              4 * R, nsteps, lane, myT, rc);
 #pragma unroll 1
-            for (int m0 = 0; m0 < nsteps; m0 += KS)
+            for (int m0 = KS; m0 < nsteps; m0 += KS)
                 walk_group<KS, C::UP, true>(urow, hrow, kr, za, ha, m0, zrow0, H, col_in, 2 * R,
                                             4 * R, nsteps, lane, myT, rc);
         } else {
+            walk_group<KS, C::UP, false, true>(urow, hrow, kr, za, ha, 0, zrow0, H, col_in, 2 * R,
+                                               4 * R, nsteps, lane, myT, rc);
 #pragma unroll 1
-            for (int m0 = 0; m0 < nsteps; m0 += KS)
+            for (int m0 = KS; m0 < nsteps; m0 += KS)
                 walk_group<KS, C::UP, false>(urow, hrow, kr, za, ha, m0, zrow0, H, col_in, 2 * R,
                                              4 * R, nsteps, lane, myT, rc);
         }

@@ -73,8 +73,9 @@ __device__ __forceinline__ void gather_pair(float (&vw)[KS + 1], float v0, float
 
 // One group of KS walk steps (see walk_group of fused_stage_fwd for the
 // row bookkeeping); urow points at this lane's first u column (2j) of the
-// step-0 row, hrow at its float2 of the h row completed at step 0.
-template <int KS, int UP, bool INTERIOR>
+// step-0 row, hrow at its float2 of the h row completed at step 0.  FIRST as
+// in walk_group: the first 2R steps only prime the z accumulators.
+template <int KS, int UP, bool INTERIOR, bool FIRST = false>
 __device__ __forceinline__ void pair_group(const float* __restrict__ urow, float2* __restrict__ hrow,
                                            const float (&kr)[KS][KS], float (&za0)[KS],
                                            float (&za1)[KS], float (&ha0)[KS], float (&ha1)[KS],
@@ -107,6 +108,9 @@ __device__ __forceinline__ void pair_group(const float* __restrict__ urow, float
         const float z0 = za0[mm], z1 = za1[mm];
         za0[mm] = 0.0f;
         za1[mm] = 0.0f;
+        if constexpr (FIRST) {
+            if (mm < 2 * R) continue;
+        }
         float v0 = rbf_phi_w(z0, wp, rc);
         float v1 = rbf_phi_w(z1, wp, rc);
         if constexpr (!INTERIOR) {
@@ -196,13 +200,17 @@ __device__ __forceinline__ void pair_tile_walk(const TileJob& j, float* smem, in
 #pragma unroll
         for (int s = 0; s < KS; ++s) za0[s] = za1[s] = ha0[s] = ha1[s] = 0.0f;
         if (!border) {
+            pair_group<KS, C::UP, true, true>(urow, hrow, kr, za0, za1, ha0, ha1, 0, zrow0, H,
+                                              col_in0, col_in1, 2 * R, 4 * R, nsteps, lane, myW, rc);
 #pragma unroll 1
-            for (int m0 = 0; m0 < nsteps; m0 += KS)
+            for (int m0 = KS; m0 < nsteps; m0 += KS)
                 pair_group<KS, C::UP, true>(urow, hrow, kr, za0, za1, ha0, ha1, m0, zrow0, H,
                                             col_in0, col_in1, 2 * R, 4 * R, nsteps, lane, myW, rc);
         } else {
+            pair_group<KS, C::UP, false, true>(urow, hrow, kr, za0, za1, ha0, ha1, 0, zrow0, H,
+                                               col_in0, col_in1, 2 * R, 4 * R, nsteps, lane, myW, rc);
 #pragma unroll 1
-            for (int m0 = 0; m0 < nsteps; m0 += KS)
+            for (int m0 = KS; m0 < nsteps; m0 += KS)
                 pair_group<KS, C::UP, false>(urow, hrow, kr, za0, za1, ha0, ha1, m0, zrow0, H,
                                              col_in0, col_in1, 2 * R, 4 * R, nsteps, lane, myW, rc);
         }
