@@ -17,6 +17,7 @@
 //   y = u / S,   x = (2/a) (f^2 (1 + 4 lam) / S - u).
 // u_t = 0 happens only when f = 0 and u~ <= 0, where y = x = 0.
 #pragma once
+#include <type_traits>
 #include "args.cuh"
 #include "fused_fwd.cuh"   // shfl_rel / gather_row
 
@@ -218,8 +219,10 @@ bwd_zb(const __grid_constant__ BwdArgs a)
 
 // One group of KS walk steps of bwd_adj starting at step m0.  Step m takes c
 // row hy0 - R + m (cv[mm], this lane's column); h row hy0 - 2R + m completes
-// there and is added to the warp's buffer at hrow[m * 32].
-template <int KS>
+// there and is added to the warp's buffer at hrow[m * 32].  FIRST: the group
+// of steps 0 .. KS-1, where kernel rows a > step reach only h rows above the
+// first stored one and are left out.
+template <int KS, bool FIRST = false>
 __device__ __forceinline__ void adj_group(const float (&cv)[KS], float* __restrict__ hrow,
                                           const float (&kr)[KS][KS], float (&ha)[KS], int m0,
                                           int mh_lo, int mh_hi, int lane)
@@ -236,6 +239,7 @@ __device__ __forceinline__ void adj_group(const float (&cv)[KS], float* __restri
         for (int b = 0; b < KS; ++b) {
 #pragma unroll
             for (int q = 0; q < KS; ++q) {
+                if (FIRST && q > mm) continue;
                 const int s = (mm + 2 * R - q) % KS;
                 ha[s] = fmaf(kr[q][b], cw[b], ha[s]);
             }
@@ -301,8 +305,15 @@ bwd_adj(const __grid_constant__ BwdArgs a)
         };
         float cv[KS];
         load_group(0, cv);
+        {
+            float cn[KS];
+            load_group(1, cn);
+            adj_group<KS, true>(cv, hrow, kr, ha, 0, 2 * R, nsteps, lane);
+#pragma unroll
+            for (int mm = 0; mm < KS; ++mm) cv[mm] = cn[mm];
+        }
 #pragma unroll 1
-        for (int g = 0; g < ngroups; ++g) {
+        for (int g = 1; g < ngroups; ++g) {
             float cn[KS];
             load_group(g + 1, cn);
             adj_group<KS>(cv, hrow, kr, ha, g * KS, 2 * R, nsteps, lane);
@@ -409,8 +420,10 @@ __global__ void __launch_bounds__(128) bwd_dk(const __grid_constant__ BwdArgs a)
 #pragma unroll
         for (int s = 0; s < KS; ++s) cprev[s] = vprev[s] = 0.0f;
         load_group(0, ccur, vcur);
-#pragma unroll 1
-        for (int g = 0; g < NG; ++g) {
+        // one group of KS steps; in the first group the slots of c/v rows above
+        // the tile, in the last those below it, are zero and left out
+        auto group = [&](int g, auto first_tag, auto last_tag) {
+            constexpr bool FIRST = decltype(first_tag)::value, LAST = decltype(last_tag)::value;
             float cnext[KS], vnext[KS];
             load_group(g + 1, cnext, vnext);
 #pragma unroll
@@ -427,6 +440,8 @@ __global__ void __launch_bounds__(128) bwd_dk(const __grid_constant__ BwdArgs a)
                 for (int p = 0; p < KS; ++p) {
                     // c/v row m - 2R + p: slot mm - 2R + p of this group or the last
                     const int sl = mm - 2 * R + p;
+                    if (FIRST && sl < 0) continue;         // rows above the tile
+                    if (LAST && sl >= KS - 2 * R) continue; // rows at or below y0 + TH
                     const float cv = sl >= 0 ? ccur[sl] : cprev[sl + KS];
                     const float vv = sl >= 0 ? vcur[sl] : vprev[sl + KS];
 #pragma unroll
@@ -441,7 +456,14 @@ __global__ void __launch_bounds__(128) bwd_dk(const __grid_constant__ BwdArgs a)
                 ccur[s] = cnext[s];
                 vcur[s] = vnext[s];
             }
-        }
+        };
+        using T_ = std::true_type;
+        using F_ = std::false_type;
+        static_assert(NG >= 2, "the walk has a first and a last group");
+        group(0, T_{}, F_{});
+#pragma unroll 1
+        for (int g = 1; g < NG - 1; ++g) group(g, F_{}, F_{});
+        group(NG - 1, F_{}, T_{});
         // reduce over the 32 lanes (columns) through shared memory
 #pragma unroll
         for (int p = 0; p < KS; ++p)
