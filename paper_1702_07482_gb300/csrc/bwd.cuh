@@ -89,7 +89,9 @@ __global__ void __launch_bounds__(256) bwd_prep(const BwdArgs a)
 // One group of KS walk steps of bwd_zb starting at step m0.  Step m takes
 // u and d row y0 - R + m (shared-memory rows m); z and b of image row
 // y0 - 2R + m complete there (rolling accumulators, slot (step + a) mod KS).
-template <int KS, int UP>
+// FIRST: the group of steps 0 .. KS-1; updates of rows completing before step
+// 2R (above the tile) are left out.
+template <int KS, int UP, bool FIRST = false>
 __device__ __forceinline__ void zb_group(
     const float* __restrict__ urow, const float* __restrict__ drow, const float (&kr)[KS][KS],
     float (&za)[KS], float (&ba)[KS], int m0, int y0, int H, int TH, bool col_in, int lane,
@@ -112,6 +114,7 @@ __device__ __forceinline__ void zb_group(
         for (int b = 0; b < KS; ++b) {
 #pragma unroll
             for (int q = 0; q < KS; ++q) {
+                if (FIRST && mm + q < 2 * R) continue;
                 const int s = (mm + q) % KS;
                 za[s] = fmaf(kr[q][b], in[b], za[s]);
                 ba[s] = fmaf(kr[q][b], dn[b], ba[s]);
@@ -198,8 +201,10 @@ bwd_zb(const __grid_constant__ BwdArgs a)
         float za[KS], ba[KS];
 #pragma unroll
         for (int s = 0; s < KS; ++s) za[s] = ba[s] = 0.0f;
+        zb_group<KS, C::UP, true>(urow, drow, kr, za, ba, 0, y0, H, TH, col_in, lane, myWp,
+                                  myHist + lane, a.rc, cpl_col, vpl_col, a.pitch);
 #pragma unroll 1
-        for (int g = 0; g < C::GROUPS; ++g)
+        for (int g = 1; g < C::GROUPS; ++g)
             zb_group<KS, C::UP>(urow, drow, kr, za, ba, g * KS, y0, H, TH, col_in, lane, myWp,
                                 myHist + lane, a.rc, cpl_col, vpl_col, a.pitch);
         __syncwarp();

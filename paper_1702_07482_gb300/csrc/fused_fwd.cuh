@@ -63,7 +63,8 @@ __device__ __forceinline__ void gather_row(float (&vw)[KS], float v, int lane)
 // steps only reach h rows above the tile, which are never stored).
 // FIRST: the group of steps 0 .. KS-1, whose first 2R steps only prime the z
 // accumulators -- their phi, shuffles and h updates would reach no stored h
-// row, so they are left out (the stored values are the same bits).
+// row, and the z updates of rows completing before step 2R no used z, so they
+// are left out (the stored values are the same bits).
 template <int KS, int UP, bool INTERIOR, bool FIRST = false>
 __device__ __forceinline__ void walk_group(const float* __restrict__ urow, float* __restrict__ hrow,
                                            const float (&kr)[KS][KS], float (&za)[KS],
@@ -84,6 +85,7 @@ __device__ __forceinline__ void walk_group(const float* __restrict__ urow, float
         for (int b = 0; b < KS; ++b) {
 #pragma unroll
             for (int a = 0; a < KS; ++a) {
+                if (FIRST && mm + a < 2 * R) continue;
                 const int s = (mm + a) % KS;
                 za[s] = fmaf(kr[a][b], in[b], za[s]);
             }

@@ -100,6 +100,7 @@ __device__ __forceinline__ void pair_group(const float* __restrict__ urow, float
         for (int b = 0; b < KS; ++b) {
 #pragma unroll
             for (int a = 0; a < KS; ++a) {
+                if (FIRST && mm + a < 2 * R) continue;
                 const int s = (mm + a) % KS;
                 za0[s] = fmaf(kr[a][b], in[2 * R - b], za0[s]);
                 za1[s] = fmaf(kr[a][b], in[2 * R + 1 - b], za1[s]);
