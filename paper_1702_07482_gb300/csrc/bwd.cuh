@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) bwd_prep(const BwdArgs a)
 // 2R (above the tile) are left out.
 template <int KS, int UP, bool FIRST = false>
 __device__ __forceinline__ void zb_group(
-    const float* __restrict__ urow, const float* __restrict__ drow, const float (&kr)[KS][KS],
+    const float2* __restrict__ udrow, const float (&kr)[KS][KS],
     float (&za)[KS], float (&ba)[KS], int m0, int y0, int H, int TH, bool col_in, int lane,
     const float* __restrict__ wp, float* __restrict__ hist_lane, const RbfConst& rc,
     float* __restrict__ cpl_col, float* __restrict__ vpl_col, int pitch)
@@ -102,13 +102,13 @@ __device__ __forceinline__ void zb_group(
 #pragma unroll
     for (int mm = 0; mm < KS; ++mm) {
         const int m = m0 + mm;
-        const float* ur = urow + m * UP;
-        const float* dr = drow + m * UP;
+        const float2* udr = udrow + m * UP;
         float in[KS], dn[KS];
 #pragma unroll
         for (int b = 0; b < KS; ++b) {
-            in[b] = ur[2 * R - b];
-            dn[b] = dr[2 * R - b];
+            const float2 ud = udr[2 * R - b];   // (u, d) interleaved: one 64-bit load
+            in[b] = ud.x;
+            dn[b] = ud.y;
         }
 #pragma unroll
         for (int b = 0; b < KS; ++b) {
@@ -154,10 +154,9 @@ bwd_zb(const __grid_constant__ BwdArgs a)
     using C = ZbCfg<KS, NK, TH>;
     constexpr int R = C::R;
     extern __shared__ __align__(16) float smem[];
-    float* sU = smem;
-    float* sD = sU + C::U_FL;
+    float2* sUD = reinterpret_cast<float2*>(smem);   // (u_{t-1}, d) interleaved
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* myHist = sD + C::U_FL + warp * C::PW_FL;
+    float* myHist = smem + 2 * C::U_FL + warp * C::PW_FL;
     float* myK = myHist + C::HIST_FL;
     float* myWp = myK + C::KPAD;
 
@@ -171,8 +170,7 @@ bwd_zb(const __grid_constant__ BwdArgs a)
         const int i = idx / C::UW, j = idx - i * C::UW;
         const int yy = sym_idx(y0 - R + i, H), xx = sym_idx(x0 - R + j, W);
         const size_t o = ioff + (size_t)yy * a.pitch + xx;
-        sU[idx] = a.u_prev[o];
-        sD[idx] = a.d[o];
+        sUD[idx] = make_float2(a.u_prev[o], a.d[o]);
     }
     for (int e = lane; e < C::HIST_FL; e += 32) myHist[e] = 0.0f;
     for (int e = lane; e < C::WPADN; e += 32) myWp[e] = 0.0f;
@@ -180,8 +178,7 @@ bwd_zb(const __grid_constant__ BwdArgs a)
 
     const int x = x0 + lane;
     const bool col_in = x < W;
-    const float* urow = sU + lane;
-    const float* drow = sD + lane;
+    const float2* udrow = sUD + lane;
     const int cta = n * (a.zb_tiles_x * a.zb_tiles_y) + blockIdx.x;
 
 #pragma unroll 1
@@ -201,11 +198,11 @@ bwd_zb(const __grid_constant__ BwdArgs a)
         float za[KS], ba[KS];
 #pragma unroll
         for (int s = 0; s < KS; ++s) za[s] = ba[s] = 0.0f;
-        zb_group<KS, C::UP, true>(urow, drow, kr, za, ba, 0, y0, H, TH, col_in, lane, myWp,
+        zb_group<KS, C::UP, true>(udrow, kr, za, ba, 0, y0, H, TH, col_in, lane, myWp,
                                   myHist + lane, a.rc, cpl_col, vpl_col, a.pitch);
 #pragma unroll 1
         for (int g = 1; g < C::GROUPS; ++g)
-            zb_group<KS, C::UP>(urow, drow, kr, za, ba, g * KS, y0, H, TH, col_in, lane, myWp,
+            zb_group<KS, C::UP>(udrow, kr, za, ba, g * KS, y0, H, TH, col_in, lane, myWp,
                                 myHist + lane, a.rc, cpl_col, vpl_col, a.pitch);
         __syncwarp();
         // per-tile dL/dw_i: sum the lanes' bins (skewed reads avoid bank conflicts)
@@ -380,8 +377,7 @@ __global__ void __launch_bounds__(128) bwd_dk(const __grid_constant__ BwdArgs a)
     static_assert(STEPS % KS == 0, "the walk must end on a whole group");
     constexpr int NG = STEPS / KS;
     constexpr int UWD = 32 + 2 * R;
-    __shared__ float sU[STEPS * UWD];
-    __shared__ float sD[STEPS * UWD];
+    __shared__ float2 sUD[STEPS * UWD];   // (u_{t-1}, d) interleaved
     __shared__ float sRed[NW][KS * KS][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = blockIdx.y;
@@ -393,8 +389,7 @@ __global__ void __launch_bounds__(128) bwd_dk(const __grid_constant__ BwdArgs a)
         const int i = idx / UWD, j = idx - i * UWD;
         const int yy = sym_idx(y0 - R + i, H), xx = sym_idx(x0 - R + j, W);
         const size_t o = ioff + (size_t)yy * a.pitch + xx;
-        sU[idx] = a.u_prev[o];
-        sD[idx] = a.d[o];
+        sUD[idx] = make_float2(a.u_prev[o], a.d[o]);
     }
     __syncthreads();
     const int x = x0 + lane;
@@ -433,13 +428,13 @@ __global__ void __launch_bounds__(128) bwd_dk(const __grid_constant__ BwdArgs a)
             load_group(g + 1, cnext, vnext);
 #pragma unroll
             for (int mm = 0; mm < KS; ++mm) {
-                const float* ur = sU + (g * KS + mm) * UWD + lane;
-                const float* dr = sD + (g * KS + mm) * UWD + lane;
+                const float2* udr = sUD + (g * KS + mm) * UWD + lane;
                 float in[KS], dn[KS];
 #pragma unroll
                 for (int b = 0; b < KS; ++b) {
-                    in[b] = ur[2 * R - b];
-                    dn[b] = dr[2 * R - b];
+                    const float2 ud = udr[2 * R - b];
+                    in[b] = ud.x;
+                    dn[b] = ud.y;
                 }
 #pragma unroll
                 for (int p = 0; p < KS; ++p) {
