@@ -38,9 +38,12 @@ def _images(region, N, H, P):
     return region.view(N, H, P)
 
 
-@pytest.mark.parametrize("algo", ["fused", "unfused", "tf32"])
+@pytest.mark.parametrize("algo", ["fused", "lane", "pair", "pair2", "unfused", "tf32", "bf16"])
 @pytest.mark.parametrize("keep", [0, 1])
-def test_forward_writes_only_its_output(algo, keep):
+def test_forward_writes_only_its_output(algo, keep, monkeypatch):
+    if algo in ("lane", "pair", "pair2"):
+        monkeypatch.setenv("TNRD_FUSED_KERNEL", algo)
+        algo = "fused"
     from paper_1702_07482_gb300 import binding as B
     from paper_1702_07482_gb300 import ops
     H, W, P, N, T = 45, 37, 44, 2, 3
@@ -69,12 +72,13 @@ def test_forward_writes_only_its_output(algo, keep):
     assert np.all(fi[..., W:] == np.float32(CANARY)), "input padding modified"
 
 
-def test_backward_writes_only_its_outputs():
+@pytest.mark.parametrize("dterm", [0, 1, 2])
+def test_backward_writes_only_its_outputs(dterm):
     from paper_1702_07482_gb300 import binding as B
     from paper_1702_07482_gb300 import ops
     H, W, P, N, T = 40, 33, 36, 2, 2
     p, f = case(H, W, 7, 48, T, N=N, cfg=201)
-    m = ops.Model.create(p.filters, p.rbf_w, p.lam)
+    m = ops.Model.create(p.filters, p.rbf_w, p.lam, data_term=dterm, proj_c=1.0)
     fp = torch.full((N, H, P), CANARY, device="cuda")
     fp[:, :, :W] = torch.tensor(f, dtype=torch.float32, device="cuda")
     u_all = ops.forward(m, fp, keep_stages=True, W=W)
@@ -132,3 +136,26 @@ def test_batch_and_noalloc_write_only_their_outputs():
     torch.cuda.synchronize()
     _check_slabs(ub2, n)
     assert np.all(ur2.view(H, P).cpu().numpy()[:, W:] == np.float32(CANARY))
+
+
+def test_quality_writes_only_its_output():
+    from paper_1702_07482_gb300 import binding as B
+    H, W, P, N = 45, 37, 40, 2
+    imgs = []
+    for k in range(3):
+        buf, reg = _guarded(N * H * P)
+        v = reg.view(N, H, P)
+        v[:, :, :W] = torch.rand((N, H, W), device="cuda") * 200 + 10
+        imgs.append((buf, reg))
+    obuf, oreg = _guarded(2 * N * 6)           # N x 6 doubles = 2 N 6 floats
+    nb = B.tnrd_quality_workspace_size(N, H, W)
+    wbuf, wreg = _guarded((nb + 3) // 4)
+    B.tnrd_quality(imgs[0][1], imgs[1][1], imgs[2][1], N, H, W, P, 255.0, oreg, wreg, nb,
+                   torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    _check_slabs(obuf, 2 * N * 6)
+    _check_slabs(wbuf, (nb + 3) // 4)
+    for buf, reg in imgs:
+        _check_slabs(buf, N * H * P)
+        assert np.all(reg.view(N, H, P).cpu().numpy()[..., W:] == np.float32(CANARY))
+    assert np.all(np.isfinite(oreg.view(torch.float64).cpu().numpy()))
