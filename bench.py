@@ -8,14 +8,17 @@ GPUs (torchrun), every rank runs its own image (independent problems, no
 collective on the data path): weak scaling.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fwd512|fwd512_unfused|small128|batched|train|
+                  [--workload fwd512|fwd512_unfused|small128|batched|batched_tf32|
+                              batched_bf16|train|
                               fit|fwd512_gauss|fwd512_proj|quality|
                               mixed_tf32|mixed_bf16|mixed_fp32]
 
 The other workloads (one GPU) measure the rest of the table with the same
 contract: fwd512_unfused (three kernels per stage), small128 (1 x 128^2,
 5x5x24), batched (64 images of 256-1024 px per side, four parameter sets, one
-persistent launch per step), train (32 x 180^2 crops, forward + backward),
+persistent launch per step; batched_tf32 / batched_bf16 the same batch with the
+tensor-core stage, one launch per stage), train (32 x 180^2 crops, forward +
+backward),
 fit (one Adam iteration of joint training on the same crops), fwd512_gauss /
 fwd512_proj (the 512^2 forward with TNRD's Gaussian-denoising reaction term on
 sigma = 25 noise, and with the explicit step plus projection), quality (the
@@ -284,7 +287,7 @@ class Fwd(Workload):
 
 
 class Batched(Workload):
-    def __init__(self, dev, n=64, lo=256, hi=1024, T_=T, cfg=3):
+    def __init__(self, dev, n=64, lo=256, hi=1024, T_=T, cfg=3, algo="fused"):
         super().__init__(dev)
         import numpy as np
         import torch
@@ -320,24 +323,63 @@ class Batched(Workload):
             imgs.append(B.tnrd_image(self.f_dev[offs[i]:].data_ptr(), self.u_dev[offs[i]:].data_ptr(),
                                      Hh, Ww, P, looks.index(Lk)))
         self.sp = torch.cuda.current_stream(dev).cuda_stream
-        self.plan = B.Plan(imgs, [m.params() for m in self.models], autotune=True, stream=self.sp)
+        self.plan = B.Plan(imgs, [m.params() for m in self.models], algo=B.ALGO[algo],
+                           autotune=True, stream=self.sp)
         self.px = sum(Hh * Ww for (Hh, Ww, _) in self.sizes)
-        self.launches = 1
+        self.launches = 1 if algo == "fused" else T_
         self.flops = float(self.px) * T_ * FLOPS_PER_PX_STAGE
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE
-        self.kernel = f"batch_persistent_fwd<7,48,{self.plan.tile_height}>"
+        self.algo = algo
+        if algo != "fused":
+            self.dtype = f"{algo} operands, f32 accumulate"
+        self.kernel = (f"batch_persistent_fwd<7,48,{self.plan.tile_height}>" if algo == "fused" else
+                       f"tc_batch_fwd<7,48,2,{algo}> (tcgen05 {algo.upper()} filter bank and "
+                       f"adjoint, FP32 phi/prox; one launch per stage)")
         self.h2d = self.d2h = int(self.f_host.numel() * 4)
         self.config = {"workload": f"TRDMD batched forward, {n} images with sides U[{lo},{hi}] "
                                    f"({self.px / 1e6:.1f} Mpx), L in {{1,2,4,8}} with one "
-                                   f"7x7x48 63-RBF parameter set each, T={T_}, one persistent "
-                                   f"launch per step (CUDA graph), autotuned tile height "
-                                   f"{self.plan.tile_height}",
+                                   f"7x7x48 63-RBF parameter set each, T={T_}, " +
+                                   (f"one persistent launch per step (CUDA graph), autotuned tile "
+                                    f"height {self.plan.tile_height}" if algo == "fused" else
+                                    f"{algo.upper()} tensor-core stage, one launch per stage over "
+                                    f"all images' tiles (CUDA graph)"),
                        "images": n, "pixels": self.px, "ksize": KS, "nfilt": NK, "nrbf": 63,
                        "T": T_, "tile_height": self.plan.tile_height,
                        "l2": f"inputs ({self.h2d / 2 ** 20:.0f} MiB) larger than L2"}
 
     def step(self):
         self.plan.forward(self.sp)
+
+    def accuracy(self):
+        """Tensor-core plans: max |du| and PSNR of image 0 against the FP64 oracle
+        on sampled pixels (crops the crop edge cannot reach)."""
+        if self.algo == "fused":
+            return None
+        import numpy as np
+        import torch
+        import oracle
+        from paper_1702_07482_gb300 import ops
+        oracle.build()
+        self.step()
+        torch.cuda.synchronize()
+        Hh, Ww, Lk = self.sizes[0]
+        P = ops.pitch_for(Ww)
+        u0 = self.u_dev[:Hh * P].view(Hh, P)[:, :Ww].double().cpu().numpy()
+        M = 2 * (KS // 2) * self.T
+        g = np.random.Generator(np.random.PCG64(5))
+        pts = [(0, 0), (Hh - 1, Ww - 1)] + [tuple(x) for x in
+                                            zip(g.integers(0, Hh, 10), g.integers(0, Ww, 10))]
+        d = []
+        for (y, x) in pts:
+            y0, y1 = max(0, y - M), min(Hh, y + M + 1)
+            x0, x1 = max(0, x - M), min(Ww, x + M + 1)
+            ref = oracle.forward(self.fs[0][y0:y1, x0:x1].copy(), self.params[0])[-1][y - y0, x - x0]
+            d.append(u0[y, x] - ref)
+        d = np.array(d)
+        mse = float((d ** 2).mean())
+        return {"vs": "FP64 oracle", "pixels": len(pts), "max_abs": float(np.abs(d).max()),
+                "psnr_db": 10 * np.log10(255.0 ** 2 / max(mse, 1e-30)),
+                "scale": "[0, 255] intensities"}
 
     def e2e(self):
         self.f_dev.copy_(self.f_host, non_blocking=True)
@@ -641,6 +683,10 @@ def make_workload(name, dev):
         return Fwd(dev, H=128, W=128, ks=5, nk=24, cfg=1)
     if name == "batched":
         return Batched(dev)
+    if name == "batched_tf32":
+        return Batched(dev, algo="tf32")
+    if name == "batched_bf16":
+        return Batched(dev, algo="bf16")
     if name == "train":
         return Train(dev)
     if name == "fit":
@@ -811,7 +857,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fwd512",
-                    choices=["fwd512", "fwd512_unfused", "small128", "batched", "train",
+                    choices=["fwd512", "fwd512_unfused", "small128", "batched", "batched_tf32",
+                             "batched_bf16", "train",
                              "fit", "fwd512_gauss", "fwd512_proj", "quality", "mixed_tf32",
                              "mixed_bf16", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

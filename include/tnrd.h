@@ -150,12 +150,14 @@ TNRD_API tnrd_status tnrd_backward(const tnrd_params* params, int N, int H, int 
 /* ---- Batched forward over images of different sizes ---------------------
  * A plan describes a fixed batch: every image with its own size, input and
  * output buffers and one of several parameter sets (e.g. one per number of
- * looks L).  tnrd_batch_forward then runs all T stages of all images in ONE
- * persistent kernel launch: CTAs take (stage, image, tile) items from a
- * stage-major queue; a tile of stage t waits until the 3 x 3 neighbouring
- * tiles of its image have finished stage t-1 (each wait bounded, see
- * tnrd_plan_set_wait_limit).  The launch is recorded in a CUDA graph at plan
- * creation and replayed by tnrd_batch_forward. */
+ * looks L).  With TNRD_ALGO_FUSED, tnrd_batch_forward runs all T stages of all
+ * images in ONE persistent kernel launch: CTAs take (stage, image, tile) items
+ * from a stage-major queue; a tile of stage t waits until the 3 x 3
+ * neighbouring tiles of its image have finished stage t-1 (each wait bounded,
+ * see tnrd_plan_set_wait_limit).  With TNRD_ALGO_TC_TF32 / _BF16 it runs one
+ * tensor-core launch per stage over all images' tiles (mixed precision as in
+ * tnrd_forward).  The launches are recorded in a CUDA graph at plan creation
+ * and replayed by tnrd_batch_forward. */
 typedef struct {
     const float* f;     /* device [H][pitch] noisy input (u_0)                 */
     float* u;           /* device [H][pitch] receives u_T; must not overlap f   */
@@ -167,7 +169,8 @@ typedef struct tnrd_plan tnrd_plan;
 
 /* Creates a plan for `nimg` images (host array, copied) and `nsets` parameter
  * sets (host array of tnrd_params with device arrays, copied; all sets must
- * share T, ksize, nfilt, nrbf).  algo must be TNRD_ALGO_FUSED.  This is the one
+ * share T, ksize, nfilt, nrbf).  algo: TNRD_ALGO_FUSED, _TC_TF32 or _TC_BF16
+ * (TNRD_ALGO_UNFUSED is not batched).  This is the one
  * call that allocates device memory (work lists, per-tile stage counters, the
  * inter-stage images, a status word).  With autotune != 0 it times each
  * compiled tile height on the actual images (running the forward, which
@@ -183,8 +186,8 @@ TNRD_API tnrd_status tnrd_plan_create(tnrd_plan** plan, const tnrd_image* images
 TNRD_API tnrd_status tnrd_batch_forward(const tnrd_plan* plan, cudaStream_t stream);
 
 /* Synchronous: TNRD_OK, or TNRD_ERR_TIMEOUT if a tile of the last
- * tnrd_batch_forward gave up waiting for its neighbours (its outputs are then
- * incomplete). */
+ * tnrd_batch_forward gave up waiting for its neighbours or (tensor-core plans)
+ * for its tensor-core operations (its outputs are then incomplete). */
 TNRD_API tnrd_status tnrd_plan_status(const tnrd_plan* plan);
 
 /* Bound, in SM clock cycles, on each wait of a tile for its neighbours
@@ -192,7 +195,8 @@ TNRD_API tnrd_status tnrd_plan_status(const tnrd_plan* plan);
  * tests the error path.  Synchronous. */
 TNRD_API tnrd_status tnrd_plan_set_wait_limit(tnrd_plan* plan, long long cycles);
 
-/* Tile height the plan uses (tiles are TH x (32 - 2 * (ksize / 2)) pixels). */
+/* Tile height the plan uses (tiles are TH x (32 - 2 * (ksize / 2)) pixels;
+ * tensor-core plans: 16 NB - 2 (ksize / 2), NB = 2). */
 TNRD_API int tnrd_plan_tile_height(const tnrd_plan* plan);
 
 /* Frees the plan's device memory and graph (synchronous). */

@@ -583,6 +583,8 @@ tnrd_status tnrd_quality(const float* ref, const float* img, const float* noisy,
 // ---------------------------------------------------------------------------
 struct tnrd_plan {
     int device = 0;
+    tnrd_algo algo = TNRD_ALGO_FUSED;   // FUSED: one persistent launch; TC_*: one launch per stage
+    int tc_nb = 2;
     int ks = 0, nk = 0, nrbf = 0, T = 0;
     int th = 0;
     int nimg = 0, nsets = 0, ntiles = 0, ntiles_max = 0;
@@ -652,10 +654,14 @@ tnrd_status plan_build(tnrd_plan* P, int th, cudaStream_t s)
     A.nfilt = P->nk;
     A.ksize = P->ks;
     A.nrbf = P->nrbf;
-    const int occ = tnrd::batch_fwd_occupancy(P->ks, P->nk, th, P->nrbf);
-    int nsm = 1;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
-    P->grid = std::max(1, nsm * std::max(occ, 1));
+    if (P->algo == TNRD_ALGO_FUSED) {
+        const int occ = tnrd::batch_fwd_occupancy(P->ks, P->nk, th, P->nrbf);
+        int nsm = 1;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
+        P->grid = std::max(1, nsm * std::max(occ, 1));
+    } else {
+        P->grid = P->ntiles;   // one CTA per tile and stage
+    }
     return TNRD_OK;
 }
 
@@ -663,7 +669,11 @@ cudaError_t plan_enqueue(const tnrd_plan* P, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(P->block + P->off_counters, 0, sizeof(int) * (2 + (size_t)P->ntiles), s);
     if (e != cudaSuccess) return e;
-    return tnrd::launch_batch_fwd(P->ks, P->nk, P->th, P->args, P->grid, s);
+    if (P->algo == TNRD_ALGO_FUSED) return tnrd::launch_batch_fwd(P->ks, P->nk, P->th, P->args, P->grid, s);
+    const bool bf16 = P->algo == TNRD_ALGO_TC_BF16;
+    for (int t = 0; t < P->T && e == cudaSuccess; ++t)
+        e = tnrd::launch_tc_batch(P->ks, P->nk, P->tc_nb, bf16, P->args, t, P->ntiles, s);
+    return e;
 }
 
 }  // namespace
@@ -678,7 +688,8 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
     *out = nullptr;
     if (!images || nimg < 1 || !sets || nsets < 1)
         return fail(TNRD_ERR_INVALID_ARG, "need at least one image and one parameter set");
-    if (algo != TNRD_ALGO_FUSED) return fail(TNRD_ERR_UNSUPPORTED, "batched forward supports TNRD_ALGO_FUSED");
+    if (algo != TNRD_ALGO_FUSED && algo != TNRD_ALGO_TC_TF32 && algo != TNRD_ALGO_TC_BF16)
+        return fail(TNRD_ERR_UNSUPPORTED, "batched forward supports the fused and tensor-core stages");
     for (int s = 0; s < nsets; ++s) {
         tnrd_status st = check_params(&sets[s]);
         if (st != TNRD_OK) return st;
@@ -709,7 +720,10 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
     P->nsets = nsets;
     P->imgs.assign(images, images + nimg);
     P->sets.assign(sets, sets + nsets);
-    const int* ths = tnrd::fused_th_list(ks);
+    P->algo = algo;
+    // tensor-core plans: the stage kernel's one tile height; fused plans: the list
+    const int tc_th[2] = {tnrd::tc_tile_h(ks, P->tc_nb), 0};
+    const int* ths = (algo == TNRD_ALGO_FUSED) ? tnrd::fused_th_list(ks) : tc_th;
     int tmax = 0;
     for (const int* p = ths; *p; ++p) {
         int n = 0;

@@ -35,6 +35,9 @@ int tc_tile_h(int ks, int nb);
 cudaError_t launch_tc_fwd(int ks, int nk, int nb, bool bf16, const StageArgs& a, int N,
                           cudaStream_t s);
 cudaError_t tc_take_error(int* out);
+// One stage t of a batched plan on the tensor cores (all images' tiles in one launch).
+cudaError_t launch_tc_batch(int ks, int nk, int nb, bool bf16, const BatchArgs& a, int t,
+                            int ntiles, cudaStream_t s);
 
 // Column-pair fused forward (two z-columns per lane, TW = 64 - 2R); nsplit 2
 // runs each tile on a cluster of two CTAs with half of the filters each.

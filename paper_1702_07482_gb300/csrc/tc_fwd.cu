@@ -18,6 +18,18 @@ cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int KS, int NK, int NB, bool BF>
+cudaError_t launch_batch_one(const BatchArgs& a, int t, int ntiles, cudaStream_t s)
+{
+    using C = TcCfg<KS, NK, NB, BF>;
+    cudaError_t e = cudaFuncSetAttribute(tc_batch_fwd<KS, NK, NB, BF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    tc_batch_fwd<KS, NK, NB, BF><<<ntiles, C::NTHREADS, C::SMEM_BYTES, s>>>(a, t);
+    return cudaGetLastError();
+}
+
 #define TNRD_TC_CASES(X) \
     X(3, 4, 2) X(3, 4, 3) X(5, 24, 2) X(5, 24, 3) X(7, 48, 2) X(7, 48, 3)
 
@@ -31,6 +43,18 @@ cudaError_t launch_tc_fwd(int ks, int nk, int nb, bool bf16, const StageArgs& a,
 #define X(K, NN, B)                                                                  \
     if (ks == K && nk == NN && nb == B)                                              \
         return bf16 ? launch_one<K, NN, B, true>(a, N, s) : launch_one<K, NN, B, false>(a, N, s);
+    TNRD_TC_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_batch(int ks, int nk, int nb, bool bf16, const BatchArgs& a, int t,
+                            int ntiles, cudaStream_t s)
+{
+#define X(K, NN, B)                                                                     \
+    if (ks == K && nk == NN && nb == B)                                                 \
+        return bf16 ? launch_batch_one<K, NN, B, true>(a, t, ntiles, s)                 \
+                    : launch_batch_one<K, NN, B, false>(a, t, ntiles, s);
     TNRD_TC_CASES(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -37,13 +37,14 @@ namespace tnrd {
 // header (the library is built without relocatable device code).
 __device__ int g_tc_error = 0;
 
+// One stage on one tile (the whole CTA).  err receives TNRD_ERR_TIMEOUT (4)
+// when a wait on the tensor core gives up (the tile's output is then not written).
 template <int KS, int NK, int NB, bool BF>
-__global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ StageArgs a)
+__device__ __forceinline__ void tc_tile(const TileJob& a, unsigned char* smem, int* err)
 {
     using C = TcCfg<KS, NK, NB, BF>;
     constexpr int R = C::R, TW = C::TW, TH = C::TH;
     constexpr long long WAIT_LIMIT = 1ll << 31;   // SM cycles, about one second
-    extern __shared__ __align__(1024) unsigned char smem[];
     float* sU = reinterpret_cast<float*>(smem + C::OFF_U);
     float* sBz = reinterpret_cast<float*>(smem + C::OFF_BZ);
     float* sKm = reinterpret_cast<float*>(smem + C::OFF_KM);
@@ -55,12 +56,11 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
     uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC + 24);
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int n = blockIdx.y;
-    const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x - ty * a.tiles_x;
+    const int ty = a.ty, tx = a.tx;
     const int H = a.H, W = a.W;
     const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
     const bool border = (ty == 0) || (ty == a.tiles_y - 1) || (tx == 0) || (tx == a.tiles_x - 1);
-    const float* uin = a.u_in + (size_t)n * a.img_stride;
+    const float* uin = a.u_in;
 
     // ---- stage operands in shared memory ----------------------------------
     if constexpr (!BF) {
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
     constexpr uint32_t ID_Z = tc::idesc(FMT, 128, C::NPAD);
     constexpr uint32_t ID_Y = tc::idesc(FMT, 128, C::NT);
     constexpr uint32_t LBO_KM = (C::NT / 8) * 128;
-    const RbfConst& rc = a.rc;
+    const RbfConst& rc = *a.rc;
 
     const int g = tid >> 3, mp = tid & 7;       // this thread's pixel in every group
     float* myh = sH + warp * (C::HROWS * C::HPITCH);
@@ -276,8 +276,8 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
         const float lam = __ldg(a.lam);
         const int wy0 = tile_split(ty, TH, H, a.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, a.tiles_y, R);
         const int wx0 = tile_split(tx, TW, W, a.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, a.tiles_x, R);
-        const float* fimg = a.f + (size_t)n * a.img_stride;
-        float* uout = a.u_out + (size_t)n * a.img_stride;
+        const float* fimg = a.f;
+        float* uout = a.u_out;
         for (int idx = tid; idx < TH * TW; idx += 128) {
             const int qy = y0 + idx / TW, qx = x0 + idx % TW;
             if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
@@ -306,11 +306,70 @@ __global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ S
             uout[(size_t)qy * a.pitch + qx] = stage_out(up, gsum, fv, lam, a.dterm, a.proj_c);
         }
     } else if (tid == 0) {
-        atomicExch(&g_tc_error, 4);
+        atomicExch(err, 4);
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+// Per-call stage: grid (tiles_x * tiles_y, N), one tile per CTA.
+template <int KS, int NK, int NB, bool BF>
+__global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ StageArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int n = blockIdx.y;
+    TileJob j;
+    j.u_in = a.u_in + (size_t)n * a.img_stride;
+    j.u_out = a.u_out + (size_t)n * a.img_stride;
+    j.f = a.f + (size_t)n * a.img_stride;
+    j.H = a.H;
+    j.W = a.W;
+    j.pitch = a.pitch;
+    j.tiles_x = a.tiles_x;
+    j.tiles_y = a.tiles_y;
+    j.ty = blockIdx.x / a.tiles_x;
+    j.tx = blockIdx.x - j.ty * a.tiles_x;
+    j.k = a.k;
+    j.w = a.w;
+    j.lam = a.lam;
+    j.nrbf = a.nrbf;
+    j.dterm = a.dterm;
+    j.proj_c = a.proj_c;
+    j.rc = &a.rc;
+    tc_tile<KS, NK, NB, BF>(j, smem, &g_tc_error);
+}
+
+// Stage t of a batched plan: grid (all images' tiles), the tile table of the
+// plan gives each CTA its (image, tile); each image's parameter set, buffers
+// and data term come from the plan.  Stage t writes u when (T-1-t) is even
+// and the plan's inter-stage image otherwise, so the last stage lands in u.
+template <int KS, int NK, int NB, bool BF>
+__global__ void __launch_bounds__(128, 2) tc_batch_fwd(const __grid_constant__ BatchArgs a, int t)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int2 ti = a.tile_img[blockIdx.x];
+    const BatchImg& im = a.imgs[ti.x];
+    const BatchSet& ps = a.sets[im.set];
+    TileJob j;
+    j.u_out = ((a.T - 1 - t) % 2 == 0) ? im.u : im.tmp;
+    j.u_in = (t == 0) ? im.f : (((a.T - t) % 2 == 0) ? im.u : im.tmp);
+    j.f = im.f;
+    j.H = im.H;
+    j.W = im.W;
+    j.pitch = im.pitch;
+    j.tiles_x = im.tiles_x;
+    j.tiles_y = im.tiles_y;
+    j.ty = ti.y / im.tiles_x;
+    j.tx = ti.y - j.ty * im.tiles_x;
+    j.k = ps.k + (size_t)t * NK * KS * KS;
+    j.w = ps.w + (size_t)t * NK * a.nrbf;
+    j.lam = ps.lam + t;
+    j.nrbf = a.nrbf;
+    j.dterm = ps.dterm;
+    j.proj_c = ps.proj_c;
+    j.rc = &ps.rc;
+    tc_tile<KS, NK, NB, BF>(j, smem, a.status);
 }
 
 }  // namespace tnrd

@@ -117,3 +117,31 @@ def test_autotuned_plan_and_user_graph_capture():
     for (H, W, L, sset), f, u in zip(SIZES, fs, uts):
         ref = oracle.forward(f, params[sset])[-1]
         assert np.abs(u[:, :W].double().cpu().numpy() - ref).max() <= TOL_U_FP32
+
+
+@pytest.mark.parametrize("algo", ["tf32", "bf16"])
+def test_tensor_core_plan_matches_per_image_forward_and_oracle(algo):
+    """A plan on the tensor cores (one launch per stage over every image's
+    tiles, in a CUDA graph) computes each image exactly as tnrd_forward does
+    with the same algorithm, and stays within the stated bound of the oracle."""
+    from paper_1702_07482_gb300 import binding as B
+    from paper_1702_07482_gb300 import ops
+    params, models, fs, fts, uts, imgs = _make(T=2, cfg=165)
+    plan = B.Plan(imgs, [m.params() for m in models], algo=B.ALGO[algo])
+    stream = torch.cuda.current_stream().cuda_stream
+    plan.forward(stream)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert plan.tile_height == 16 * 2 - 2 * 3
+    tol = {"tf32": 0.02, "bf16": 0.2}[algo]
+    for (H, W, L, s), f, ft, ut in zip(SIZES, fs, fts, uts):
+        ref = ops.forward(models[s], ft.unsqueeze(0), W=W, algo=algo)[0]
+        torch.cuda.synchronize()
+        assert torch.equal(ut[:, :W], ref[:, :W])
+        u_or = oracle.forward(f, params[s])[-1]
+        assert np.abs(ut[:, :W].double().cpu().numpy() - u_or).max() <= tol
+    first = [u.clone() for u in uts]
+    plan.forward(stream)          # graph replay: same bits
+    torch.cuda.synchronize()
+    for (H, W, L, s), a, b in zip(SIZES, first, uts):
+        assert torch.equal(a[:, :W], b[:, :W])
