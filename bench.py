@@ -326,21 +326,23 @@ class Batched(Workload):
         self.plan = B.Plan(imgs, [m.params() for m in self.models], algo=B.ALGO[algo],
                            autotune=True, stream=self.sp)
         self.px = sum(Hh * Ww for (Hh, Ww, _) in self.sizes)
-        self.launches = 1 if algo == "fused" else T_
+        self.launches = self.plan.launches
         self.flops = float(self.px) * T_ * FLOPS_PER_PX_STAGE
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE
         self.algo = algo
         if algo != "fused":
             self.dtype = f"{algo} operands, f32 accumulate"
-        self.kernel = (f"batch_persistent_fwd<7,48,{self.plan.tile_height}>" if algo == "fused" else
+        sched = "batch_persistent_fwd" if self.launches == 1 else "batch_stage_fwd"
+        self.kernel = (f"{sched}<7,48,{self.plan.tile_height}>" if algo == "fused" else
                        f"tc_batch_fwd<7,48,2,{algo}> (tcgen05 {algo.upper()} filter bank and "
                        f"adjoint, FP32 phi/prox; one launch per stage)")
         self.h2d = self.d2h = int(self.f_host.numel() * 4)
         self.config = {"workload": f"TRDMD batched forward, {n} images with sides U[{lo},{hi}] "
                                    f"({self.px / 1e6:.1f} Mpx), L in {{1,2,4,8}} with one "
                                    f"7x7x48 63-RBF parameter set each, T={T_}, " +
-                                   (f"one persistent launch per step (CUDA graph), autotuned tile "
-                                    f"height {self.plan.tile_height}" if algo == "fused" else
+                                   (f"{'one persistent launch' if self.launches == 1 else 'one launch per stage'} "
+                                    f"per step (CUDA graph), autotuned tile height and schedule "
+                                    f"(tile height {self.plan.tile_height})" if algo == "fused" else
                                     f"{algo.upper()} tensor-core stage, one launch per stage over "
                                     f"all images' tiles (CUDA graph)"),
                        "images": n, "pixels": self.px, "ksize": KS, "nfilt": NK, "nrbf": 63,

@@ -199,6 +199,11 @@ TNRD_API tnrd_status tnrd_plan_set_wait_limit(tnrd_plan* plan, long long cycles)
  * tensor-core plans: 16 NB - 2 (ksize / 2), NB = 2). */
 TNRD_API int tnrd_plan_tile_height(const tnrd_plan* plan);
 
+/* Kernel launches per tnrd_batch_forward of the plan: 1 for the persistent
+ * schedule, T for one launch per stage (tensor-core plans, and fused plans
+ * whose autotuner found that schedule faster). */
+TNRD_API int tnrd_plan_launches(const tnrd_plan* plan);
+
 /* Frees the plan's device memory and graph (synchronous). */
 TNRD_API void tnrd_plan_destroy(tnrd_plan* plan);
 

@@ -583,8 +583,9 @@ tnrd_status tnrd_quality(const float* ref, const float* img, const float* noisy,
 // ---------------------------------------------------------------------------
 struct tnrd_plan {
     int device = 0;
-    tnrd_algo algo = TNRD_ALGO_FUSED;   // FUSED: one persistent launch; TC_*: one launch per stage
+    tnrd_algo algo = TNRD_ALGO_FUSED;   // FUSED: fused stage kernel; TC_*: tensor-core stage
     int tc_nb = 2;
+    int stages = 0;   // FUSED: 0 one persistent launch, 1 one launch per stage (autotuned)
     int ks = 0, nk = 0, nrbf = 0, T = 0;
     int th = 0;
     int nimg = 0, nsets = 0, ntiles = 0, ntiles_max = 0;
@@ -669,7 +670,9 @@ cudaError_t plan_enqueue(const tnrd_plan* P, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(P->block + P->off_counters, 0, sizeof(int) * (2 + (size_t)P->ntiles), s);
     if (e != cudaSuccess) return e;
-    if (P->algo == TNRD_ALGO_FUSED) return tnrd::launch_batch_fwd(P->ks, P->nk, P->th, P->args, P->grid, s);
+    if (P->algo == TNRD_ALGO_FUSED)
+        return P->stages ? tnrd::launch_batch_stages(P->ks, P->nk, P->th, P->args, s)
+                         : tnrd::launch_batch_fwd(P->ks, P->nk, P->th, P->args, P->grid, s);
     const bool bf16 = P->algo == TNRD_ALGO_TC_BF16;
     for (int t = 0; t < P->T && e == cudaSuccess; ++t)
         e = tnrd::launch_tc_batch(P->ks, P->nk, P->tc_nb, bf16, P->args, t, P->ntiles, s);
@@ -768,36 +771,44 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
         return cuda_fail(e, "plan upload");
     }
 
-    // tile height: timed on the data (autotune) or by total work incl. halos
-    int best = ths[0];
+    // tile height (and, for the fused stage, the schedule: one persistent launch
+    // or one launch per stage): timed on the data (autotune) or, without
+    // autotune, the persistent launch with the tile height of least total work
+    // including halos
+    int best = ths[0], best_stages = 0;
     if (autotune) {
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
+        const int nmodes = (algo == TNRD_ALGO_FUSED) ? 2 : 1;
         for (const int* p = ths; *p; ++p) {
             tnrd_status st = plan_build(P, *p, stream);
             if (st != TNRD_OK) { tnrd_plan_destroy(P); return st; }
-            float ms = 0.0f;
-            e = plan_enqueue(P, stream);   // warm-up
-            for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
-                cudaEventRecord(e0, stream);
-                e = plan_enqueue(P, stream);
-                cudaEventRecord(e1, stream);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                float m = 0.0f;
-                cudaEventElapsedTime(&m, e0, e1);
-                ms += m;
-            }
-            if (e != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                tnrd_plan_destroy(P);
-                return cuda_fail(e, "autotune run");
-            }
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = *p;
+            for (int mode = 0; mode < nmodes; ++mode) {
+                P->stages = mode;
+                float ms = 0.0f;
+                e = plan_enqueue(P, stream);   // warm-up
+                for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+                    cudaEventRecord(e0, stream);
+                    e = plan_enqueue(P, stream);
+                    cudaEventRecord(e1, stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float m = 0.0f;
+                    cudaEventElapsedTime(&m, e0, e1);
+                    ms += m;
+                }
+                if (e != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    tnrd_plan_destroy(P);
+                    return cuda_fail(e, "autotune run");
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = *p;
+                    best_stages = mode;
+                }
             }
         }
         cudaEventDestroy(e0);
@@ -816,6 +827,11 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
                 best = *p;
             }
         }
+    }
+    P->stages = best_stages;
+    if (const char* env = std::getenv("TNRD_BATCH_SCHEDULE")) {   // tuning override
+        if (algo == TNRD_ALGO_FUSED && std::strcmp(env, "stages") == 0) P->stages = 1;
+        if (std::strcmp(env, "persistent") == 0) P->stages = 0;
     }
     tnrd_status st = plan_build(P, best, stream);
     if (st != TNRD_OK) { tnrd_plan_destroy(P); return st; }
@@ -870,6 +886,12 @@ tnrd_status tnrd_plan_set_wait_limit(tnrd_plan* P, long long cycles)
 }
 
 int tnrd_plan_tile_height(const tnrd_plan* P) { return P ? P->th : 0; }
+
+int tnrd_plan_launches(const tnrd_plan* P)
+{
+    if (!P) return 0;
+    return (P->algo == TNRD_ALGO_FUSED && !P->stages) ? 1 : P->T;
+}
 
 void tnrd_plan_destroy(tnrd_plan* P)
 {

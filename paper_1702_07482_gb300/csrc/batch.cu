@@ -105,7 +105,54 @@ batch_persistent_fwd(const __grid_constant__ BatchArgs a)
     }
 }
 
+// The same tiles one stage at a time: stage t of every image's tiles in one
+// launch (grid = tiles of all images), the stages ordered by the stream, so no
+// tile waits for another.  The plan's autotuner times this schedule against
+// the persistent one.
+template <int KS, int NK, int TH>
+__global__ void __launch_bounds__(FusedCfg<KS, NK, TH>::NTHREADS, FusedCfg<KS, NK, TH>::MINB)
+batch_stage_fwd(const __grid_constant__ BatchArgs a, int t)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int2 ti = a.tile_img[blockIdx.x];
+    const BatchImg& im = a.imgs[ti.x];
+    const BatchSet& ps = a.sets[im.set];
+    TileJob j;
+    j.u_out = ((a.T - 1 - t) % 2 == 0) ? im.u : im.tmp;
+    j.u_in = (t == 0) ? im.f : (((a.T - t) % 2 == 0) ? im.u : im.tmp);
+    j.f = im.f;
+    j.H = im.H;
+    j.W = im.W;
+    j.pitch = im.pitch;
+    j.tiles_x = im.tiles_x;
+    j.tiles_y = im.tiles_y;
+    j.ty = ti.y / im.tiles_x;
+    j.tx = ti.y - j.ty * im.tiles_x;
+    j.k = ps.k + (size_t)t * NK * KS * KS;
+    j.w = ps.w + (size_t)t * NK * a.nrbf;
+    j.lam = ps.lam + t;
+    j.nrbf = a.nrbf;
+    j.dterm = ps.dterm;
+    j.proj_c = ps.proj_c;
+    j.rc = &ps.rc;
+    stage_tile<KS, NK, TH>(j, smem);
+}
+
 namespace {
+
+template <int KS, int NK, int TH>
+cudaError_t launch_stages_one(const BatchArgs& a, cudaStream_t s)
+{
+    using C = FusedCfg<KS, NK, TH>;
+    const size_t smem = C::smem_bytes(a.nrbf);
+    cudaError_t e = cudaFuncSetAttribute(batch_stage_fwd<KS, NK, TH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int t = 0; t < a.T && e == cudaSuccess; ++t) {
+        batch_stage_fwd<KS, NK, TH><<<a.ntiles, C::NTHREADS, smem, s>>>(a, t);
+        e = cudaGetLastError();
+    }
+    return e;
+}
 
 template <int KS, int NK, int TH>
 cudaError_t launch_one(const BatchArgs& a, int grid, cudaStream_t s)
@@ -143,6 +190,14 @@ int occupancy_one(int nrbf)
 cudaError_t launch_batch_fwd(int ks, int nk, int th, const BatchArgs& a, int grid, cudaStream_t s)
 {
 #define X(K, N, T) if (ks == K && nk == N && th == T) return launch_one<K, N, T>(a, grid, s);
+    TNRD_BATCH_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_stages(int ks, int nk, int th, const BatchArgs& a, cudaStream_t s)
+{
+#define X(K, N, T) if (ks == K && nk == N && th == T) return launch_stages_one<K, N, T>(a, s);
     TNRD_BATCH_CASES(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -48,6 +48,8 @@ cudaError_t launch_pair_fwd(int ks, int nk, int th, int nsplit, const StageArgs&
 // Persistent batched forward.
 cudaError_t launch_batch_fwd(int ks, int nk, int th, const BatchArgs& a, int grid, cudaStream_t s);
 int batch_fwd_occupancy(int ks, int nk, int th, int nrbf);
+// The same plan one stage per launch (T launches, no waits between tiles).
+cudaError_t launch_batch_stages(int ks, int nk, int th, const BatchArgs& a, cudaStream_t s);
 
 // Backward: tile height of bwd_zb / bwd_adj, one stage's prep + zb + adj +
 // filter-gradient launches, and the fixed-order partial reduce (three sets).

@@ -65,6 +65,32 @@ def test_batch_matches_per_image_forward_bit_for_bit():
         del os.environ["TNRD_FUSED_KERNEL"]
 
 
+def test_stage_schedule_matches_persistent_bit_for_bit():
+    """One launch per stage over the plan's tile table gives the same bits as
+    the persistent schedule (same tiles, same stage kernel body)."""
+    from paper_1702_07482_gb300 import binding as B
+    params, models, fs, fts, uts, imgs = _make(T=3, cfg=164)
+    stream = torch.cuda.current_stream().cuda_stream
+    plan = B.Plan(imgs, [m.params() for m in models])
+    assert plan.launches == 1
+    plan.forward(stream)
+    torch.cuda.synchronize()
+    first = [u.clone() for u in uts]
+    os.environ["TNRD_BATCH_SCHEDULE"] = "stages"
+    try:
+        plan2 = B.Plan(imgs, [m.params() for m in models])
+    finally:
+        del os.environ["TNRD_BATCH_SCHEDULE"]
+    assert plan2.launches == 3 and plan2.tile_height == plan.tile_height
+    for u in uts:
+        u.fill_(float("nan"))
+    plan2.forward(stream)
+    torch.cuda.synchronize()
+    assert plan2.status() == 0
+    for (H, W, L, s), a, b in zip(SIZES, first, uts):
+        assert torch.equal(a[:, :W], b[:, :W])
+
+
 def test_batch_matches_oracle_and_replays():
     from paper_1702_07482_gb300 import binding as B
     params, models, fs, fts, uts, imgs = _make(T=2, cfg=161)
