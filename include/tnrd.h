@@ -151,10 +151,13 @@ TNRD_API tnrd_status tnrd_backward(const tnrd_params* params, int N, int H, int 
  * A plan describes a fixed batch: every image with its own size, input and
  * output buffers and one of several parameter sets (e.g. one per number of
  * looks L).  With TNRD_ALGO_FUSED, tnrd_batch_forward runs all T stages of all
- * images in ONE persistent kernel launch: CTAs take (stage, image, tile) items
- * from a stage-major queue; a tile of stage t waits until the 3 x 3
+ * images either in ONE persistent kernel launch -- CTAs take (stage, image,
+ * tile) items from a stage-major queue; a tile of stage t waits until the 3 x 3
  * neighbouring tiles of its image have finished stage t-1 (each wait bounded,
- * see tnrd_plan_set_wait_limit).  With TNRD_ALGO_TC_TF32 / _BF16 it runs one
+ * see tnrd_plan_set_wait_limit) -- or in one launch per stage over all images'
+ * tiles, whichever the autotuner measured faster (tnrd_plan_launches; the
+ * persistent launch without autotune).  Both schedules give the same bits.
+ * With TNRD_ALGO_TC_TF32 / _BF16 it runs one
  * tensor-core launch per stage over all images' tiles (mixed precision as in
  * tnrd_forward).  The launches are recorded in a CUDA graph at plan creation
  * and replayed by tnrd_batch_forward. */
@@ -173,9 +176,10 @@ typedef struct tnrd_plan tnrd_plan;
  * (TNRD_ALGO_UNFUSED is not batched).  This is the one
  * call that allocates device memory (work lists, per-tile stage counters, the
  * inter-stage images, a status word).  With autotune != 0 it times each
- * compiled tile height on the actual images (running the forward, which
- * writes the outputs) on `stream` and keeps the fastest; otherwise a size
- * heuristic picks it.  Synchronises `stream`. */
+ * compiled tile height (and, for TNRD_ALGO_FUSED, both schedules) on the
+ * actual images (running the forward, which writes the outputs) on `stream`
+ * and keeps the fastest; otherwise a size heuristic picks the tile height.
+ * Synchronises `stream`. */
 TNRD_API tnrd_status tnrd_plan_create(tnrd_plan** plan, const tnrd_image* images, int nimg,
                                       const tnrd_params* sets, int nsets, tnrd_algo algo,
                                       int autotune, cudaStream_t stream);
