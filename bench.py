@@ -81,7 +81,7 @@ _TRAFFIC = {"kernel": "fused_pair2_fwd<7,48,37> tiles 37x58", "sources_sha256_16
 def _kernel_sources_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("fused_fwd.cuh", "fused_pair.cuh", "common.cuh", "args.cuh"):
+    for f in ("fused_fwd.cuh", "fused_pair.cuh", "tile_stage.cuh", "common.cuh", "args.cuh"):
         with open(os.path.join(ROOT, "paper_1702_07482_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -121,7 +121,10 @@ TNRD_API tnrd_status tnrd_forward(const tnrd_params* params, int N, int H, int W
                          void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /* Describes the stage kernel tnrd_forward would launch for this shape and
- * algo (kernel name and tile geometry), as a NUL-terminated string of at most
+ * algo (kernel name, tile geometry and, for the fused stages, how the haloed
+ * u_{t-1} tile reaches shared memory: "tma staging" -- a bulk tensor copy, the
+ * out-of-image halo mirrored in shared memory -- or "gather staging" when
+ * TNRD_TMA=0), as a NUL-terminated string of at most
  * len - 1 characters written to buf.  Host-only: launches nothing.  Returns
  * TNRD_ERR_INVALID_ARG for a null or empty buf, otherwise the status
  * tnrd_forward's parameter checks would return. */
@@ -259,10 +262,10 @@ TNRD_API tnrd_status tnrd_forward_noalloc(const tnrd_params* params, int N, int 
                                           int pitch, const float* f, float* u,
                                           cudaStream_t stream);
 
-/* Synchronous: TNRD_OK, or TNRD_ERR_TIMEOUT if a tensor-core stage launched
- * since the last call gave up waiting for its tensor-core operations (a
- * bounded wait; the affected tile's output is then not written).  Reading
- * clears the device-side word. */
+/* Synchronous: TNRD_OK, or TNRD_ERR_TIMEOUT if a stage launched since the
+ * last call gave up waiting for its tensor-core operations or (fused stages)
+ * for the bulk tensor copy of its u_{t-1} tile (bounded waits; the affected
+ * tile's output is then not written).  Reading clears the device-side word. */
 TNRD_API tnrd_status tnrd_device_status(void);
 
 /* Message describing the last error status returned on this host thread. */

@@ -271,7 +271,7 @@ tnrd_status tnrd_device_status(void)
     int v = 0;
     cudaError_t e = tnrd::tc_take_error(&v);
     if (e != cudaSuccess) return cuda_fail(e, "device status read");
-    if (v != 0) return fail((tnrd_status)v, "a tensor-core stage gave up waiting for its MMAs");
+    if (v != 0) return fail((tnrd_status)v, "a stage gave up waiting for its MMAs or its tile copy");
     return TNRD_OK;
 }
 
@@ -299,11 +299,14 @@ tnrd_status tnrd_forward_kernel(const tnrd_params* p, int N, int H, int W, tnrd_
     const int ks = p->ksize, nk = p->nfilt, R = ks / 2;
     if (algo == TNRD_ALGO_FUSED) {
         const FusedChoice c = pick_fused(ks, nk, N, H, W);
+        const char* staging = tnrd::tma_staging_enabled() ? "tma" : "gather";
         if (c.pair)
-            std::snprintf(buf, len, "%s<%d,%d,%d> tiles %dx%d", c.nsplit == 2 ? "fused_pair2_fwd" : "fused_pair_fwd",
-                          ks, nk, c.th, c.th, c.tw);
+            std::snprintf(buf, len, "%s<%d,%d,%d> tiles %dx%d, %s staging",
+                          c.nsplit == 2 ? "fused_pair2_fwd" : "fused_pair_fwd", ks, nk, c.th, c.th,
+                          c.tw, staging);
         else
-            std::snprintf(buf, len, "fused_stage_fwd<%d,%d,%d> tiles %dx%d", ks, nk, c.th, c.th, c.tw);
+            std::snprintf(buf, len, "fused_stage_fwd<%d,%d,%d> tiles %dx%d, %s staging", ks, nk, c.th,
+                          c.th, c.tw, staging);
     } else if (algo == TNRD_ALGO_UNFUSED) {
         std::snprintf(buf, len, "unf_bank_phi + unf_adjoint + unf_prox <%d,%d>", ks, nk);
     } else if (algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16) {
@@ -594,6 +597,7 @@ struct tnrd_plan {
     std::vector<tnrd_params> sets;
     char* block = nullptr;          // the plan's one device allocation
     size_t off_imgs = 0, off_sets = 0, off_tiles = 0, off_counters = 0, off_limit = 0, off_tmp = 0;
+    size_t off_maps = 0;            // per image: tensor maps of f, u, tmp (per-stage fused kernel)
     std::vector<size_t> tmp_off;    // per image, offset of its inter-stage image
     tnrd::BatchArgs args{};
     cudaGraph_t graph = nullptr;
@@ -635,8 +639,29 @@ tnrd_status plan_build(tnrd_plan* P, int th, cudaStream_t s)
     }
     P->th = th;
     P->ntiles = base;
+    // tensor maps of every image's f, u and tmp for the per-stage fused kernel's
+    // tile copies (boxes of this tile height); none if any cannot be encoded
+    std::vector<CUtensorMap> maps;
+    int bw = 0, bh = 0;
+    if (P->algo == TNRD_ALGO_FUSED && tnrd::tma_staging_enabled() &&
+        tnrd::fused_fwd_box(P->ks, P->nk, th, &bw, &bh) && tnrd::device_status_word()) {
+        maps.resize(3 * (size_t)P->nimg);
+        for (int i = 0; i < P->nimg && !maps.empty(); ++i) {
+            const float* src[3] = {bi[i].f, bi[i].u, bi[i].tmp};
+            for (int k = 0; k < 3; ++k) {
+                if (!tnrd::encode_tile_map(&maps[3 * i + k], src[k], bi[i].W, bi[i].H, 1, bi[i].pitch,
+                                           (long long)bi[i].H * bi[i].pitch, bw, bh)) {
+                    maps.clear();
+                    break;
+                }
+            }
+        }
+    }
     cudaError_t e = cudaMemcpyAsync(P->block + P->off_imgs, bi.data(), sizeof(tnrd::BatchImg) * bi.size(),
                                     cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !maps.empty())
+        e = cudaMemcpyAsync(P->block + P->off_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                            cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(P->block + P->off_tiles, tiles.data(), sizeof(int2) * tiles.size(),
                             cudaMemcpyHostToDevice, s);
@@ -651,6 +676,8 @@ tnrd_status plan_build(tnrd_plan* P, int th, cudaStream_t s)
     A.tile_done = A.work_counter + 2;
     A.wait_limit = (const long long*)(P->block + P->off_limit);
     A.ntiles = P->ntiles;
+    A.maps = maps.empty() ? nullptr : (const CUtensorMap*)(P->block + P->off_maps);
+    A.err = tnrd::device_status_word();
     A.T = P->T;
     A.nfilt = P->nk;
     A.ksize = P->ks;
@@ -744,6 +771,7 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
     P->off_tiles = take(sizeof(int2) * tmax);
     P->off_counters = take(sizeof(int) * (2 + (size_t)tmax));
     P->off_limit = take(sizeof(long long));
+    P->off_maps = take(sizeof(CUtensorMap) * 3 * (size_t)nimg);
     P->tmp_off.resize(nimg);
     for (int i = 0; i < nimg; ++i) P->tmp_off[i] = take(sizeof(float) * (size_t)images[i].H * images[i].pitch);
     cudaError_t e = cudaMalloc((void**)&P->block, off);

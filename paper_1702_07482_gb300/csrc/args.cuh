@@ -1,6 +1,7 @@
 // Kernel argument structs and compile-time tile configurations, shared by
 // the kernel translation units and the host-side dispatcher.
 #pragma once
+#include <cuda.h>
 #include "common.cuh"
 
 namespace tnrd {
@@ -19,6 +20,9 @@ struct StageArgs {
     int dterm;             // tnrd_data_term of the model
     float proj_c;          // projection floor (dterm 2)
     RbfConst rc;
+    int use_tma;           // umap describes u_in: stage tiles with bulk tensor copies
+    int* err;              // device status word (TNRD_ERR_TIMEOUT on a copy that never landed)
+    CUtensorMap umap;      // [N][H][pitch] float32 view of u_in, box of the kernel's staged tile
 };
 
 // One tile of one stage for stage_tile(): pointers already offset to the image.
@@ -35,6 +39,9 @@ struct TileJob {
     int dterm;
     float proj_c;
     const RbfConst* rc;
+    const CUtensorMap* umap = nullptr;   // tensor map of u_in (null: symmetric gather)
+    int img = 0;                         // z coordinate of this image in umap
+    int* err = nullptr;                  // status word for a copy that timed out
 };
 
 template <int KS, int NK, int TH>
@@ -52,7 +59,7 @@ struct FusedCfg {
     static constexpr int UH_INT = R + GROUPS_INT * KS;
     static constexpr int UH = UH_EXT > UH_INT ? UH_EXT : UH_INT;   // u rows from y0 - 3R
     static constexpr int UW = 32 + 2 * R;          // u cols from x0 - 2R
-    static constexpr int UP = UW;
+    static constexpr int UP = staged_pitch(UW);    // staged row pitch (16-byte aligned box)
     static constexpr int H_FL = (TH + 2 * R) * 32; // h rows from y0 - R, one column per lane
     static constexpr int KPAD = (KS * KS + 3) & ~3;
     static constexpr int WPADN = MAX_NRBF + 2 * RBF_WPAD;
@@ -255,6 +262,8 @@ struct BatchArgs {
     int ntiles;                  // tiles per stage over all images
     int T;
     int nfilt, ksize, nrbf;
+    const CUtensorMap* maps;     // per image: f, u, tmp views for the per-stage kernel (or null)
+    int* err;                    // device status word of the per-stage kernel's copies
 };
 
 // ---------------------------------------------------------------------------

@@ -33,7 +33,7 @@ template <int KS, int NK, int TH>
 __global__ void __launch_bounds__(FusedCfg<KS, NK, TH>::NTHREADS, FusedCfg<KS, NK, TH>::MINB)
 batch_persistent_fwd(const __grid_constant__ BatchArgs a)
 {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     __shared__ int s_item, s_ok;
     const long long limit = *a.wait_limit;
     const int total = a.ntiles * a.T;
@@ -113,13 +113,18 @@ template <int KS, int NK, int TH>
 __global__ void __launch_bounds__(FusedCfg<KS, NK, TH>::NTHREADS, FusedCfg<KS, NK, TH>::MINB)
 batch_stage_fwd(const __grid_constant__ BatchArgs a, int t)
 {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     const int2 ti = a.tile_img[blockIdx.x];
     const BatchImg& im = a.imgs[ti.x];
     const BatchSet& ps = a.sets[im.set];
     TileJob j;
+    // stage t writes u when (T-1-t) is even, so that stage T-1 lands in u
+    const int src = (t == 0) ? 0 : (((a.T - t) % 2 == 0) ? 1 : 2);   // f, u, tmp
     j.u_out = ((a.T - 1 - t) % 2 == 0) ? im.u : im.tmp;
-    j.u_in = (t == 0) ? im.f : (((a.T - t) % 2 == 0) ? im.u : im.tmp);
+    j.u_in = src == 0 ? im.f : (src == 1 ? im.u : im.tmp);
+    j.umap = a.maps ? a.maps + 3 * ti.x + src : nullptr;
+    j.img = 0;
+    j.err = a.err;
     j.f = im.f;
     j.H = im.H;
     j.W = im.W;

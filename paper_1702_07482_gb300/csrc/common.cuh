@@ -59,6 +59,10 @@ __device__ __forceinline__ float ex2_approx(float x)
 }
 
 // Half-sample symmetric index into [0, n), any integer i (period 2n).
+// Row pitch (floats) of a staged tile of uw columns: room for a start column
+// rounded down to 16 bytes (up to 3 floats earlier), a multiple of 4 floats.
+__host__ __device__ constexpr int staged_pitch(int uw) { return (uw + 3 + 3) & ~3; }
+
 __device__ __forceinline__ int sym_idx(int i, int n)
 {
     const int p = 2 * n;

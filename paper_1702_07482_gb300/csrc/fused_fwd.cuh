@@ -24,6 +24,7 @@
 // The epilogue sums the warps' h, folds, applies the prox and stores u_t.
 #pragma once
 #include "args.cuh"
+#include "tile_stage.cuh"
 
 namespace tnrd {
 
@@ -118,8 +119,9 @@ __device__ __forceinline__ void walk_group(const float* __restrict__ urow, float
     }
 }
 
-// One stage on one tile (the whole CTA).  Loads of u_{t-1} go through L2
-// (ld.global.cg) so that a persistent kernel can read tiles that other CTAs
+// One stage on one tile (the whole CTA).  The haloed u_{t-1} tile is staged by
+// a bulk tensor copy when j.umap is set, else gathered through L2
+// (ld.global.cg), which lets a persistent kernel read tiles that other CTAs
 // wrote earlier in the same launch; ends with a CTA barrier after the stores.
 template <int KS, int NK, int TH>
 __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
@@ -138,21 +140,17 @@ __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
     const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
     const bool ext = (ty == 0) || (ty == j.tiles_y - 1);
     const bool border = ext || (tx == 0) || (tx == j.tiles_x - 1);
-    const float* uin = j.u_in;
     const RbfConst& rc = *j.rc;
 
-    for (int idx = threadIdx.x; idx < C::UH * C::UW; idx += C::NTHREADS) {
-        const int i = idx / C::UW, jj = idx - i * C::UW;
-        const int yy = sym_idx(y0 - 3 * R + i, H), xx = sym_idx(x0 - 2 * R + jj, W);
-        sU[i * C::UP + jj] = __ldcg(uin + (size_t)yy * j.pitch + xx);
-    }
     float* myH = sH + warp * C::H_FL;
     float* myK = sKW + warp * C::KW_FL;
     float* myW = myK + C::KPAD;
     float* myT = sTab + warp * RBF_TP * RBF_NCOEF;
     for (int e = lane; e < C::H_FL; e += 32) myH[e] = 0.0f;
     for (int e = lane; e < C::WPADN; e += 32) myW[e] = 0.0f;
-    __syncthreads();
+    // staged column of x0 - 2R (ends with a CTA barrier)
+    const int xoff = stage_u_tile<C::UH, C::UW, C::NTHREADS, 1>(j, sU, y0 - 3 * R, x0 - 2 * R);
+    if (xoff < 0) return;   // the copy never landed (status recorded)
 
     // Walk geometry.  h rows [hy0, hy0 + nh); step m reads u row hy0 - 2R + m,
     // completes z row hy0 - 3R + m (valid from m = 2R) and h row hy0 - 4R + m
@@ -162,7 +160,7 @@ __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
     const int nh = ext ? TH + 2 * R : TH;
     const int nsteps = nh + 4 * R;
     const int ub0 = ext ? 0 : R;                         // U buffer row of step 0
-    const float* urow = sU + ub0 * C::UP + lane;
+    const float* urow = sU + ub0 * C::UP + xoff + lane;
     float* hrow = myH + (hy0 - 4 * R - (y0 - R)) * 32 + lane;
     const int zrow0 = hy0 - 3 * R;
     const bool col_in = (unsigned)(x0 - R + lane) < (unsigned)W;
@@ -229,7 +227,7 @@ __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
                 g += hs;
             }
         }
-        const float up = sU[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R)];
+        const float up = sU[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R) + xoff];
         const float fv = __ldg(j.f + (size_t)qy * j.pitch + qx);
         j.u_out[(size_t)qy * j.pitch + qx] = stage_out(up, g, fv, lam, j.dterm, j.proj_c);
     }
@@ -240,7 +238,7 @@ template <int KS, int NK, int TH>
 __global__ void __launch_bounds__(FusedCfg<KS, NK, TH>::NTHREADS, FusedCfg<KS, NK, TH>::MINB)
 fused_stage_fwd(const __grid_constant__ StageArgs a)
 {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     const int n = blockIdx.y;
     TileJob j;
     j.u_in = a.u_in + (size_t)n * a.img_stride;
@@ -260,6 +258,9 @@ fused_stage_fwd(const __grid_constant__ StageArgs a)
     j.dterm = a.dterm;
     j.proj_c = a.proj_c;
     j.rc = &a.rc;
+    j.umap = a.use_tma ? &a.umap : nullptr;
+    j.img = n;
+    j.err = a.err;
     stage_tile<KS, NK, TH>(j, smem);
 }
 

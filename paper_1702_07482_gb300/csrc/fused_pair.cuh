@@ -46,7 +46,7 @@ struct PairCfg {
     static constexpr int UH_INT = R + GROUPS_INT * KS;
     static constexpr int UH = UH_EXT > UH_INT ? UH_EXT : UH_INT;   // u rows from y0 - 3R
     static constexpr int UW = 64 + 2 * R;          // u cols from x0 - 2R
-    static constexpr int UP = (UW + 1) & ~1;       // even pitch: float2 row reads
+    static constexpr int UP = staged_pitch(UW);    // staged row pitch (16-byte aligned box)
     static constexpr int U_FL = UH * UP;
     static constexpr int H_FL = (TH + 2 * R) * 64; // h rows from y0 - R, two columns per lane
     static constexpr int KPAD = (KS * KS + 3) & ~3;
@@ -147,9 +147,11 @@ __device__ __forceinline__ void pair_group(const float* __restrict__ urow, float
 // One stage on one tile.  rank selects the CTA's half of the filters and of
 // the epilogue when NSPLIT = 2 (the two CTAs of a cluster share the tile);
 // remote_h is then the other CTA's h buffers (distributed shared memory).
-// Loads of u_{t-1} go through L2 (ld.global.cg).
+// The haloed u_{t-1} tile is staged by a bulk tensor copy (j.umap set, start
+// column even) or gathered through L2.  Returns the staged column of x0 - 2R,
+// or -1 (uniform over the CTA) if the copy never landed.
 template <int KS, int NK, int TH, int NSPLIT>
-__device__ __forceinline__ void pair_tile_walk(const TileJob& j, float* smem, int rank)
+__device__ __forceinline__ int pair_tile_walk(const TileJob& j, float* smem, int rank)
 {
     using C = PairCfg<KS, NK, TH, NSPLIT>;
     constexpr int R = C::R;
@@ -166,20 +168,17 @@ __device__ __forceinline__ void pair_tile_walk(const TileJob& j, float* smem, in
     const bool border = ext || (tx == 0) || (tx == j.tiles_x - 1);
     const RbfConst& rc = *j.rc;
 
-    for (int idx = threadIdx.x; idx < C::UH * C::UW; idx += C::NTHREADS) {
-        const int i = idx / C::UW, jj = idx - i * C::UW;
-        const int yy = sym_idx(y0 - 3 * R + i, H), xx = sym_idx(x0 - 2 * R + jj, W);
-        sU[i * C::UP + jj] = __ldcg(j.u_in + (size_t)yy * j.pitch + xx);
-    }
     for (int e = lane; e < C::H_FL; e += 32) myH[e] = 0.0f;
     for (int e = lane; e < C::WPADN; e += 32) myW[e] = 0.0f;
-    __syncthreads();
+    // float2 row reads: the staged column of x0 - 2R must be even (ends with a CTA barrier)
+    const int xoff = stage_u_tile<C::UH, C::UW, C::NTHREADS, 2>(j, sU, y0 - 3 * R, x0 - 2 * R);
+    if (xoff < 0) return -1;
 
     const int hy0 = ext ? y0 - R : y0;
     const int nh = ext ? TH + 2 * R : TH;
     const int nsteps = nh + 4 * R;
     const int ub0 = ext ? 0 : R;
-    const float* urow = sU + ub0 * C::UP + 2 * lane;
+    const float* urow = sU + ub0 * C::UP + xoff + 2 * lane;
     float2* hrow = reinterpret_cast<float2*>(myH) + (hy0 - 4 * R - (y0 - R)) * 32 + lane;
     const int zrow0 = hy0 - 3 * R;
     const int c0 = x0 - R + 2 * lane;
@@ -217,13 +216,16 @@ __device__ __forceinline__ void pair_tile_walk(const TileJob& j, float* smem, in
         }
         __syncwarp();
     }
+    return xoff;
 }
 
 // Epilogue over the tile's own pixels idx = first, first + step, ...:
-// g = fold(sum of the h buffers), u_t = prox(u_{t-1} - g).
+// g = fold(sum of the h buffers), u_t = prox(u_{t-1} - g).  xoff: staged
+// column of x0 - 2R.
 template <int KS, int NK, int TH, int NSPLIT>
 __device__ __forceinline__ void pair_tile_epilogue(const TileJob& j, const float* smem,
-                                                   const float* remote, int first, int step)
+                                                   const float* remote, int first, int step,
+                                                   int xoff)
 {
     using C = PairCfg<KS, NK, TH, NSPLIT>;
     constexpr int R = C::R;
@@ -265,7 +267,7 @@ __device__ __forceinline__ void pair_tile_epilogue(const TileJob& j, const float
                 g += hs;
             }
         }
-        const float up = sU[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R)];
+        const float up = sU[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R) + xoff];
         const float fv = __ldg(j.f + (size_t)qy * j.pitch + qx);
         j.u_out[(size_t)qy * j.pitch + qx] = stage_out(up, g, fv, lam, j.dterm, j.proj_c);
     }
@@ -292,6 +294,9 @@ __device__ __forceinline__ TileJob pair_job(const StageArgs& a, int tile)
     j.dterm = a.dterm;
     j.proj_c = a.proj_c;
     j.rc = &a.rc;
+    j.umap = a.use_tma ? &a.umap : nullptr;
+    j.img = n;
+    j.err = a.err;
     return j;
 }
 
@@ -300,12 +305,13 @@ template <int KS, int NK, int TH>
 __global__ void __launch_bounds__(PairCfg<KS, NK, TH, 1>::NTHREADS, 2)
 fused_pair_fwd(const __grid_constant__ StageArgs a)
 {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     const TileJob j = pair_job(a, blockIdx.x);
-    pair_tile_walk<KS, NK, TH, 1>(j, smem, 0);
+    const int xoff = pair_tile_walk<KS, NK, TH, 1>(j, smem, 0);
+    if (xoff < 0) return;
     __syncthreads();
     pair_tile_epilogue<KS, NK, TH, 1>(j, smem, nullptr, threadIdx.x,
-                                      PairCfg<KS, NK, TH, 1>::NTHREADS);
+                                      PairCfg<KS, NK, TH, 1>::NTHREADS, xoff);
 }
 
 // A cluster of two CTAs per tile; grid (2 * tiles_x * tiles_y, N).
@@ -315,15 +321,19 @@ fused_pair2_fwd(const __grid_constant__ StageArgs a)
 {
     namespace cg = cooperative_groups;
     using C = PairCfg<KS, NK, TH, 2>;
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
+    __shared__ int s_xoff;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const TileJob j = pair_job(a, blockIdx.x >> 1);
-    pair_tile_walk<KS, NK, TH, 2>(j, smem, rank);
+    const int xoff = pair_tile_walk<KS, NK, TH, 2>(j, smem, rank);
+    if (threadIdx.x == 0) s_xoff = xoff;
     cl.sync();   // both CTAs' h buffers complete and visible in the cluster
     const float* remote = cl.map_shared_rank(smem, rank ^ 1) + ((C::U_FL + 3) & ~3);
-    pair_tile_epilogue<KS, NK, TH, 2>(j, smem, remote, rank * C::NTHREADS + threadIdx.x,
-                                      2 * C::NTHREADS);
+    // both CTAs pass both cluster barriers; the epilogue runs only if both tiles staged
+    if (xoff >= 0 && *cl.map_shared_rank(&s_xoff, rank ^ 1) >= 0)
+        pair_tile_epilogue<KS, NK, TH, 2>(j, smem, remote, rank * C::NTHREADS + threadIdx.x,
+                                          2 * C::NTHREADS, xoff);
     cl.sync();   // keep this CTA's shared memory alive until the other has read it
 }
 

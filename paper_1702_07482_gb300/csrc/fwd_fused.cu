@@ -14,8 +14,10 @@ cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
     cudaError_t e = cudaFuncSetAttribute(fused_stage_fwd<KS, NK, TH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    StageArgs b = a;
+    stage_args_tma(b, N, C::UP, C::UH);
     dim3 grid(a.tiles_x * a.tiles_y, N);
-    fused_stage_fwd<KS, NK, TH><<<grid, C::NTHREADS, smem, s>>>(a);
+    fused_stage_fwd<KS, NK, TH><<<grid, C::NTHREADS, smem, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -48,6 +50,19 @@ size_t fused_fwd_smem(int ks, int nk, int th, int nrbf)
     TNRD_FUSED_CASES(X)
 #undef X
     return 0;
+}
+
+bool fused_fwd_box(int ks, int nk, int th, int* box_w, int* box_h)
+{
+#define X(K, N, T)                                                                  \
+    if (ks == K && nk == N && th == T) {                                            \
+        *box_w = FusedCfg<K, N, T>::UP;                                             \
+        *box_h = FusedCfg<K, N, T>::UH;                                             \
+        return true;                                                                \
+    }
+    TNRD_FUSED_CASES(X)
+#undef X
+    return false;
 }
 
 int fused_fwd_threads(int ks, int nk, int th)

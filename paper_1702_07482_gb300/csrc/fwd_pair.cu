@@ -16,15 +16,19 @@ cudaError_t launch_one(const StageArgs& a, int N, int nsplit, cudaStream_t s)
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)C::SMEM_BYTES);
         if (e != cudaSuccess) return e;
+        StageArgs b = a;
+        stage_args_tma(b, N, C::UP, C::UH);
         fused_pair2_fwd<KS, NK, TH>
-            <<<dim3(2 * a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(a);
+            <<<dim3(2 * a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(b);
     } else {
         using C = PairCfg<KS, NK, TH, 1>;
         cudaError_t e = cudaFuncSetAttribute(fused_pair_fwd<KS, NK, TH>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)C::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        fused_pair_fwd<KS, NK, TH><<<dim3(a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(a);
+        StageArgs b = a;
+        stage_args_tma(b, N, C::UP, C::UH);
+        fused_pair_fwd<KS, NK, TH><<<dim3(a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(b);
     }
     return cudaGetLastError();
 }

@@ -35,6 +35,20 @@ int tc_tile_h(int ks, int nb);
 cudaError_t launch_tc_fwd(int ks, int nk, int nb, bool bf16, const StageArgs& a, int N,
                           cudaStream_t s);
 cudaError_t tc_take_error(int* out);
+// Address of that word on the current device (null if it cannot be had); the
+// fused stages record a tile copy that never landed there too.
+int* device_status_word();
+
+// Bulk-tensor-copy staging of u_{t-1} tiles: TNRD_TMA=0 turns it off (the
+// kernels gather instead); a 3-D [N][H][pitch] float32 tensor map with a
+// box_w x box_h x 1 box; and StageArgs set-up for a kernel whose staged tile is
+// box_w x box_h (falls back to the gather if a map cannot be encoded).
+bool tma_staging_enabled();
+bool encode_tile_map(CUtensorMap* map, const float* base, int W, int H, int N, int pitch,
+                     long long img_stride, int box_w, int box_h);
+void stage_args_tma(StageArgs& a, int N, int box_w, int box_h);
+// Staged tile (columns x rows) of the fused forward kernel of tile height th.
+bool fused_fwd_box(int ks, int nk, int th, int* box_w, int* box_h);
 // One stage t of a batched plan on the tensor cores (all images' tiles in one launch).
 cudaError_t launch_tc_batch(int ks, int nk, int nb, bool bf16, const BatchArgs& a, int t,
                             int ntiles, cudaStream_t s);

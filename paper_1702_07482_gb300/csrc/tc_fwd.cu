@@ -60,6 +60,23 @@ cudaError_t launch_tc_batch(int ks, int nk, int nb, bool bf16, const BatchArgs& 
     return cudaErrorInvalidValue;
 }
 
+int* device_status_word()
+{
+    constexpr int MAXDEV = 64;
+    static int* words[MAXDEV] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return nullptr;
+    if (!words[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_tc_error) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        words[dev] = static_cast<int*>(p);
+    }
+    return words[dev];
+}
+
 cudaError_t tc_take_error(int* out)
 {
     int v = 0, zero = 0;
