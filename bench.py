@@ -74,8 +74,8 @@ def _peaks():
 # workload, from one ncu capture (profiles/fused_pair2_fwd_7x7x48_512x512.md),
 # valid only for the kernel that capture measured and the sources it was taken
 # on (the kernel name and the sources' hash are checked at run time).
-_TRAFFIC = {"kernel": "fused_pair2_fwd<7,48,37> tiles 37x58", "sources_sha256_16": "3a93348fb79a3875",
-            "bytes_per_launch": 2257920}
+_TRAFFIC = {"kernel": "fused_pair2_fwd<7,48,37> tiles 37x58, tma staging",
+            "sources_sha256_16": "ea57490c2e92212d", "bytes_per_launch": 2268672}
 
 
 def _kernel_sources_hash() -> str:

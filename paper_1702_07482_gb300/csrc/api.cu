@@ -116,7 +116,24 @@ tnrd::RbfConst make_rbf(const tnrd_params* p)
     return rc;
 }
 
-// Pick the fused tile height minimising (max tiles per SM) x (work per tile).
+// Estimated duration, in walk steps of one CTA, of one fused stage launch over
+// N images of H x W: tiles of th x tw pixels, `split` CTAs per tile, `slots`
+// CTAs resident at once (two per SM).  A tile in the first or last tile row
+// walks th + 6R steps, the others th + 4R.  When every CTA is resident at once
+// the launch lasts as long as its longest CTA; otherwise the work spreads over
+// the slots, plus half the longest CTA for the tail.
+double fused_cost(int N, int H, int W, int th, int tw, int R, int split, int slots)
+{
+    const long long ty = (H + th - 1) / th, tx = (W + tw - 1) / tw;
+    const long long n_ext = ty >= 2 ? 2 : 1;
+    const double w_ext = th + 6 * R, w_int = th + 4 * R;
+    const long long ctas = (long long)N * ty * tx * split;
+    if (ctas <= slots) return w_ext;
+    const double per_col = n_ext * w_ext + (double)(ty - n_ext) * w_int;
+    return (double)N * tx * split * per_col / slots + 0.5 * w_ext;
+}
+
+// Pick the fused tile height of least estimated duration (fused_cost).
 int pick_fused_th(int ks, int nk, int N, int H, int W)
 {
     const int* list = tnrd::fused_th_list(ks);
@@ -135,9 +152,7 @@ int pick_fused_th(int ks, int nk, int N, int H, int W)
     int best_th = list[0];
     for (const int* p = list; *p; ++p) {
         const int th = *p;
-        const long long tiles = (long long)N * ((H + th - 1) / th) * ((W + tw - 1) / tw);
-        const long long per_sm = (tiles + 2 * nsm - 1) / (2 * nsm);
-        const double cost = per_sm * (double)(th + 4 * R);
+        const double cost = fused_cost(N, H, W, th, tw, R, 1, 2 * nsm);
         if (cost < best * 0.999) {
             best = cost;
             best_th = th;
@@ -150,8 +165,8 @@ int pick_fused_th(int ks, int nk, int N, int H, int W)
 // (fused_stage_fwd) is the default.  When it cannot give every SM two CTAs
 // (a single small image), the column-pair kernel on two-CTA clusters
 // (fused_pair2_fwd, half of the filters per CTA) spreads the same work over
-// more CTAs; its tile height minimises (CTAs per SM, rounded up) x (walk
-// steps x filters per CTA).  TNRD_FUSED_KERNEL=lane|pair|pair2 and
+// more CTAs; its tile height minimises the estimated duration (fused_cost).
+// TNRD_FUSED_KERNEL=lane|pair|pair2 and
 // TNRD_FUSED_TH override the choice (tuning and measurement).
 struct FusedChoice {
     int pair = 0;     // 0: one column per lane; 1: column pairs
@@ -191,9 +206,7 @@ FusedChoice pick_fused(int ks, int nk, int N, int H, int W)
     for (const int* p = list; *p; ++p) {
         const int th = *p;
         if (want_th && th != want_th) continue;
-        const long long tiles = (long long)N * ((H + th - 1) / th) * ((W + tw - 1) / tw);
-        const long long per_sm = (tiles * ns + nsm - 1) / nsm;
-        const double cost = per_sm * (double)(th + 4 * R);
+        const double cost = fused_cost(N, H, W, th, tw, R, ns, 2 * nsm);
         if (cost < best * 0.999) {
             best = cost;
             c.th = th;

@@ -66,7 +66,9 @@ __device__ __forceinline__ void gather_row(float (&vw)[KS], float v, int lane)
 // accumulators -- their phi, shuffles and h updates would reach no stored h
 // row, and the z updates of rows completing before step 2R no used z, so they
 // are left out (the stored values are the same bits).
-template <int KS, int UP, bool INTERIOR, bool FIRST = false>
+// LAST: the walk's final group, which may be partial: steps from mh_hi (the
+// walk's step count) on are not taken.
+template <int KS, int UP, bool INTERIOR, bool FIRST = false, bool LAST = false>
 __device__ __forceinline__ void walk_group(const float* __restrict__ urow, float* __restrict__ hrow,
                                            const float (&kr)[KS][KS], float (&za)[KS],
                                            float (&ha)[KS], int m0, int zrow0, int H, bool col_in,
@@ -77,6 +79,9 @@ __device__ __forceinline__ void walk_group(const float* __restrict__ urow, float
 #pragma unroll
     for (int mm = 0; mm < KS; ++mm) {
         const int m = m0 + mm;
+        if constexpr (LAST) {
+            if (m >= mh_hi) break;
+        }
         const float* row = urow + m * UP;
         float in[KS];
 #pragma unroll
@@ -154,8 +159,8 @@ __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
 
     // Walk geometry.  h rows [hy0, hy0 + nh); step m reads u row hy0 - 2R + m,
     // completes z row hy0 - 3R + m (valid from m = 2R) and h row hy0 - 4R + m
-    // (valid for m in [4R, nh + 4R)).  Steps run in whole groups of KS; the
-    // U buffer has rows for the overhang and its results are never stored.
+    // (valid for m in [4R, nh + 4R)).  Steps run in groups of KS, the last one
+    // stopping at step nh + 4R; the U buffer has rows for a whole last group.
     const int hy0 = ext ? y0 - R : y0;
     const int nh = ext ? TH + 2 * R : TH;
     const int nsteps = nh + 4 * R;
@@ -181,20 +186,28 @@ __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
         float za[KS], ha[KS];
 #pragma unroll
         for (int s = 0; s < KS; ++s) za[s] = ha[s] = 0.0f;
+        // whole groups of KS steps, then the partial last one (if any)
+        int m0 = KS;
         if (!border) {
             walk_group<KS, C::UP, true, true>(urow, hrow, kr, za, ha, 0, zrow0, H, col_in, 2 * R,
                                               4 * R, nsteps, lane, myT, rc);
 #pragma unroll 1
-            for (int m0 = KS; m0 < nsteps; m0 += KS)
+            for (; m0 + KS <= nsteps; m0 += KS)
                 walk_group<KS, C::UP, true>(urow, hrow, kr, za, ha, m0, zrow0, H, col_in, 2 * R,
                                             4 * R, nsteps, lane, myT, rc);
+            if (m0 < nsteps)
+                walk_group<KS, C::UP, true, false, true>(urow, hrow, kr, za, ha, m0, zrow0, H,
+                                                         col_in, 2 * R, 4 * R, nsteps, lane, myT, rc);
         } else {
             walk_group<KS, C::UP, false, true>(urow, hrow, kr, za, ha, 0, zrow0, H, col_in, 2 * R,
                                                4 * R, nsteps, lane, myT, rc);
 #pragma unroll 1
-            for (int m0 = KS; m0 < nsteps; m0 += KS)
+            for (; m0 + KS <= nsteps; m0 += KS)
                 walk_group<KS, C::UP, false>(urow, hrow, kr, za, ha, m0, zrow0, H, col_in, 2 * R,
                                              4 * R, nsteps, lane, myT, rc);
+            if (m0 < nsteps)
+                walk_group<KS, C::UP, false, false, true>(urow, hrow, kr, za, ha, m0, zrow0, H,
+                                                          col_in, 2 * R, 4 * R, nsteps, lane, myT, rc);
         }
         __syncwarp();
     }

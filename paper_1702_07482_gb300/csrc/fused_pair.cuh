@@ -75,7 +75,7 @@ __device__ __forceinline__ void gather_pair(float (&vw)[KS + 1], float v0, float
 // row bookkeeping); urow points at this lane's first u column (2j) of the
 // step-0 row, hrow at its float2 of the h row completed at step 0.  FIRST as
 // in walk_group: the first 2R steps only prime the z accumulators.
-template <int KS, int UP, bool INTERIOR, bool FIRST = false>
+template <int KS, int UP, bool INTERIOR, bool FIRST = false, bool LAST = false>
 __device__ __forceinline__ void pair_group(const float* __restrict__ urow, float2* __restrict__ hrow,
                                            const float (&kr)[KS][KS], float (&za0)[KS],
                                            float (&za1)[KS], float (&ha0)[KS], float (&ha1)[KS],
@@ -87,6 +87,9 @@ __device__ __forceinline__ void pair_group(const float* __restrict__ urow, float
 #pragma unroll
     for (int mm = 0; mm < KS; ++mm) {
         const int m = m0 + mm;
+        if constexpr (LAST) {
+            if (m >= mh_hi) break;   // partial last group
+        }
         const float2* row = reinterpret_cast<const float2*>(urow + m * UP);
         float in[2 * R + 2];   // in[t] = u(row, c0 - R + t)
 #pragma unroll
@@ -199,20 +202,30 @@ __device__ __forceinline__ int pair_tile_walk(const TileJob& j, float* smem, int
         float za0[KS], za1[KS], ha0[KS], ha1[KS];
 #pragma unroll
         for (int s = 0; s < KS; ++s) za0[s] = za1[s] = ha0[s] = ha1[s] = 0.0f;
+        // whole groups of KS steps, then the partial last one (if any)
+        int m0 = KS;
         if (!border) {
             pair_group<KS, C::UP, true, true>(urow, hrow, kr, za0, za1, ha0, ha1, 0, zrow0, H,
                                               col_in0, col_in1, 2 * R, 4 * R, nsteps, lane, myW, rc);
 #pragma unroll 1
-            for (int m0 = KS; m0 < nsteps; m0 += KS)
+            for (; m0 + KS <= nsteps; m0 += KS)
                 pair_group<KS, C::UP, true>(urow, hrow, kr, za0, za1, ha0, ha1, m0, zrow0, H,
                                             col_in0, col_in1, 2 * R, 4 * R, nsteps, lane, myW, rc);
+            if (m0 < nsteps)
+                pair_group<KS, C::UP, true, false, true>(urow, hrow, kr, za0, za1, ha0, ha1, m0,
+                                                         zrow0, H, col_in0, col_in1, 2 * R, 4 * R,
+                                                         nsteps, lane, myW, rc);
         } else {
             pair_group<KS, C::UP, false, true>(urow, hrow, kr, za0, za1, ha0, ha1, 0, zrow0, H,
                                                col_in0, col_in1, 2 * R, 4 * R, nsteps, lane, myW, rc);
 #pragma unroll 1
-            for (int m0 = KS; m0 < nsteps; m0 += KS)
+            for (; m0 + KS <= nsteps; m0 += KS)
                 pair_group<KS, C::UP, false>(urow, hrow, kr, za0, za1, ha0, ha1, m0, zrow0, H,
                                              col_in0, col_in1, 2 * R, 4 * R, nsteps, lane, myW, rc);
+            if (m0 < nsteps)
+                pair_group<KS, C::UP, false, false, true>(urow, hrow, kr, za0, za1, ha0, ha1, m0,
+                                                          zrow0, H, col_in0, col_in1, 2 * R, 4 * R,
+                                                          nsteps, lane, myW, rc);
         }
         __syncwarp();
     }

@@ -33,16 +33,17 @@ cudaError_t launch_one(const StageArgs& a, int N, int nsplit, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Tile heights per filter size: TH + 4R is a multiple of ksize.
+// Tile heights per filter size (as for the one-column kernel).
 #define TNRD_PAIR_CASES(X)                                                         \
     X(3, 4, 17) X(3, 4, 23) X(3, 4, 29) X(5, 24, 17) X(5, 24, 22) X(5, 24, 27)    \
-    X(5, 24, 32) X(7, 48, 16) X(7, 48, 23) X(7, 48, 30) X(7, 48, 37)
+    X(5, 24, 32) X(7, 48, 16) X(7, 48, 23) X(7, 48, 30) X(7, 48, 32) X(7, 48, 37)
 
 }  // namespace
 
 const int* pair_th_list(int ks)
 {
-    static const int l3[] = {17, 23, 29, 0}, l5[] = {17, 22, 27, 32, 0}, l7[] = {16, 23, 30, 37, 0};
+    static const int l3[] = {17, 23, 29, 0}, l5[] = {17, 22, 27, 32, 0},
+                     l7[] = {16, 23, 30, 32, 37, 0};
     static const int none[] = {0};
     return ks == 3 ? l3 : ks == 5 ? l5 : ks == 7 ? l7 : none;
 }
