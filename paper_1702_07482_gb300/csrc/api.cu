@@ -117,66 +117,100 @@ tnrd::RbfConst make_rbf(const tnrd_params* p)
 }
 
 // Estimated duration, in walk steps of one CTA, of one fused stage launch over
-// N images of H x W: tiles of th x tw pixels, `split` CTAs per tile, `slots`
-// CTAs resident at once (two per SM).  A tile in the first or last tile row
-// walks th + 6R steps, the others th + 4R.  When every CTA is resident at once
-// the launch lasts as long as its longest CTA; otherwise the work spreads over
-// the slots, plus half the longest CTA for the tail.
-double fused_cost(int N, int H, int W, int th, int tw, int R, int split, int slots)
+// N images of H x W: tiles of th x tw pixels (border tile rows te, 0: th; see
+// row_tile), `split` CTAs per tile, `slots` CTAs resident at once (two per
+// SM).  A tile in the first or last tile row walks te + 6R steps, the others
+// th + 4R.  When every CTA is resident at once the launch lasts as long as its
+// longest CTA; otherwise the work spreads over the slots, plus half the
+// longest CTA for the tail.
+double fused_cost(int N, int H, int W, int th, int te, int tw, int R, int split, int slots)
 {
-    const long long ty = (H + th - 1) / th, tx = (W + tw - 1) / tw;
+    const long long ty = tnrd::row_tiles(H, th, te), tx = (W + tw - 1) / tw;
     const long long n_ext = ty >= 2 ? 2 : 1;
-    const double w_ext = th + 6 * R, w_int = th + 4 * R;
+    const double w_ext = (te > 0 ? te : th) + 6 * R, w_int = th + 4 * R;
+    const double w_max = ty > n_ext ? std::max(w_ext, w_int) : w_ext;
     const long long ctas = (long long)N * ty * tx * split;
-    if (ctas <= slots) return w_ext;
+    if (ctas <= slots) return w_max;
     const double per_col = n_ext * w_ext + (double)(ty - n_ext) * w_int;
-    return (double)N * tx * split * per_col / slots + 0.5 * w_ext;
+    return (double)N * tx * split * per_col / slots + 0.5 * w_max;
 }
 
-// Pick the fused tile height of least estimated duration (fused_cost).
-int pick_fused_th(int ks, int nk, int N, int H, int W)
+// Row tiling of a fused launch: runtime tile height th, border tile rows te
+// (0: uniform tiles), and the compiled kernel tile height kth >= th.
+struct RowChoice {
+    int th = 0, te = 0, kth = 0;
+    double cost = 1e300;
+};
+
+// The row tiling of least estimated duration over th from the largest
+// compiled tile height down to the smallest, uniform or with border tiles 2R
+// shorter (so that they walk as many steps as interior ones).  Overrides:
+// TNRD_FUSED_TH pins th, TNRD_FUSED_ROWS=uniform|short pins the tiling.
+RowChoice pick_rows(const int* list, int R, int N, int H, int W, int tw, int split, int nsm)
 {
-    const int* list = tnrd::fused_th_list(ks);
-    if (const char* env = std::getenv("TNRD_FUSED_TH")) {   // tuning override
-        const int v = std::atoi(env);
-        for (const int* p = list; *p; ++p)
-            if (*p == v) return v;
+    int kmin = 1 << 30, kmax = 0;
+    for (const int* p = list; *p; ++p) {
+        kmin = std::min(kmin, *p);
+        kmax = std::max(kmax, *p);
     }
-    (void)nk;
+    int want = 0, rows = -1;   // rows: -1 either, 0 uniform, 1 short border tiles
+    if (const char* env = std::getenv("TNRD_FUSED_TH")) want = std::atoi(env);
+    if (const char* env = std::getenv("TNRD_FUSED_ROWS"))
+        rows = !std::strcmp(env, "uniform") ? 0 : !std::strcmp(env, "short") ? 1 : -1;
+    if (want > kmax || (want > 0 && want < 2 * R + 1)) want = 0;
+    RowChoice best;
+    for (int th = want ? want : kmax; th >= (want ? want : kmin); --th) {
+        int kth = 0;
+        for (const int* p = list; *p; ++p)
+            if (*p >= th && (kth == 0 || *p < kth)) kth = *p;
+        for (int shrt = 0; shrt < 2; ++shrt) {
+            if (rows >= 0 && shrt != rows) continue;
+            const int te = shrt ? th - 2 * R : 0;
+            if (shrt && (te < 2 * R || H < 2 * te + th)) continue;
+            const double cost = fused_cost(N, H, W, th, te, tw, R, split, 2 * nsm);
+            if (cost < best.cost * 0.999) {
+                best.th = th;
+                best.te = te;
+                best.kth = kth;
+                best.cost = cost;
+            }
+        }
+    }
+    if (best.kth == 0) {   // nothing allowed by the overrides: uniform, largest tile height
+        best.th = best.kth = kmax;
+        best.te = 0;
+    }
+    return best;
+}
+
+int device_sm_count()
+{
     int nsm = 148;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int R = ks / 2, tw = 32 - 2 * R;
-    double best = 1e300;
-    int best_th = list[0];
-    for (const int* p = list; *p; ++p) {
-        const int th = *p;
-        const double cost = fused_cost(N, H, W, th, tw, R, 1, 2 * nsm);
-        if (cost < best * 0.999) {
-            best = cost;
-            best_th = th;
-        }
-    }
-    return best_th;
+    return nsm;
 }
 
 // Fused forward kernel choice.  The one-column-per-lane kernel
 // (fused_stage_fwd) is the default.  When it cannot give every SM two CTAs
 // (a single small image), the column-pair kernel on two-CTA clusters
 // (fused_pair2_fwd, half of the filters per CTA) spreads the same work over
-// more CTAs; its tile height minimises the estimated duration (fused_cost).
-// TNRD_FUSED_KERNEL=lane|pair|pair2 and
-// TNRD_FUSED_TH override the choice (tuning and measurement).
+// more CTAs.  Either way the row tiling minimises the estimated duration
+// (pick_rows).  TNRD_FUSED_KERNEL=lane|pair|pair2, TNRD_FUSED_TH and
+// TNRD_FUSED_ROWS override the choice (tuning and measurement).
 struct FusedChoice {
     int pair = 0;     // 0: one column per lane; 1: column pairs
-    int th = 0;
+    int th = 0;       // runtime tile height
+    int te = 0;       // border tile rows (0: uniform tiles)
+    int kth = 0;      // compiled tile height of the kernel (>= th)
     int nsplit = 1;
     int tw = 0;
 };
 
 FusedChoice pick_fused(int ks, int nk, int N, int H, int W)
 {
+    (void)nk;
     FusedChoice c;
     int force = -1;   // -1 auto, 0 lane, 1 pair, 2 pair2
     if (const char* env = std::getenv("TNRD_FUSED_KERNEL")) {
@@ -185,33 +219,22 @@ FusedChoice pick_fused(int ks, int nk, int N, int H, int W)
         else if (!std::strcmp(env, "pair2")) force = 2;
     }
     const int R = ks / 2;
-    int nsm = 148;
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    c.th = pick_fused_th(ks, nk, N, H, W);
+    const int nsm = device_sm_count();
     c.tw = 32 - 2 * R;
-    const long long lane_ctas = (long long)N * ((H + c.th - 1) / c.th) * ((W + c.tw - 1) / c.tw);
+    RowChoice rc = pick_rows(tnrd::fused_th_list(ks), R, N, H, W, c.tw, 1, nsm);
+    c.th = rc.th;
+    c.te = rc.te;
+    c.kth = rc.kth;
+    const long long lane_ctas = (long long)N * tnrd::row_tiles(H, c.th, c.te) * ((W + c.tw - 1) / c.tw);
     if (force == 0 || (force < 0 && lane_ctas >= 2LL * nsm)) return c;
     const int ns = (force == 1) ? 1 : 2;
-    const int* list = tnrd::pair_th_list(ks);
-    int want_th = 0;
-    if (const char* env = std::getenv("TNRD_FUSED_TH")) want_th = std::atoi(env);
-    const int tw = 64 - 2 * R;
-    double best = 1e300;
     c.pair = 1;
     c.nsplit = ns;
-    c.tw = tw;
-    c.th = list[0];
-    for (const int* p = list; *p; ++p) {
-        const int th = *p;
-        if (want_th && th != want_th) continue;
-        const double cost = fused_cost(N, H, W, th, tw, R, ns, 2 * nsm);
-        if (cost < best * 0.999) {
-            best = cost;
-            c.th = th;
-        }
-    }
+    c.tw = 64 - 2 * R;
+    rc = pick_rows(tnrd::pair_th_list(ks), R, N, H, W, c.tw, ns, nsm);
+    c.th = rc.th;
+    c.te = rc.te;
+    c.kth = rc.kth;
     return c;
 }
 
@@ -313,13 +336,11 @@ tnrd_status tnrd_forward_kernel(const tnrd_params* p, int N, int H, int W, tnrd_
     if (algo == TNRD_ALGO_FUSED) {
         const FusedChoice c = pick_fused(ks, nk, N, H, W);
         const char* staging = tnrd::tma_staging_enabled() ? "tma" : "gather";
-        if (c.pair)
-            std::snprintf(buf, len, "%s<%d,%d,%d> tiles %dx%d, %s staging",
-                          c.nsplit == 2 ? "fused_pair2_fwd" : "fused_pair_fwd", ks, nk, c.th, c.th,
-                          c.tw, staging);
-        else
-            std::snprintf(buf, len, "fused_stage_fwd<%d,%d,%d> tiles %dx%d, %s staging", ks, nk, c.th,
-                          c.th, c.tw, staging);
+        char rows[40] = "";
+        if (c.te > 0) std::snprintf(rows, sizeof rows, " (border rows %d)", c.te);
+        std::snprintf(buf, len, "%s<%d,%d,%d> tiles %dx%d%s, %s staging",
+                      !c.pair ? "fused_stage_fwd" : c.nsplit == 2 ? "fused_pair2_fwd" : "fused_pair_fwd",
+                      ks, nk, c.kth, c.th, c.tw, rows, staging);
     } else if (algo == TNRD_ALGO_UNFUSED) {
         std::snprintf(buf, len, "unf_bank_phi + unf_adjoint + unf_prox <%d,%d>", ks, nk);
     } else if (algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16) {
@@ -401,7 +422,9 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.W = W;
             a.pitch = pitch;
             a.tiles_x = (W + fc.tw - 1) / fc.tw;
-            a.tiles_y = (H + fc.th - 1) / fc.th;
+            a.tiles_y = tnrd::row_tiles(H, fc.th, fc.te);
+            a.th = fc.th;
+            a.te = fc.te;
             a.k = kt;
             a.w = wt;
             a.lam = p->lambda + t;
@@ -409,8 +432,8 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.dterm = p->data_term;
             a.proj_c = p->proj_c;
             a.rc = rc;
-            e = fc.pair ? tnrd::launch_pair_fwd(ks, nk, fc.th, fc.nsplit, a, N, stream)
-                        : tnrd::launch_fused_fwd(ks, nk, fc.th, a, N, stream);
+            e = fc.pair ? tnrd::launch_pair_fwd(ks, nk, fc.kth, fc.nsplit, a, N, stream)
+                        : tnrd::launch_fused_fwd(ks, nk, fc.kth, a, N, stream);
         } else if (algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16) {
             tnrd::StageArgs a{};
             const int tw = 32 - 2 * (ks / 2), tth = tnrd::tc_tile_h(ks, tc_nb);

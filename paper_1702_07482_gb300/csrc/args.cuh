@@ -20,6 +20,7 @@ struct StageArgs {
     int dterm;             // tnrd_data_term of the model
     float proj_c;          // projection floor (dterm 2)
     RbfConst rc;
+    int th, te;            // row tiling (row_tile): tile height <= the kernel's TH, short border tiles
     int use_tma;           // umap describes u_in: stage tiles with bulk tensor copies
     int* err;              // device status word (TNRD_ERR_TIMEOUT on a copy that never landed)
     CUtensorMap umap;      // [N][H][pitch] float32 view of u_in, box of the kernel's staged tile
@@ -39,6 +40,7 @@ struct TileJob {
     int dterm;
     float proj_c;
     const RbfConst* rc;
+    int th = 0, te = 0;                  // row tiling (row_tile); th <= the kernel's TH
     const CUtensorMap* umap = nullptr;   // tensor map of u_in (null: symmetric gather)
     int img = 0;                         // z coordinate of this image in umap
     int* err = nullptr;                  // status word for a copy that timed out
@@ -94,6 +96,59 @@ __device__ __forceinline__ int tile_split(int t, int T, int n, int nt, int R)
     if (t >= nt) return n;
     if (t == nt - 1) return min(t * T, n - R);
     return t * T;
+}
+
+// Row range of tile t of nt along an image axis of n rows.
+//   te == 0: uniform tiles of th rows, the last shifted back to end at n
+//            (tile_origin / tile_split).
+//   te > 0 (short border tiles; requires n >= 2 te + th): the first tile is
+//            [0, te), the last [n - te, n), the others th rows from te on, the
+//            last of them shifted back to end at n - te.  With te = th - 2R a
+//            border tile walks as many steps as an interior one (th + 4R).
+// Tile t covers [y0, y0 + h) and writes [wy0, wy1); the written ranges
+// partition [0, n), rows within R of a border go to the border tiles, and the
+// last interior tile writes at least 2R rows.
+struct RowTile {
+    int y0, h, wy0, wy1;
+};
+
+__host__ __device__ __forceinline__ int row_tiles(int n, int th, int te)
+{
+    return te > 0 ? 2 + (n - 2 * te + th - 1) / th : (n + th - 1) / th;
+}
+
+__device__ __forceinline__ int row_split_short(int s, int nt, int n, int th, int te, int R)
+{
+    if (s <= 0) return 0;
+    if (s >= nt) return n;
+    if (s == nt - 1) return n - te;
+    const int v = te + (s - 1) * th;
+    return (s == nt - 2) ? min(v, n - te - 2 * R) : v;
+}
+
+__device__ __forceinline__ RowTile row_tile(int t, int nt, int n, int th, int te, int R)
+{
+    RowTile r;
+    if (te <= 0) {
+        r.y0 = tile_origin(t, th, n);
+        r.h = th;
+        r.wy0 = tile_split(t, th, n, nt, R);
+        r.wy1 = tile_split(t + 1, th, n, nt, R);
+        return r;
+    }
+    if (t == 0) {
+        r.y0 = 0;
+        r.h = te;
+    } else if (t == nt - 1) {
+        r.y0 = n - te;
+        r.h = te;
+    } else {
+        r.y0 = min(te + (t - 1) * th, n - te - th);
+        r.h = th;
+    }
+    r.wy0 = row_split_short(t, nt, n, th, te, R);
+    r.wy1 = row_split_short(t + 1, nt, n, th, te, R);
+    return r;
 }
 
 struct UnfArgs {

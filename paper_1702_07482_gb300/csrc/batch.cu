@@ -86,6 +86,8 @@ batch_persistent_fwd(const __grid_constant__ BatchArgs a)
             j.pitch = im.pitch;
             j.tiles_x = im.tiles_x;
             j.tiles_y = im.tiles_y;
+            j.th = TH;
+            j.te = 0;
             j.ty = ty;
             j.tx = tx;
             j.k = ps.k + (size_t)t * NK * KS * KS;
@@ -131,6 +133,8 @@ batch_stage_fwd(const __grid_constant__ BatchArgs a, int t)
     j.pitch = im.pitch;
     j.tiles_x = im.tiles_x;
     j.tiles_y = im.tiles_y;
+    j.th = TH;
+    j.te = 0;
     j.ty = ti.y / im.tiles_x;
     j.tx = ti.y - j.ty * im.tiles_x;
     j.k = ps.k + (size_t)t * NK * KS * KS;

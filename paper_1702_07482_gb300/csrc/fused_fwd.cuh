@@ -142,7 +142,9 @@ __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ty = j.ty, tx = j.tx;
     const int H = j.H, W = j.W;
-    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
+    // rows of this tile (runtime height th <= TH; border tile rows te, if set)
+    const RowTile rt = row_tile(ty, j.tiles_y, H, min(j.th, TH), min(j.te, TH), R);
+    const int y0 = rt.y0, x0 = tile_origin(tx, TW, W);
     const bool ext = (ty == 0) || (ty == j.tiles_y - 1);
     const bool border = ext || (tx == 0) || (tx == j.tiles_x - 1);
     const RbfConst& rc = *j.rc;
@@ -162,7 +164,7 @@ __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
     // (valid for m in [4R, nh + 4R)).  Steps run in groups of KS, the last one
     // stopping at step nh + 4R; the U buffer has rows for a whole last group.
     const int hy0 = ext ? y0 - R : y0;
-    const int nh = ext ? TH + 2 * R : TH;
+    const int nh = ext ? rt.h + 2 * R : rt.h;
     const int nsteps = nh + 4 * R;
     const int ub0 = ext ? 0 : R;                         // U buffer row of step 0
     const float* urow = sU + ub0 * C::UP + xoff + lane;
@@ -215,9 +217,9 @@ __device__ __forceinline__ void stage_tile(const TileJob& j, float* smem)
 
     // Epilogue: g = fold(sum over warps of h), u_t = prox(u_{t-1} - g).
     const float lam = __ldg(j.lam);
-    const int wy0 = tile_split(ty, TH, H, j.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, j.tiles_y, R);
+    const int wy0 = rt.wy0, wy1 = rt.wy1;
     const int wx0 = tile_split(tx, TW, W, j.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, j.tiles_x, R);
-    for (int idx = threadIdx.x; idx < TH * TW; idx += C::NTHREADS) {
+    for (int idx = threadIdx.x; idx < rt.h * TW; idx += C::NTHREADS) {
         const int qy = y0 + idx / TW, qx = x0 + idx % TW;
         if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
         int sy[2], sx[2];
@@ -262,6 +264,8 @@ fused_stage_fwd(const __grid_constant__ StageArgs a)
     j.pitch = a.pitch;
     j.tiles_x = a.tiles_x;
     j.tiles_y = a.tiles_y;
+    j.th = a.th > 0 ? a.th : TH;
+    j.te = a.te;
     j.ty = blockIdx.x / a.tiles_x;
     j.tx = blockIdx.x - j.ty * a.tiles_x;
     j.k = a.k;

@@ -166,7 +166,8 @@ __device__ __forceinline__ int pair_tile_walk(const TileJob& j, float* smem, int
     float* myW = myK + C::KPAD;
     const int ty = j.ty, tx = j.tx;
     const int H = j.H, W = j.W;
-    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
+    const RowTile rt = row_tile(ty, j.tiles_y, H, min(j.th, TH), min(j.te, TH), R);
+    const int y0 = rt.y0, x0 = tile_origin(tx, TW, W);
     const bool ext = (ty == 0) || (ty == j.tiles_y - 1);
     const bool border = ext || (tx == 0) || (tx == j.tiles_x - 1);
     const RbfConst& rc = *j.rc;
@@ -178,7 +179,7 @@ __device__ __forceinline__ int pair_tile_walk(const TileJob& j, float* smem, int
     if (xoff < 0) return -1;
 
     const int hy0 = ext ? y0 - R : y0;
-    const int nh = ext ? TH + 2 * R : TH;
+    const int nh = ext ? rt.h + 2 * R : rt.h;
     const int nsteps = nh + 4 * R;
     const int ub0 = ext ? 0 : R;
     const float* urow = sU + ub0 * C::UP + xoff + 2 * lane;
@@ -247,13 +248,14 @@ __device__ __forceinline__ void pair_tile_epilogue(const TileJob& j, const float
     const float* sH = smem + ((C::U_FL + 3) & ~3);
     const int ty = j.ty, tx = j.tx;
     const int H = j.H, W = j.W;
-    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
+    const RowTile rt = row_tile(ty, j.tiles_y, H, min(j.th, TH), min(j.te, TH), R);
+    const int y0 = rt.y0, x0 = tile_origin(tx, TW, W);
     const bool ext = (ty == 0) || (ty == j.tiles_y - 1);
     const bool border = ext || (tx == 0) || (tx == j.tiles_x - 1);
     const float lam = __ldg(j.lam);
-    const int wy0 = tile_split(ty, TH, H, j.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, j.tiles_y, R);
+    const int wy0 = rt.wy0, wy1 = rt.wy1;
     const int wx0 = tile_split(tx, TW, W, j.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, j.tiles_x, R);
-    for (int idx = first; idx < TH * TW; idx += step) {
+    for (int idx = first; idx < rt.h * TW; idx += step) {
         const int qy = y0 + idx / TW, qx = x0 + idx % TW;
         if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
         int sy[2], sx[2];
@@ -274,8 +276,13 @@ __device__ __forceinline__ void pair_tile_epilogue(const TileJob& j, const float
 #pragma unroll
                 for (int wq = 0; wq < C::NWARP; ++wq) hs += sH[wq * C::PW_FL + o];
                 if constexpr (NSPLIT == 2) {
+                    // the other CTA's filters summed apart and added last: the
+                    // result (a + b = b + a) does not depend on which CTA of the
+                    // cluster finishes the pixel, i.e. not on the tiling
+                    float hr = 0.0f;
 #pragma unroll
-                    for (int wq = 0; wq < C::NWARP; ++wq) hs += remote[wq * C::PW_FL + o];
+                    for (int wq = 0; wq < C::NWARP; ++wq) hr += remote[wq * C::PW_FL + o];
+                    hs += hr;
                 }
                 g += hs;
             }
@@ -286,7 +293,7 @@ __device__ __forceinline__ void pair_tile_epilogue(const TileJob& j, const float
     }
 }
 
-__device__ __forceinline__ TileJob pair_job(const StageArgs& a, int tile)
+__device__ __forceinline__ TileJob pair_job(const StageArgs& a, int tile, int th_kernel)
 {
     const int n = blockIdx.y;
     TileJob j;
@@ -298,6 +305,8 @@ __device__ __forceinline__ TileJob pair_job(const StageArgs& a, int tile)
     j.pitch = a.pitch;
     j.tiles_x = a.tiles_x;
     j.tiles_y = a.tiles_y;
+    j.th = a.th > 0 ? a.th : th_kernel;
+    j.te = a.te;
     j.ty = tile / a.tiles_x;
     j.tx = tile - j.ty * a.tiles_x;
     j.k = a.k;
@@ -319,7 +328,7 @@ __global__ void __launch_bounds__(PairCfg<KS, NK, TH, 1>::NTHREADS, 2)
 fused_pair_fwd(const __grid_constant__ StageArgs a)
 {
     extern __shared__ __align__(128) float smem[];
-    const TileJob j = pair_job(a, blockIdx.x);
+    const TileJob j = pair_job(a, blockIdx.x, TH);
     const int xoff = pair_tile_walk<KS, NK, TH, 1>(j, smem, 0);
     if (xoff < 0) return;
     __syncthreads();
@@ -338,7 +347,7 @@ fused_pair2_fwd(const __grid_constant__ StageArgs a)
     __shared__ int s_xoff;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const TileJob j = pair_job(a, blockIdx.x >> 1);
+    const TileJob j = pair_job(a, blockIdx.x >> 1, TH);
     const int xoff = pair_tile_walk<KS, NK, TH, 2>(j, smem, rank);
     if (threadIdx.x == 0) s_xoff = xoff;
     cl.sync();   // both CTAs' h buffers complete and visible in the cluster

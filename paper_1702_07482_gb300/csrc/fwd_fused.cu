@@ -10,6 +10,7 @@ template <int KS, int NK, int TH>
 cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
 {
     using C = FusedCfg<KS, NK, TH>;
+    if (a.th > TH || a.te > a.th || a.te < 0) return cudaErrorInvalidValue;   // buffers hold TH rows
     const size_t smem = C::smem_bytes(a.nrbf);
     cudaError_t e = cudaFuncSetAttribute(fused_stage_fwd<KS, NK, TH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -10,6 +10,7 @@ namespace {
 template <int KS, int NK, int TH>
 cudaError_t launch_one(const StageArgs& a, int N, int nsplit, cudaStream_t s)
 {
+    if (a.th > TH || a.te > a.th || a.te < 0) return cudaErrorInvalidValue;   // buffers hold TH rows
     if (nsplit == 2) {
         using C = PairCfg<KS, NK, TH, 2>;
         cudaError_t e = cudaFuncSetAttribute(fused_pair2_fwd<KS, NK, TH>,

@@ -1,0 +1,93 @@
+"""Row tilings of the fused forward stage: runtime tile heights below the
+compiled one, and short border tile rows (the first and last tile rows 2R
+shorter, so that every tile walks th + 4R steps).
+
+Each output pixel's sums run in the same order whatever tile computes it, so
+every tiling must give the same bits; one tiling per case is also checked
+against the FP64 oracle.  Heights include the smallest image that allows short
+border rows (H = 2 te + th), ragged last tiles, a last interior tile shifted
+back onto its neighbour, and several images per call.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from _cases import TOL_U_FP32, case
+
+pytestmark = pytest.mark.gpu
+
+ENV = ("TNRD_FUSED_KERNEL", "TNRD_FUSED_TH", "TNRD_FUSED_ROWS")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1702_07482_gb300 import binding, build
+    build.build()
+    binding.load()
+
+
+def _run(p, f, **env):
+    from paper_1702_07482_gb300 import binding as B
+    from paper_1702_07482_gb300 import ops
+    old = {k: os.environ.get(k) for k in ENV}
+    for k in ENV:
+        os.environ.pop(k, None)
+    os.environ.update({k: str(v) for k, v in env.items()})
+    try:
+        m = ops.Model.create(p.filters, p.rbf_w, p.lam, p.mu0, p.delta, p.gamma)
+        N, H, W = f.shape
+        name = B.tnrd_forward_kernel(m.params(), N, H, W, B.ALGO["fused"])
+        ft = torch.tensor(f, dtype=torch.float32, device="cuda")
+        out = ops.forward(m, ft)
+        torch.cuda.synchronize()
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return out[..., :W], name
+
+
+# (H, W, N): 99 = 2 * 31 + 37 (short rows just allowed at th 37), 100, 150
+# (ragged), 241 (last interior tile shifted back), 3 images of 77 x 50.
+SIZES = [(99, 70, 1), (100, 129, 1), (150, 61, 1), (241, 90, 1), (77, 50, 3)]
+
+
+@pytest.mark.parametrize("kernel", ["lane", "pair", "pair2"])
+@pytest.mark.parametrize("H,W,N", SIZES)
+def test_row_tilings_give_the_same_bits(kernel, H, W, N):
+    p, f = case(H, W, 7, 48, 2, L=1, N=N, cfg=501 + H + W)
+    ref, _ = _run(p, f, TNRD_FUSED_KERNEL=kernel, TNRD_FUSED_TH=37, TNRD_FUSED_ROWS="uniform")
+    for th in (16, 23, 33, 37):
+        for rows in ("uniform", "short"):
+            got, name = _run(p, f, TNRD_FUSED_KERNEL=kernel, TNRD_FUSED_TH=th, TNRD_FUSED_ROWS=rows)
+            assert torch.equal(got, ref), name
+    from paper_1702_07482_gb300 import binding as B
+    assert B.tnrd_device_status() == 0
+
+
+@pytest.mark.parametrize("kernel", ["lane", "pair2"])
+def test_short_border_rows_match_oracle(kernel):
+    import oracle
+    p, f = case(130, 90, 7, 48, 2, L=1, N=1, cfg=560)
+    got, name = _run(p, f, TNRD_FUSED_KERNEL=kernel, TNRD_FUSED_TH=33, TNRD_FUSED_ROWS="short")
+    assert "border rows 27" in name
+    ref = oracle.forward(f[0], p)[-1]
+    assert np.abs(got[0].double().cpu().numpy() - ref).max() <= TOL_U_FP32
+
+
+def test_512_image_tiling_is_one_wave():
+    """The 512 x 512 workload: 33-row tiles with 27-row border rows, 16 tile
+    rows x 9 tile columns x 2 CTAs = 288 CTAs, one per slot of 152 SMs."""
+    import synth
+    from paper_1702_07482_gb300 import binding as B
+    from paper_1702_07482_gb300 import ops
+    q = synth.params(2, 7, 48, seed=3)
+    prm = ops.Model.create(q.filters, q.rbf_w, q.lam).params()
+    if torch.cuda.get_device_properties(0).multi_processor_count < 144:
+        pytest.skip("fewer than 144 SMs")
+    name = B.tnrd_forward_kernel(prm, 1, 512, 512, B.ALGO["fused"])
+    assert name.startswith("fused_pair2_fwd<7,48,37> tiles 33x58 (border rows 27)"), name
