@@ -192,7 +192,8 @@ int occupancy_one(int nrbf)
 
 #define TNRD_BATCH_CASES(X)                                                         \
     X(3, 4, 17) X(3, 4, 23) X(3, 4, 29) X(5, 24, 17) X(5, 24, 22) X(5, 24, 27)     \
-    X(5, 24, 32) X(7, 48, 16) X(7, 48, 23) X(7, 48, 30) X(7, 48, 32) X(7, 48, 37)
+    X(5, 24, 32) X(7, 48, 16) X(7, 48, 23) X(7, 48, 30) X(7, 48, 32) X(7, 48, 37)  \
+    X(7, 48, 45)
 
 }  // namespace
 

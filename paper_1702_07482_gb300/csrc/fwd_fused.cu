@@ -39,10 +39,12 @@ int occupancy_one(int nrbf)
 
 // Tile heights per filter size.  Most have TH + 4R a multiple of ksize (the
 // walk of an interior tile has no partial group of steps); 7x7 also has 32,
-// which tiles 512 rows in 16 (a single 512^2 image in one wave).
+// which tiles 512 rows in 16 (a single 512^2 image in one wave), and 45 (the
+// largest with two CTAs per SM: four tile rows for 180-row crops).
 #define TNRD_FUSED_CASES(X)                                                         \
     X(3, 4, 17) X(3, 4, 23) X(3, 4, 29) X(5, 24, 17) X(5, 24, 22) X(5, 24, 27)     \
-    X(5, 24, 32) X(7, 48, 16) X(7, 48, 23) X(7, 48, 30) X(7, 48, 32) X(7, 48, 37)
+    X(5, 24, 32) X(7, 48, 16) X(7, 48, 23) X(7, 48, 30) X(7, 48, 32) X(7, 48, 37)  \
+    X(7, 48, 45)
 
 }  // namespace
 

@@ -16,7 +16,7 @@ inline const int* fused_th_list(int ks)
 {
     static const int k3[] = {17, 23, 29, 0};
     static const int k5[] = {17, 22, 27, 32, 0};
-    static const int k7[] = {16, 23, 30, 32, 37, 0};
+    static const int k7[] = {16, 23, 30, 32, 37, 45, 0};
     return ks == 3 ? k3 : ks == 5 ? k5 : k7;
 }
 

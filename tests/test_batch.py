@@ -130,7 +130,7 @@ def test_autotuned_plan_and_user_graph_capture():
     from paper_1702_07482_gb300 import binding as B
     params, models, fs, fts, uts, imgs = _make(T=2, cfg=163)
     plan = B.Plan(imgs, [m.params() for m in models], autotune=True)
-    assert plan.tile_height in (16, 23, 30, 32, 37)
+    assert plan.tile_height in (16, 23, 30, 32, 37, 45)
     s = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):

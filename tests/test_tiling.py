@@ -61,7 +61,7 @@ SIZES = [(99, 70, 1), (100, 129, 1), (150, 61, 1), (241, 90, 1), (77, 50, 3)]
 def test_row_tilings_give_the_same_bits(kernel, H, W, N):
     p, f = case(H, W, 7, 48, 2, L=1, N=N, cfg=501 + H + W)
     ref, _ = _run(p, f, TNRD_FUSED_KERNEL=kernel, TNRD_FUSED_TH=37, TNRD_FUSED_ROWS="uniform")
-    for th in (16, 23, 33, 37):
+    for th in (16, 23, 33, 37, 45):
         for rows in ("uniform", "short"):
             got, name = _run(p, f, TNRD_FUSED_KERNEL=kernel, TNRD_FUSED_TH=th, TNRD_FUSED_ROWS=rows)
             assert torch.equal(got, ref), name
