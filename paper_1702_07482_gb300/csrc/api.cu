@@ -176,9 +176,11 @@ RowChoice pick_rows(const int* list, int R, int N, int H, int W, int tw, int spl
             }
         }
     }
-    if (best.kth == 0) {   // nothing allowed by the overrides: uniform, largest tile height
-        best.th = best.kth = kmax;
+    if (best.kth == 0) {   // the overrides allow nothing: uniform tiles of the pinned (or largest) height
+        best.th = want ? want : kmax;
         best.te = 0;
+        for (const int* p = list; *p; ++p)
+            if (*p >= best.th && (best.kth == 0 || *p < best.kth)) best.kth = *p;
     }
     return best;
 }

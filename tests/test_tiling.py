@@ -16,8 +16,6 @@ import torch
 
 from _cases import TOL_U_FP32, case
 
-pytestmark = pytest.mark.gpu
-
 ENV = ("TNRD_FUSED_KERNEL", "TNRD_FUSED_TH", "TNRD_FUSED_ROWS")
 
 
@@ -56,6 +54,7 @@ def _run(p, f, **env):
 SIZES = [(99, 70, 1), (100, 129, 1), (150, 61, 1), (241, 90, 1), (77, 50, 3)]
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("kernel", ["lane", "pair", "pair2"])
 @pytest.mark.parametrize("H,W,N", SIZES)
 def test_row_tilings_give_the_same_bits(kernel, H, W, N):
@@ -69,6 +68,7 @@ def test_row_tilings_give_the_same_bits(kernel, H, W, N):
     assert B.tnrd_device_status() == 0
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("kernel", ["lane", "pair2"])
 def test_short_border_rows_match_oracle(kernel):
     import oracle
@@ -79,6 +79,7 @@ def test_short_border_rows_match_oracle(kernel):
     assert np.abs(got[0].double().cpu().numpy() - ref).max() <= TOL_U_FP32
 
 
+@pytest.mark.gpu
 def test_512_image_tiling_is_one_wave():
     """The 512 x 512 workload: 33-row tiles with 27-row border rows, 16 tile
     rows x 9 tile columns x 2 CTAs = 288 CTAs, one per slot of 152 SMs."""
@@ -91,3 +92,49 @@ def test_512_image_tiling_is_one_wave():
         pytest.skip("fewer than 144 SMs")
     name = B.tnrd_forward_kernel(prm, 1, 512, 512, B.ALGO["fused"])
     assert name.startswith("fused_pair2_fwd<7,48,37> tiles 33x58 (border rows 27)"), name
+
+
+@pytest.mark.parametrize("N,H,W", [(1, 512, 512), (32, 180, 180), (16, 2048, 2048), (1, 128, 128),
+                                   (1, 97, 65), (1, 7, 7), (4, 512, 512), (3, 1000, 333)])
+@pytest.mark.parametrize("ks,nk", [(7, 48), (5, 24), (3, 4)])
+def test_tiling_choice_host_only(N, H, W, ks, nk):
+    """Host-only (no GPU): the row tiling named by tnrd_forward_kernel keeps the
+    runtime tile height within the compiled one, uses short border rows only
+    where the image holds two of them and a full interior tile (te = th - 2R),
+    and honours the overrides."""
+    import re
+    import synth
+    from paper_1702_07482_gb300 import binding as B
+    from paper_1702_07482_gb300 import ops
+    q = synth.params(1, ks, nk, seed=5)
+    prm = ops.Model.create(q.filters, q.rbf_w, q.lam, device="cpu").params()
+    R = ks // 2
+    old = {k: os.environ.pop(k, None) for k in ENV}
+    try:
+        name = B.tnrd_forward_kernel(prm, N, H, W, B.ALGO["fused"])
+        m = re.match(r"(fused_stage_fwd|fused_pair2_fwd|fused_pair_fwd)<(\d+),(\d+),(\d+)> "
+                     r"tiles (\d+)x(\d+)(?: \(border rows (\d+)\))?, (tma|gather) staging$", name)
+        assert m, name
+        kth, th, tw = int(m.group(4)), int(m.group(5)), int(m.group(6))
+        assert (int(m.group(2)), int(m.group(3))) == (ks, nk)
+        assert 2 * R < th <= kth
+        assert tw == (32 if m.group(1) == "fused_stage_fwd" else 64) - 2 * R
+        if m.group(7):
+            te = int(m.group(7))
+            assert te == th - 2 * R and H >= 2 * te + th
+        for rows in ("uniform", "short"):
+            os.environ["TNRD_FUSED_ROWS"] = rows
+            os.environ["TNRD_FUSED_TH"] = str(kth)
+            n2 = B.tnrd_forward_kernel(prm, N, H, W, B.ALGO["fused"])
+            te2 = re.search(r"border rows (\d+)", n2)
+            if rows == "uniform" or H < 2 * (kth - 2 * R) + kth:
+                assert te2 is None, n2
+                assert f"tiles {kth}x" in n2, n2
+            else:
+                assert te2 and int(te2.group(1)) == kth - 2 * R, n2
+    finally:
+        for k in ENV:
+            os.environ.pop(k, None)
+        for k, v in old.items():
+            if v is not None:
+                os.environ[k] = v
