@@ -4,7 +4,9 @@
 // live only in registers; u_{t-1} is staged once per tile in shared memory and
 // only u_t is written to HBM.
 //
-// Tile: TH rows x TW = 32 - 2R output columns, R = ksize/2.  Warp lane j owns
+// Tile: th rows (runtime, at most the compiled TH; the first and last tile
+// rows may be shorter, see row_tile) x TW = 32 - 2R output columns, R =
+// ksize/2.  Warp lane j owns
 // z-column x0 - R + j, so the 32 lanes cover the tile plus the R-wide column
 // halo that the adjoint needs.  Each warp owns nfilt/NWARP filters; for each
 // filter it walks down its columns once ("walk"), one input row per step:
