@@ -111,6 +111,19 @@ def forward(model: Model, f: torch.Tensor, keep_stages: bool = False, algo: str 
     return out
 
 
+def forward_band(model: Model, f: torch.Tensor, world: int, rank: int, algo: str = "fused"):
+    """u_T of this rank's row band of one image f ([H][W] float32 CUDA), from
+    the cascade on the band plus its ghost rows (shard.band_rows).  Returns
+    (rows [own1 - own0][W], own0, own1).  No exchange between ranks."""
+    from .shard import band_rows
+    H, W = f.shape[-2], f.shape[-1]
+    own0, own1, g0, g1 = band_rows(H, world, rank, model.ksize, model.T)
+    if own1 <= own0:
+        return f.new_empty((0, W)), own0, own1
+    u = forward(model, f[..., g0:g1, :].contiguous(), algo=algo)
+    return u[..., own0 - g0:own1 - g0, :W].reshape(own1 - own0, W), own0, own1
+
+
 def backward(model: Model, f: torch.Tensor, u_stages: torch.Tensor, grad_uT: torch.Tensor,
              want_grad_u0: bool = True, W: int | None = None, workspace=None):
     """Gradients (grad_u0, grad_filters, grad_rbf_w, grad_lambda) given dL/du_T.

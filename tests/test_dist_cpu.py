@@ -113,3 +113,72 @@ def test_allreduce_is_noop_without_process_group():
     t.grad = torch.tensor([1.0, 2.0, 3.0])
     allreduce_gradients([t])
     assert torch.equal(t.grad, torch.tensor([1.0, 2.0, 3.0]))
+
+
+def test_band_rows_partition():
+    from paper_1702_07482_gb300.shard import band_rows
+    for H in (1, 7, 37, 100, 513):
+        for world in (1, 2, 3, 8):
+            for ks, T in ((3, 2), (7, 5)):
+                bands = [band_rows(H, world, r, ks, T) for r in range(world)]
+                owned = [row for o0, o1, _, _ in bands for row in range(o0, o1)]
+                assert owned == list(range(H))
+                sizes = [o1 - o0 for o0, o1, _, _ in bands]
+                assert max(sizes) - min(sizes) <= 1
+                ghost = 2 * (ks // 2) * T
+                for o0, o1, g0, g1 in bands:
+                    assert g0 == max(0, o0 - ghost) and g1 == min(H, o1 + ghost)
+    with pytest.raises(ValueError):
+        band_rows(10, 2, 2, 3, 1)
+
+
+def _band_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    import oracle
+    import synth
+    from paper_1702_07482_gb300.shard import band_rows, gather_bands
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    results = []
+    for (H, W, ks, nk, T) in ((37, 23, 3, 4, 3), (41, 19, 5, 4, 2)):
+        p = synth.params(T, ks, nk, seed=11 + ks)
+        _, f = synth.single_image(H, W, 1, 7, index=ks)
+        own0, own1, g0, g1 = band_rows(H, world, rank, ks, T)
+        band = oracle.forward(f[g0:g1].copy(), p)[-1][own0 - g0:own1 - g0]
+        whole = gather_bands(torch.from_numpy(np.ascontiguousarray(band)), H).numpy()
+        results.append(whole)
+    q.put((rank, results))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_row_bands_reproduce_the_whole_image(world):
+    """One image split into row bands with 2R T ghost rows, each band run alone
+    through the FP64 oracle and the owned rows gathered over gloo ranks, equals
+    the oracle's whole-image result exactly: the cascade needs no exchange."""
+    import oracle
+    import synth
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_band_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for k, (H, W, ks, nk, T) in enumerate(((37, 23, 3, 4, 3), (41, 19, 5, 4, 2))):
+        p = synth.params(T, ks, nk, seed=11 + ks)
+        _, f = synth.single_image(H, W, 1, 7, index=ks)
+        ref = oracle.forward(f, p)[-1]
+        for r in range(world):
+            np.testing.assert_array_equal(out[r][k], ref)
+        # and the ghosts are needed: one row fewer on each side changes the result
+        ghost = 2 * (ks // 2) * T - 1
+        cut = H // 2
+        short = oracle.forward(f[max(0, cut - ghost):].copy(), p)[-1][min(cut, ghost):]
+        assert not np.array_equal(short[0], ref[cut])
