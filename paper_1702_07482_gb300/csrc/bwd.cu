@@ -2,6 +2,9 @@
 #include "launch.h"
 #include "bwd.cuh"
 
+#include <cstdio>
+#include <cstdlib>
+
 namespace tnrd {
 
 // bwd_zb and bwd_adj tile heights: TH + 2R is a multiple of ksize, so that
@@ -9,6 +12,35 @@ namespace tnrd {
 int bwd_tile_h(int ks) { return ks == 3 ? 34 : 36; }
 
 namespace {
+
+// Filter split S of a kernel whose warps walk fpw filters each per tile: S
+// CTAs of a tile share them out (a divisor of fpw).  Picks the S of least
+// estimated duration, in filter walks: ceil(ctas S / slots) waves of
+// fpw / S walks plus a per-CTA overhead (staging the tile, partials) of 0.3
+// walk, the value that ranks the measured splits of the 32 x 180^2 training
+// step as measured (3 and 3 best for bwd_zb and bwd_dk; none for large batches).
+int filter_split(long long tiles, int fpw, long long slots)
+{
+    int best = 1;
+    double best_cost = 1e300;
+    for (int sp = 1; sp <= fpw; ++sp) {
+        if (fpw % sp) continue;
+        const long long waves = (tiles * sp + slots - 1) / slots;
+        const double cost = (double)waves * ((double)fpw / sp + 0.3);
+        if (cost < best_cost * 0.999) {
+            best_cost = cost;
+            best = sp;
+        }
+    }
+    return best;
+}
+
+int sm_count()
+{
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return nsm;
+}
 
 template <int KS, int NK, int TH>
 cudaError_t launch_stage(const BwdArgs& a, int N, cudaStream_t s)
@@ -22,13 +54,37 @@ cudaError_t launch_stage(const BwdArgs& a, int N, cudaStream_t s)
     e = cudaFuncSetAttribute(bwd_adj<KS, NK, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)A::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    bwd_zb<KS, NK, TH><<<dim3(a.zb_tiles_x * a.zb_tiles_y, N), Z::NTHREADS, Z::SMEM_BYTES, s>>>(a);
+    // resident CTAs per SM of bwd_zb and bwd_dk (for the filter split)
+    static const int occ_zb = [] {
+        int b = 0;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bwd_zb<KS, NK, TH>, Z::NTHREADS,
+                                                             Z::SMEM_BYTES) == cudaSuccess && b > 0 ? b : 1;
+    }();
+    static const int occ_dk = [] {
+        int b = 0;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bwd_dk<KS, NK, TH>, 128, 0) ==
+                       cudaSuccess && b > 0 ? b : 1;
+    }();
+    const long long nsm = sm_count();
+    const long long zb_tiles = (long long)a.zb_tiles_x * a.zb_tiles_y * N;
+    const long long dk_tiles = (long long)a.dk_tiles_x * a.dk_tiles_y * N;
+    int zs = filter_split(zb_tiles, Z::FPW, nsm * occ_zb);
+    int ds = filter_split(dk_tiles, NK / 4, nsm * occ_dk);
+    if (const char* env = std::getenv("TNRD_BWD_SPLIT")) {   // tuning override "zb,dk"
+        int z = 0, d = 0;
+        if (std::sscanf(env, "%d,%d", &z, &d) == 2 && z >= 1 && d >= 1 && Z::FPW % z == 0 &&
+            (NK / 4) % d == 0) {
+            zs = z;
+            ds = d;
+        }
+    }
+    bwd_zb<KS, NK, TH><<<dim3(a.zb_tiles_x * a.zb_tiles_y, N, zs), Z::NTHREADS, Z::SMEM_BYTES, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     bwd_adj<KS, NK, TH><<<dim3(a.tiles_x * a.tiles_y, N), A::NTHREADS, A::SMEM_BYTES, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    bwd_dk<KS, NK, TH><<<dim3(a.dk_tiles_x * a.dk_tiles_y, N), 128, 0, s>>>(a);
+    bwd_dk<KS, NK, TH><<<dim3(a.dk_tiles_x * a.dk_tiles_y, N, ds), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -146,7 +146,8 @@ __device__ __forceinline__ void zb_group(
     }
 }
 
-// grid (zb_tiles_x * zb_tiles_y, N), ZbCfg::NTHREADS threads, 2 CTAs per SM
+// grid (zb_tiles_x * zb_tiles_y, N, S), ZbCfg::NTHREADS threads, 2 CTAs per SM;
+// the S CTAs of a tile share out each warp's filters (fl = blockIdx.z, + S, ...).
 template <int KS, int NK, int TH>
 __global__ void __launch_bounds__(ZbCfg<KS, NK, TH>::NTHREADS, 2)
 bwd_zb(const __grid_constant__ BwdArgs a)
@@ -182,7 +183,7 @@ bwd_zb(const __grid_constant__ BwdArgs a)
     const int cta = n * (a.zb_tiles_x * a.zb_tiles_y) + blockIdx.x;
 
 #pragma unroll 1
-    for (int fl = 0; fl < C::FPW; ++fl) {
+    for (int fl = blockIdx.z; fl < C::FPW; fl += gridDim.z) {
         const int fi = warp * C::FPW + fl;
         for (int e = lane; e < KS * KS; e += 32) myK[e] = __ldg(a.k + fi * KS * KS + e);
         for (int e = lane; e < a.nrbf; e += 32) myWp[RBF_WPAD + e] = __ldg(a.w + fi * a.nrbf + e);
@@ -356,7 +357,8 @@ bwd_adj(const __grid_constant__ BwdArgs a)
     }
 }
 
-// grid (dk_tiles_x * dk_tiles_y, N), 4 warps; tiles of 32 columns x TH rows
+// grid (dk_tiles_x * dk_tiles_y, N, S), 4 warps (the S CTAs of a tile share out
+// each warp's filters: fl = blockIdx.z, + S, ...); tiles of 32 columns x TH rows
 // (TH + 2R a multiple of KS).  Per warp and filter: lane = pixel column, walk
 // over the u/d rows of the tile plus R above and below; step m takes u/d row
 // y0 - R + m and the 2R+1 c and v rows y0 + m - 2R + a (a = 0..2R) that meet it:
@@ -397,7 +399,7 @@ __global__ void __launch_bounds__(128) bwd_dk(const __grid_constant__ BwdArgs a)
     const int rows_here = min(TH, H - y0);
     const int cta = n * (a.dk_tiles_x * a.dk_tiles_y) + blockIdx.x;
 #pragma unroll 1
-    for (int fl = 0; fl < FPW; ++fl) {
+    for (int fl = blockIdx.z; fl < FPW; fl += gridDim.z) {
         const int fi = warp * FPW + fl;
         const size_t plane = ioff * (size_t)a.nfilt + (size_t)fi * a.img_stride;
         const float* cp = a.cpl + plane + (size_t)y0 * a.pitch + (col_ok ? x : 0);
