@@ -193,8 +193,10 @@ TNRD_API tnrd_status tnrd_plan_create(tnrd_plan** plan, const tnrd_image* images
 TNRD_API tnrd_status tnrd_batch_forward(const tnrd_plan* plan, cudaStream_t stream);
 
 /* Synchronous: TNRD_OK, or TNRD_ERR_TIMEOUT if a tile of the last
- * tnrd_batch_forward gave up waiting for its neighbours or (tensor-core plans)
- * for its tensor-core operations (its outputs are then incomplete). */
+ * tnrd_batch_forward gave up waiting for its neighbours (persistent schedule),
+ * for the bulk tensor copy of its u_{t-1} tile (per-stage schedule) or, in
+ * tensor-core plans, for its tensor-core operations (its outputs are then
+ * incomplete). */
 TNRD_API tnrd_status tnrd_plan_status(const tnrd_plan* plan);
 
 /* Bound, in SM clock cycles, on each wait of a tile for its neighbours

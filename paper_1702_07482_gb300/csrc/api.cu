@@ -682,7 +682,7 @@ tnrd_status plan_build(tnrd_plan* P, int th, cudaStream_t s)
     std::vector<CUtensorMap> maps;
     int bw = 0, bh = 0;
     if (P->algo == TNRD_ALGO_FUSED && tnrd::tma_staging_enabled() &&
-        tnrd::fused_fwd_box(P->ks, P->nk, th, &bw, &bh) && tnrd::device_status_word()) {
+        tnrd::fused_fwd_box(P->ks, P->nk, th, &bw, &bh)) {
         maps.resize(3 * (size_t)P->nimg);
         for (int i = 0; i < P->nimg && !maps.empty(); ++i) {
             const float* src[3] = {bi[i].f, bi[i].u, bi[i].tmp};
@@ -715,7 +715,7 @@ tnrd_status plan_build(tnrd_plan* P, int th, cudaStream_t s)
     A.wait_limit = (const long long*)(P->block + P->off_limit);
     A.ntiles = P->ntiles;
     A.maps = maps.empty() ? nullptr : (const CUtensorMap*)(P->block + P->off_maps);
-    A.err = tnrd::device_status_word();
+    A.err = A.status;   // a tile copy that never landed is a plan failure (tnrd_plan_status)
     A.T = P->T;
     A.nfilt = P->nk;
     A.ksize = P->ks;

@@ -318,7 +318,7 @@ struct BatchArgs {
     int T;
     int nfilt, ksize, nrbf;
     const CUtensorMap* maps;     // per image: f, u, tmp views for the per-stage kernel (or null)
-    int* err;                    // device status word of the per-stage kernel's copies
+    int* err;                    // status word for the per-stage kernel's copies (the plan's)
 };
 
 // ---------------------------------------------------------------------------
