@@ -270,6 +270,17 @@ TNRD_API tnrd_status tnrd_forward_noalloc(const tnrd_params* params, int N, int 
  * tile's output is then not written).  Reading clears the device-side word. */
 TNRD_API tnrd_status tnrd_device_status(void);
 
+/* Test hook for the bounded waits of the fused stages' tile copies (the
+ * one-column, pair and cluster-pair kernels of tnrd_forward): `cycles` is the
+ * limit of each wait in SM cycles (default 2^31, about one second; >= 0), and
+ * never_complete != 0 arms each copy's mbarrier for 16 bytes more than the copy
+ * brings, so that every wait runs out: each tile records TNRD_ERR_TIMEOUT (read
+ * by tnrd_device_status), waits the limit once more for its copy still in
+ * flight, and writes no output.  The copies themselves complete normally and
+ * the context stays usable.  Process-wide, read when a launch is issued; not
+ * for concurrent use.  TNRD_ERR_INVALID_ARG for a negative limit. */
+TNRD_API tnrd_status tnrd_stage_wait_test(long long cycles, int never_complete);
+
 /* Message describing the last error status returned on this host thread. */
 TNRD_API const char* tnrd_last_error(void);
 

@@ -26,7 +26,8 @@ EXPORTS = ["tnrd_workspace_size", "tnrd_forward", "tnrd_backward", "tnrd_plan_cr
            "tnrd_batch_forward", "tnrd_plan_status", "tnrd_plan_set_wait_limit",
            "tnrd_plan_tile_height", "tnrd_plan_launches", "tnrd_plan_destroy",
            "tnrd_forward_noalloc", "tnrd_forward_kernel", "tnrd_quality_workspace_size",
-           "tnrd_quality", "tnrd_device_status", "tnrd_last_error", "tnrd_version"]
+           "tnrd_quality", "tnrd_device_status", "tnrd_stage_wait_test", "tnrd_last_error",
+           "tnrd_version"]
 
 # Largest N * H * pitch (floats) tnrd_forward_noalloc accepts (TNRD_NOALLOC_MAX_FLOATS).
 NOALLOC_MAX_FLOATS = 1 << 22
@@ -103,6 +104,8 @@ def load(path: str = LIB_PATH):
         L.tnrd_quality.argtypes = [P, P, P, i, i, i, i, ctypes.c_float, P, P, sz, P]
         L.tnrd_device_status.restype = i
         L.tnrd_device_status.argtypes = []
+        L.tnrd_stage_wait_test.restype = i
+        L.tnrd_stage_wait_test.argtypes = [ctypes.c_longlong, i]
         L.tnrd_last_error.restype = ctypes.c_char_p
         L.tnrd_last_error.argtypes = []
         L.tnrd_version.restype = i
@@ -238,3 +241,9 @@ def tnrd_quality(ref, img, noisy, N, H, W, pitch, peak, out, workspace, workspac
 def tnrd_device_status() -> int:
     """Synchronous: 0, or TNRD_ERR_TIMEOUT if a tensor-core stage gave up waiting."""
     return load().tnrd_device_status()
+
+
+def tnrd_stage_wait_test(cycles: int, never_complete: bool) -> None:
+    """Test hook: wait limit of the fused stages' tile copies, and whether every
+    copy's wait is made to run out (see include/tnrd.h)."""
+    check(load().tnrd_stage_wait_test(int(cycles), int(bool(never_complete))))

@@ -313,6 +313,13 @@ tnrd_status tnrd_device_status(void)
     return TNRD_OK;
 }
 
+tnrd_status tnrd_stage_wait_test(long long cycles, int never_complete)
+{
+    if (cycles < 0) return fail(TNRD_ERR_INVALID_ARG, "negative wait limit");
+    tnrd::set_stage_wait_test(cycles, never_complete);
+    return TNRD_OK;
+}
+
 int tnrd_version(void) { return 1 * 10000 + 0 * 100 + 0; }
 
 size_t tnrd_workspace_size(tnrd_op op, const tnrd_params* params, int N, int H, int W,

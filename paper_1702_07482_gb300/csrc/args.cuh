@@ -23,6 +23,8 @@ struct StageArgs {
     int th, te;            // row tiling (row_tile): tile height <= the kernel's TH, short border tiles
     int use_tma;           // umap describes u_in: stage tiles with bulk tensor copies
     int* err;              // device status word (TNRD_ERR_TIMEOUT on a copy that never landed)
+    long long wait_limit;  // SM cycles per wait on a tile copy
+    int tx_extra;          // test hook: extra bytes the copy's mbarrier expects (0)
     CUtensorMap umap;      // [N][H][pitch] float32 view of u_in, box of the kernel's staged tile
 };
 
@@ -44,6 +46,8 @@ struct TileJob {
     const CUtensorMap* umap = nullptr;   // tensor map of u_in (null: symmetric gather)
     int img = 0;                         // z coordinate of this image in umap
     int* err = nullptr;                  // status word for a copy that timed out
+    long long wait_limit = 1ll << 31;    // SM cycles per wait on the copy (about one second)
+    int tx_extra = 0;                    // test hook: extra bytes the copy's mbarrier expects
 };
 
 template <int KS, int NK, int TH>

@@ -127,6 +127,7 @@ batch_stage_fwd(const __grid_constant__ BatchArgs a, int t)
     j.umap = a.maps ? a.maps + 3 * ti.x + src : nullptr;
     j.img = 0;
     j.err = a.err;
+    j.wait_limit = *a.wait_limit;
     j.f = im.f;
     j.H = im.H;
     j.W = im.W;

@@ -280,6 +280,8 @@ fused_stage_fwd(const __grid_constant__ StageArgs a)
     j.umap = a.use_tma ? &a.umap : nullptr;
     j.img = n;
     j.err = a.err;
+    j.wait_limit = a.wait_limit;
+    j.tx_extra = a.tx_extra;
     stage_tile<KS, NK, TH>(j, smem);
 }
 

@@ -319,6 +319,8 @@ __device__ __forceinline__ TileJob pair_job(const StageArgs& a, int tile, int th
     j.umap = a.use_tma ? &a.umap : nullptr;
     j.img = n;
     j.err = a.err;
+    j.wait_limit = a.wait_limit;
+    j.tx_extra = a.tx_extra;
     return j;
 }
 

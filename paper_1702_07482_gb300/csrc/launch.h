@@ -47,6 +47,8 @@ bool tma_staging_enabled();
 bool encode_tile_map(CUtensorMap* map, const float* base, int W, int H, int N, int pitch,
                      long long img_stride, int box_w, int box_h);
 void stage_args_tma(StageArgs& a, int N, int box_w, int box_h);
+// Test hook behind tnrd_stage_wait_test (process-wide).
+void set_stage_wait_test(long long cycles, int never_complete);
 // Staged tile (columns x rows) of the fused forward kernel of tile height th.
 bool fused_fwd_box(int ks, int nk, int th, int* box_w, int* box_h);
 // One stage t of a batched plan on the tensor cores (all images' tiles in one launch).

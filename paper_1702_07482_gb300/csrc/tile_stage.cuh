@@ -24,8 +24,6 @@
 
 namespace tnrd {
 
-constexpr long long STAGE_WAIT_LIMIT = 1ll << 31;   // SM cycles, about one second
-
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
@@ -47,8 +45,11 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 // coordinate j.img of j.umap) into sU with row pitch UP = staged_pitch(UW).
 // XALIGN: the buffer column of xl must be a multiple of it (2 for float2 row
 // reads).  Returns that buffer column, or -1 (uniform over the CTA) if the
-// copy did not complete within the wait limit; then *j.err is set to
-// TNRD_ERR_TIMEOUT and sU must not be used.  Ends with a CTA barrier.
+// copy did not complete within j.wait_limit cycles; then *j.err is set to
+// TNRD_ERR_TIMEOUT, the CTA waits the limit once more for its copy still in
+// flight, and sU must not be used.  j.tx_extra (a test hook) arms the mbarrier
+// for that many bytes more than the copy brings, so that the waits run out.
+// Ends with a CTA barrier.
 template <int UH, int UW, int NT, int XALIGN>
 __device__ __forceinline__ int stage_u_tile(const TileJob& j, float* sU, int ys, int xl)
 {
@@ -61,12 +62,14 @@ __device__ __forceinline__ int stage_u_tile(const TileJob& j, float* sU, int ys,
         if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
         __syncthreads();
         if (threadIdx.x == 0) {
-            mbar_expect_tx(&bar, (uint32_t)(UH * UP * sizeof(float)));
+            mbar_expect_tx(&bar, (uint32_t)(UH * UP * sizeof(float)) + (uint32_t)j.tx_extra);
             tma_load_3d(sU, j.umap, xs, ys, j.img, &bar);
         }
-        const bool got = __syncthreads_and(tc::mbar_wait(&bar, 0, STAGE_WAIT_LIMIT));
+        const bool got = __syncthreads_and(tc::mbar_wait(&bar, 0, j.wait_limit));
         if (!got) {
             if (threadIdx.x == 0) atomicExch(j.err, 4 /* TNRD_ERR_TIMEOUT */);
+            tc::mbar_wait(&bar, 0, j.wait_limit);   // let a late copy land before the CTA leaves
+            __syncthreads();
             return -1;
         }
         if (ys < 0 || ys + UH > H || xs < 0 || xs + UP > W) {

@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include "launch.h"
 
@@ -56,8 +57,21 @@ bool encode_tile_map(CUtensorMap* map, const float* base, int W, int H, int N, i
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+namespace {
+std::atomic<long long> g_wait_limit{1ll << 31};
+std::atomic<int> g_tx_extra{0};
+}  // namespace
+
+void set_stage_wait_test(long long cycles, int never_complete)
+{
+    g_wait_limit.store(cycles);
+    g_tx_extra.store(never_complete ? 16 : 0);
+}
+
 void stage_args_tma(StageArgs& a, int N, int box_w, int box_h)
 {
+    a.wait_limit = g_wait_limit.load();
+    a.tx_extra = g_tx_extra.load();
     a.err = device_status_word();
     a.use_tma = a.err != nullptr && tma_staging_enabled() &&
                 encode_tile_map(&a.umap, a.u_in, a.W, a.H, N, a.pitch, a.img_stride, box_w, box_h);

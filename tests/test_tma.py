@@ -130,3 +130,41 @@ def test_kernel_query_names_the_staging():
         assert B.tnrd_forward_kernel(prm, 1, 512, 512, B.ALGO["fused"]).endswith("gather staging")
     finally:
         del os.environ["TNRD_TMA"]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kernel", ["lane", "pair2"])
+def test_copy_wait_runs_out_and_reports(kernel):
+    """A tile copy whose wait runs out (tnrd_stage_wait_test: the mbarrier armed
+    for more bytes than the copy brings): every tile records TNRD_ERR_TIMEOUT and
+    writes nothing, no GPU fault, and the context stays usable -- the next call
+    matches the oracle with status OK."""
+    import oracle
+    from paper_1702_07482_gb300 import binding as B
+    from paper_1702_07482_gb300 import ops
+    H, W = 40, 60
+    p, f = case(H, W, 7, 48, 1, L=1, N=1, cfg=391)
+    m = ops.Model.create(p.filters, p.rbf_w, p.lam, p.mu0, p.delta, p.gamma)
+    ft = torch.tensor(f, dtype=torch.float32, device="cuda")
+    assert B.tnrd_device_status() in (0, 4)          # clears the word
+    old = os.environ.get("TNRD_FUSED_KERNEL")
+    os.environ["TNRD_FUSED_KERNEL"] = kernel
+    try:
+        out = torch.full((1, H, ops.pitch_for(W)), float("nan"), device="cuda")
+        B.tnrd_stage_wait_test(200_000, True)
+        try:
+            ops.forward(m, ft, out=out)
+            torch.cuda.synchronize()
+        finally:
+            B.tnrd_stage_wait_test(1 << 31, False)
+        assert B.tnrd_device_status() == 4           # TNRD_ERR_TIMEOUT
+        assert torch.isnan(out[..., :W]).all()       # no tile wrote its outputs
+        good = ops.forward(m, ft)[0, :, :W].double().cpu().numpy()
+        torch.cuda.synchronize()
+        assert B.tnrd_device_status() == 0
+    finally:
+        if old is None:
+            os.environ.pop("TNRD_FUSED_KERNEL", None)
+        else:
+            os.environ["TNRD_FUSED_KERNEL"] = old
+    assert np.abs(good - oracle.forward(f[0], p)[-1]).max() <= TOL_U_FP32
