@@ -76,6 +76,27 @@ class Params:
             return self.filters().clone(), self.w.detach().clone(), self.lam().clone()
 
 
+def save(p: Params, path: str) -> None:
+    """Writes the trainable parameters (theta, w, beta: the unconstrained
+    values, so training resumes exactly) and the model constants to an .npz
+    archive; one file per model (e.g. per number of looks L)."""
+    import numpy as np
+    np.savez(path, theta=p.theta.detach().cpu().numpy(), w=p.w.detach().cpu().numpy(),
+             beta=p.beta.detach().cpu().numpy(),
+             consts=np.array([p.mu0, p.delta, p.gamma, p.proj_c], dtype=np.float64),
+             data_term=np.array(p.data_term, dtype=np.int64))
+
+
+def load(path: str, device="cuda") -> Params:
+    """Reads an archive written by save(): the same values, trainable again."""
+    import numpy as np
+    with np.load(path) as z:
+        t = lambda a: torch.as_tensor(a, dtype=torch.float32, device=device).clone().requires_grad_()
+        mu0, delta, gamma, proj_c = (float(v) for v in z["consts"])
+        return Params(t(z["theta"]), t(z["w"]), t(z["beta"]), mu0, delta, gamma,
+                      int(z["data_term"]), proj_c)
+
+
 def loss_sum(u: torch.Tensor, clean: torch.Tensor) -> torch.Tensor:
     """Eq. learning: sum over samples and pixels of 1/2 (u - u_gt)^2."""
     return 0.5 * ((u - clean) ** 2).sum()

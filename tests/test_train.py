@@ -74,3 +74,26 @@ def test_greedy_phase_leaves_other_stages_alone():
     for b, a in zip(before, after):
         assert torch.equal(b[0], a[0].detach()) and torch.equal(b[2], a[2].detach())
         assert not torch.equal(b[1], a[1].detach())
+
+
+def test_save_load_round_trip(tmp_path):
+    """Host-only: parameters written by train.save come back by train.load bit
+    for bit (the unconstrained theta, w, beta and the constants), trainable."""
+    import numpy as np
+    import synth
+    from paper_1702_07482_gb300 import train
+    q = synth.params(3, 5, 24, seed=21)
+    p = train.Params.from_model(q.filters, q.rbf_w, q.lam, mu0=-300.0, delta=12.0, gamma=9.0,
+                                device="cpu", data_term=2, proj_c=1.5)
+    with torch.no_grad():
+        p.theta.add_(0.25)            # not zero-mean: the raw parameters are what is stored
+    path = str(tmp_path / "model_L4.npz")
+    train.save(p, path)
+    r = train.load(path, device="cpu")
+    for a, b in zip(p.tensors(), r.tensors()):
+        assert torch.equal(a.detach(), b.detach()) and b.requires_grad
+    assert (r.mu0, r.delta, r.gamma, r.data_term, r.proj_c) == (-300.0, 12.0, 9.0, 2, 1.5)
+    f0, w0, l0 = p.detached()
+    f1, w1, l1 = r.detached()
+    assert torch.equal(f0, f1) and torch.equal(w0, w1) and torch.equal(l0, l1)
+    assert np.allclose(f1.sum(dim=(-2, -1)).numpy(), 0.0, atol=1e-5)
