@@ -1,4 +1,6 @@
 // Instantiations and launcher of the tensor-core forward stage.
+#include <atomic>
+
 #include "launch.h"
 #include "tc_fwd.cuh"
 
@@ -63,18 +65,20 @@ cudaError_t launch_tc_batch(int ks, int nk, int nb, bool bf16, const BatchArgs& 
 int* device_status_word()
 {
     constexpr int MAXDEV = 64;
-    static int* words[MAXDEV] = {};
+    static std::atomic<int*> words[MAXDEV] = {};   // per device, filled on first use
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return nullptr;
-    if (!words[dev]) {
+    int* w = words[dev].load(std::memory_order_acquire);
+    if (!w) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_tc_error) != cudaSuccess) {
             (void)cudaGetLastError();
             return nullptr;
         }
-        words[dev] = static_cast<int*>(p);
+        w = static_cast<int*>(p);
+        words[dev].store(w, std::memory_order_release);   // every thread stores the same address
     }
-    return words[dev];
+    return w;
 }
 
 cudaError_t tc_take_error(int* out)
