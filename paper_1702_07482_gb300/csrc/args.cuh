@@ -84,7 +84,7 @@ struct FusedCfg {
 // Tile origin along one axis: tiles of size T cover [0, n); the last tile is
 // shifted back to end at n (when n >= T) so that every tile lies inside the
 // image and only the first and the last tile touch a border.
-__device__ __forceinline__ int tile_origin(int t, int T, int n)
+__host__ __device__ __forceinline__ int tile_origin(int t, int T, int n)
 {
     return (n >= T) ? min(t * T, n - T) : 0;
 }
@@ -94,7 +94,7 @@ __device__ __forceinline__ int tile_origin(int t, int T, int n)
 // images of their adjoint values, which only the first (top) and the last
 // (bottom) tile compute, so the split between the last two tiles is moved to
 // at most n - R, and never below R when there are only two tiles (n >= 2R).
-__device__ __forceinline__ int tile_split(int t, int T, int n, int nt, int R)
+__host__ __device__ __forceinline__ int tile_split(int t, int T, int n, int nt, int R)
 {
     if (t <= 0) return 0;
     if (t >= nt) return n;
@@ -121,7 +121,7 @@ __host__ __device__ __forceinline__ int row_tiles(int n, int th, int te)
     return te > 0 ? 2 + (n - 2 * te + th - 1) / th : (n + th - 1) / th;
 }
 
-__device__ __forceinline__ int row_split_short(int s, int nt, int n, int th, int te, int R)
+__host__ __device__ __forceinline__ int row_split_short(int s, int nt, int n, int th, int te, int R)
 {
     if (s <= 0) return 0;
     if (s >= nt) return n;
@@ -130,7 +130,7 @@ __device__ __forceinline__ int row_split_short(int s, int nt, int n, int th, int
     return (s == nt - 2) ? min(v, n - te - 2 * R) : v;
 }
 
-__device__ __forceinline__ RowTile row_tile(int t, int nt, int n, int th, int te, int R)
+__host__ __device__ __forceinline__ RowTile row_tile(int t, int nt, int n, int th, int te, int R)
 {
     RowTile r;
     if (te <= 0) {
