@@ -65,7 +65,8 @@ QUALITY_FLOPS_PER_PX = 484 + 1089 + 21 + 3 + 18 + 4 + 3
 CONFIG = {"workload": "TRDMD forward, 1 x 512x512 per GPU, 7x7x48, 63 RBF, T=5, L=1, "
                       "fused FP32 stage kernel",
           "H": H, "W": W, "images_per_gpu": 1, "ksize": KS, "nfilt": NK, "nrbf": 63, "T": T,
-          "looks": L, "l2": "flushed between steps (256 MiB write outside the events)"}
+          "looks": L, "data_term": "idiv",
+          "l2": "flushed between steps (256 MiB write outside the events)"}
 
 
 def _peaks():
@@ -77,8 +78,8 @@ def _peaks():
 
 
 # DRAM bytes (read + write) per launch of the fused stage kernel at the 512 x 512
-# workload, from one ncu capture (profiles/fused_pair2_fwd_7x7x48_512x512.md),
-# valid only for the kernel that capture measured and the sources it was taken
+# workload, from one ncu capture of that kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of a steady-state launch), valid only for the kernel that capture measured and the sources it was taken
 # on (the kernel name and the sources' hash are checked at run time).
 _TRAFFIC = {"kernel": "fused_pair2_fwd<7,48,37> tiles 33x58 (border rows 27), tma staging",
             "sources_sha256_16": "9cfb30f7a9e63c51", "bytes_per_launch": 2274304}
@@ -108,8 +109,84 @@ def _fp32_peak_tflops(sm_mhz: float, n_sm: int) -> float:
     return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+class NvmlClocks:
+    """Read-only SM clock and clock-event-reason samples through NVML (the
+    driver's libnvidia-ml, via ctypes), taken every ~1 ms by a host thread;
+    only the samples that fall inside the marked timed windows are kept."""
+
+    SM = 1   # NVML_CLOCK_SM
+    # clock event reason bits (nvmlClocksEventReason*)
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, dev):
+        import ctypes
+        self.ok = False
+        self.samples = []
+        self.windows = []
+        self._stop = threading.Event()
+        self._t = None
+        try:
+            L = ctypes.CDLL("libnvidia-ml.so.1")
+            if L.nvmlInit_v2() != 0:
+                return
+            self.L = L
+            h = ctypes.c_void_p()
+            import torch
+            pr = torch.cuda.get_device_properties(dev)
+            bus = getattr(pr, "pci_bus_id", None)
+            rc = 1
+            if bus is not None:
+                pci = f"{getattr(pr, 'pci_domain_id', 0):08x}:{bus:02x}:{pr.pci_device_id:02x}.0"
+                rc = L.nvmlDeviceGetHandleByPciBusId_v2(pci.encode(), ctypes.byref(h))
+            if rc != 0:
+                rc = L.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(dev.index or 0), ctypes.byref(h))
+            if rc != 0:
+                return
+            self.h = h
+            self.reasons_fn = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                L.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint()
+            self.sm_max = (float(mx.value) if L.nvmlDeviceGetMaxClockInfo(h, self.SM, ctypes.byref(mx))
+                           == 0 else None)
+            self.ok = True
+        except (OSError, AttributeError):
+            self.ok = False
+
+    def _read(self):
+        import ctypes
+        c = ctypes.c_uint()
+        r = ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            t = time.perf_counter()
+            if self.L.nvmlDeviceGetClockInfo(self.h, self.SM, ctypes.byref(c)) == 0:
+                rr = r.value if self.reasons_fn(self.h, ctypes.byref(r)) == 0 else 0
+                self.samples.append((t, float(c.value), rr))
+            time.sleep(0.001)
+
+    def start(self):
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def mark(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=2)
+        inside = [(c, r) for (t, c, r) in self.samples
+                  if any(a <= t <= b for a, b in self.windows)]
+        reasons = sorted({nm for _, r in inside for bit, nm in self.BITS.items() if r & bit})
+        return {"sm_mhz": statistics.median(c for c, _ in inside) if inside else None,
+                "sm_max_mhz": self.sm_max, "reasons": reasons, "samples": len(inside),
+                "source": "NVML, read-only, ~1 ms period; only samples inside the timed "
+                          "regions (device-timed steps and end-to-end steps)",
+                "window_ms": round(1e3 * sum(b - a for a, b in self.windows), 3)}
+
+
 class ClockSampler:
-    """Samples nvidia-smi during the timed region."""
+    """Samples nvidia-smi during the timed region (used when NVML cannot be read)."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -218,6 +295,69 @@ def _rows_rate(fn, rows0, target_s, max_rows):
     return rows, dt
 
 
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_baseline(fn, rows0, max_rows, width, what, full=None):
+    """The FP64 oracle's rate on the host cores, all cores and one thread.
+    fn(rows) runs the oracle on the first `rows` rows of the workload's image;
+    `full` = (pixels, seconds) of a timed all-core oracle run over a whole image
+    (the accuracy check's), used as the all-core sample when given."""
+    import oracle
+    oracle.build()
+    n = oracle.get_threads()
+    if full is not None:
+        px, dt = full
+        v_all, s_all = px / dt / 1e6, f"the whole {what}, all stages ({dt:.1f} s)"
+    else:
+        rows, dt = _rows_rate(fn, rows0, 12.0, max_rows)
+        v_all, s_all = rows * width / dt / 1e6, f"rows 0..{rows - 1} of {what}, all stages ({dt:.1f} s)"
+    oracle.set_threads(1)
+    try:
+        rows1, dt1 = _rows_rate(fn, max(1, rows0 // 4), 8.0, max_rows)
+    finally:
+        oracle.set_threads(n)
+    return {"value": v_all, "unit": "Mpixel/s", "cores": n, "kind": "oracle", "sample": s_all,
+            "value_1thread": rows1 * width / dt1 / 1e6,
+            "sample_1thread": f"rows 0..{rows1 - 1} of {what}, all stages, 1 thread ({dt1:.1f} s)",
+            "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
+
+
+def _accuracy(got, ref, what):
+    """max |du| and PSNR of a whole GPU result against the FP64 oracle's."""
+    import numpy as np
+    d = np.asarray(got, np.float64) - np.asarray(ref, np.float64)
+    mse = float((d ** 2).mean())
+    return {"vs": "FP64 oracle", "pixels": int(d.size), "image": what,
+            "max_abs": float(np.abs(d).max()),
+            "psnr_db": float(10 * np.log10(255.0 ** 2 / max(mse, 1e-30))),
+            "scale": "[0, 255] intensities"}
+
+
+def _timed_oracle_forward(f, p):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    u = oracle.forward(f, p)
+    return u, time.perf_counter() - t0
+
+
 class Fwd(Workload):
     def __init__(self, dev, H=512, W=512, ks=KS, nk=NK, T_=T, algo="fused", cfg=CFG_ID,
                  data_term=0):
@@ -281,15 +421,22 @@ class Fwd(Workload):
         self.step()
         self.u_host.copy_(self.u_dev, non_blocking=True)
 
+    def accuracy(self):
+        """u_T of the whole image against the FP64 oracle (whose run, timed on
+        all host cores, is also the all-core CPU baseline sample)."""
+        import torch
+        self.step()
+        torch.cuda.synchronize()
+        got = self.u_dev[0, :, :self.Ww].double().cpu().numpy()
+        u, dt = _timed_oracle_forward(self.f, self.p)
+        self._full = (self.Hh * self.Ww, dt)
+        return _accuracy(got, u[-1], f"{self.Hh}x{self.Ww} image (u_T)")
+
     def cpu_baseline(self):
         import oracle
-        oracle.build()
         band = lambda r: oracle.forward(self.f[:r].copy(), self.p)
-        rows, dt = _rows_rate(band, 8, 12.0, self.Hh)
-        return {"value": rows * self.Ww / dt / 1e6, "unit": "Mpixel/s",
-                "cores": oracle.get_threads(), "kind": "oracle",
-                "sample": f"rows 0..{rows - 1} of the {self.Hh}x{self.Ww} image, all "
-                          f"T={self.T} stages ({dt:.1f} s)"}
+        return _oracle_baseline(band, 8, self.Hh, self.Ww, f"the {self.Hh}x{self.Ww} image",
+                                getattr(self, "_full", None))
 
 
 class Batched(Workload):
@@ -338,6 +485,7 @@ class Batched(Workload):
         self.algo = algo
         if algo != "fused":
             self.dtype = f"{algo} operands, f32 accumulate"
+            self.tensor_dtype = algo
         sched = "batch_persistent_fwd" if self.launches == 1 else "batch_stage_fwd"
         self.kernel = (f"{sched}<7,48,{self.plan.tile_height}>" if algo == "fused" else
                        f"tc_batch_fwd<7,48,2,{algo}> (tcgen05 {algo.upper()} filter bank and "
@@ -359,35 +507,17 @@ class Batched(Workload):
         self.plan.forward(self.sp)
 
     def accuracy(self):
-        """Tensor-core plans: max |du| and PSNR of image 0 against the FP64 oracle
-        on sampled pixels (crops the crop edge cannot reach)."""
-        if self.algo == "fused":
-            return None
-        import numpy as np
+        """u_T of the whole image 0 of the batch against the FP64 oracle."""
         import torch
-        import oracle
         from paper_1702_07482_gb300 import ops
-        oracle.build()
         self.step()
         torch.cuda.synchronize()
         Hh, Ww, Lk = self.sizes[0]
         P = ops.pitch_for(Ww)
-        u0 = self.u_dev[:Hh * P].view(Hh, P)[:, :Ww].double().cpu().numpy()
-        M = 2 * (KS // 2) * self.T
-        g = np.random.Generator(np.random.PCG64(5))
-        pts = [(0, 0), (Hh - 1, Ww - 1)] + [tuple(x) for x in
-                                            zip(g.integers(0, Hh, 10), g.integers(0, Ww, 10))]
-        d = []
-        for (y, x) in pts:
-            y0, y1 = max(0, y - M), min(Hh, y + M + 1)
-            x0, x1 = max(0, x - M), min(Ww, x + M + 1)
-            ref = oracle.forward(self.fs[0][y0:y1, x0:x1].copy(), self.params[0])[-1][y - y0, x - x0]
-            d.append(u0[y, x] - ref)
-        d = np.array(d)
-        mse = float((d ** 2).mean())
-        return {"vs": "FP64 oracle", "pixels": len(pts), "max_abs": float(np.abs(d).max()),
-                "psnr_db": 10 * np.log10(255.0 ** 2 / max(mse, 1e-30)),
-                "scale": "[0, 255] intensities"}
+        got = self.u_dev[:Hh * P].view(Hh, P)[:, :Ww].double().cpu().numpy()
+        u, dt = _timed_oracle_forward(self.fs[0], self.params[0])
+        self._full = (Hh * Ww, dt)
+        return _accuracy(got, u[-1], f"image 0 of the batch, {Hh}x{Ww}, L={Lk} (u_T)")
 
     def e2e(self):
         self.f_dev.copy_(self.f_host, non_blocking=True)
@@ -396,15 +526,12 @@ class Batched(Workload):
 
     def cpu_baseline(self):
         import oracle
-        oracle.build()
         f0 = self.fs[0]
         p0 = self.params[0]
         band = lambda r: oracle.forward(f0[:r].copy(), p0)
-        rows, dt = _rows_rate(band, 8, 12.0, f0.shape[0])
-        return {"value": rows * f0.shape[1] / dt / 1e6, "unit": "Mpixel/s",
-                "cores": oracle.get_threads(), "kind": "oracle",
-                "sample": f"rows 0..{rows - 1} of image 0 ({f0.shape[0]}x{f0.shape[1]}), all "
-                          f"T={self.T} stages ({dt:.1f} s)"}
+        return _oracle_baseline(band, 8, f0.shape[0], f0.shape[1],
+                                f"image 0 ({f0.shape[0]}x{f0.shape[1]})",
+                                getattr(self, "_full", None))
 
 
 class Train(Workload):
@@ -474,11 +601,11 @@ class Train(Workload):
             ua = oracle.forward(f0[:r].copy(), self.p)
             oracle.backward(f0[:r].copy(), self.p, ua, ua[-1] - c0[:r])
 
-        rows, dt = _rows_rate(band, 6, 12.0, self.S)
-        return {"value": rows * self.S / dt / 1e6, "unit": "Mpixel/s",
-                "cores": oracle.get_threads(), "kind": "oracle",
-                "sample": f"rows 0..{rows - 1} of crop 0, forward + backward of all "
-                          f"T={self.T} stages ({dt:.1f} s)"}
+        r = _oracle_baseline(band, 6, self.S, self.S, f"crop 0 ({self.S}x{self.S})")
+        r["sample"] = r["sample"].replace("all stages", "forward + backward of all stages")
+        r["sample_1thread"] = r["sample_1thread"].replace("all stages",
+                                                          "forward + backward of all stages")
+        return r
 
 
 class Fit(Train):
@@ -580,7 +707,8 @@ class Quality(Workload):
         Q.indexes(*(a[:r, :r] for a in self.sample))
         dt = time.perf_counter() - t0
         return {"value": r * r / dt / 1e6, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
-                "sample": f"all six indexes of a {r}x{r} crop of image 0 ({dt:.1f} s)"}
+                "sample": f"all six indexes of a {r}x{r} crop of image 0 ({dt:.1f} s, numpy, "
+                          f"one thread)", "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
 
 
 class Mixed(Workload):
@@ -594,6 +722,7 @@ class Mixed(Workload):
         from paper_1702_07482_gb300 import binding as B
         from paper_1702_07482_gb300 import ops
         self.T, self.n, self.S, self.algo = T_, n, S, algo
+        self.tensor_dtype = algo if algo in ("tf32", "bf16") else None
         self.dtype = {"tf32": "tf32 operands, f32 accumulate",
                       "bf16": "bf16 operands, f32 accumulate"}.get(algo, "f32")
         self.p = _p32(synth.params(T_, KS, NK, seed=synth.seed_for(cfg, 0, "params")))
@@ -642,39 +771,29 @@ class Mixed(Workload):
         self.u_host.copy_(self.u_dev, non_blocking=True)
 
     def accuracy(self):
-        """max |du| and PSNR against the FP64 oracle on sampled pixels of image 0
-        (the oracle runs on crops the crop edge cannot reach, radius 2RT)."""
-        import numpy as np
-        import oracle
-        oracle.build()
-        self.step()
+        """u_T of a whole 1024 x 1024 image (the top-left crop of image 0, run as
+        its own image through the same kernel) against the FP64 oracle."""
         import torch
+        from paper_1702_07482_gb300 import binding as B
+        S = 1024
+        f = self.f0[:S, :S].copy()
+        fd = torch.tensor(f, dtype=torch.float32, device=self.dev).unsqueeze(0).contiguous()
+        ud = torch.empty_like(fd)
+        nb = B.tnrd_workspace_size(B.OP_FORWARD, self.prm, 1, S, S, S, 0, self.code)
+        ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=self.dev)
+        B.tnrd_forward(self.prm, 1, S, S, S, fd, ud, 0, self.code, ws, nb, self.sp)
         torch.cuda.synchronize()
-        u0 = self.u_dev[0].double().cpu().numpy()
-        S, M = self.S, 2 * (KS // 2) * self.T
-        g = np.random.Generator(np.random.PCG64(5))
-        pts = [(0, 0), (S - 1, S - 1), (0, S // 2)] + [tuple(x) for x in g.integers(0, S, size=(9, 2))]
-        d = []
-        for (y, x) in pts:
-            y0, y1 = max(0, y - M), min(S, y + M + 1)
-            x0, x1 = max(0, x - M), min(S, x + M + 1)
-            ref = oracle.forward(self.f0[y0:y1, x0:x1].copy(), self.p)[-1][y - y0, x - x0]
-            d.append(u0[y, x] - ref)
-        d = np.array(d)
-        mse = float((d ** 2).mean())
-        return {"vs": "FP64 oracle", "pixels": len(pts), "max_abs": float(np.abs(d).max()),
-                "psnr_db": 10 * np.log10(255.0 ** 2 / max(mse, 1e-30)),
-                "scale": "[0, 255] intensities"}
+        got = ud[0].double().cpu().numpy()
+        u, dt = _timed_oracle_forward(f, self.p)
+        self._full = (S * S, dt)
+        return _accuracy(got, u[-1], f"{S}x{S} top-left crop of image 0 run as its own image, "
+                                     f"L=2, T={self.T} (u_T)")
 
     def cpu_baseline(self):
         import oracle
-        oracle.build()
-        band = lambda r: oracle.forward(self.f0[:r].copy(), self.p)
-        rows, dt = _rows_rate(band, 4, 12.0, self.S)
-        return {"value": rows * self.S / dt / 1e6, "unit": "Mpixel/s",
-                "cores": oracle.get_threads(), "kind": "oracle",
-                "sample": f"rows 0..{rows - 1} of image 0 (2048 wide), all T={self.T} stages "
-                          f"({dt:.1f} s)"}
+        band = lambda r: oracle.forward(self.f0[:r, :1024].copy(), self.p)
+        return _oracle_baseline(band, 4, 1024, 1024, "the 1024x1024 crop of image 0",
+                                getattr(self, "_full", None))
 
 
 def make_workload(name, dev):
@@ -740,12 +859,49 @@ def run_reference(args):
         "data": "synthetic",
         "config": CONFIG,
         "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": _cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+# Per pixel-stage at 7x7x48: the filter bank and the adjoint are the two
+# contractions (2 x 2 N_k k^2 flops), phi and the prox the rest.
+CONV_FLOPS_PER_PX_STAGE = 2 * 2 * NK * KS * KS
+ALU_FLOPS_PER_PX_STAGE = 2 * NK * 63 + 12
+# dense tensor-core rates relative to BF16 (nominal: TF32 1.1, BF16 2.25 PFLOP/s)
+TENSOR_RATIO = {"tf32": 1.1 / 2.25, "bf16": 1.0}
+
+
+def _split_roofline(wl, tc, ms, peaks, src, peak_fp32, n_sm, sm_max):
+    """Roofline of a tensor-core stage: the step cannot be shorter than
+    T_min = max(conv flops / tensor peak, (phi + prox) flops / FP32 peak); the
+    binding term is reported (frac = T_min / T)."""
+    px_st = wl.flops / wl.flops_per_px_stage
+    conv, alu = px_st * CONV_FLOPS_PER_PX_STAGE, px_st * ALU_FLOPS_PER_PX_STAGE
+    bf = float(peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1700.0)
+    tpeak = bf * TENSOR_RATIO[tc]
+    t = ms / 1e3
+    terms = {
+        "tensor": {"flops": conv, "achieved": conv / t / 1e12, "peak": tpeak,
+                   "frac": conv / t / 1e12 / tpeak,
+                   "peak_source": f"{src} bf16_tflops_sustained {bf:.1f} x nominal {tc}/bf16 "
+                                  f"ratio {TENSOR_RATIO[tc]:.3f}"},
+        "alu": {"flops": alu, "achieved": alu / t / 1e12, "peak": peak_fp32,
+                "frac": alu / t / 1e12 / peak_fp32,
+                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
+    }
+    bound = max(terms, key=lambda k: terms[k]["flops"] / terms[k]["peak"])
+    b = terms[bound]
+    return {"bound": bound, "achieved": b["achieved"], "peak": b["peak"], "unit": "TFLOP/s",
+            "frac": b["frac"], "traffic": wl.traffic, "kernel": wl.kernel,
+            "launches_per_step": wl.launches,
+            "achieved_basis": "split roofline: T_min = max(filter bank + adjoint flops / tensor "
+                              "peak, (phi + prox) flops / FP32 peak); frac = T_min / step time "
+                              "of the binding term",
+            "terms": terms, "peak_source": b["peak_source"]}
 
 
 def run_ours(args):
@@ -778,30 +934,36 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(fn):
+    def timed(fn, clk):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         barrier()
+        t0 = time.perf_counter()
         for i in range(args.steps):
             flush.fill_(i & 0xFF)          # evict the previous step's data from L2
             evs[i][0].record(stream)
             fn()
             evs[i][1].record(stream)
         barrier()
+        if hasattr(clk, "mark"):
+            clk.mark(t0, time.perf_counter())
         return [a.elapsed_time(b) for a, b in evs]
 
     for _ in range(max(args.warmup, 3)):
         wl.step()
     barrier()
-    sampler = ClockSampler(local)
+    sampler = NvmlClocks(dev)
+    if not sampler.ok:
+        sampler = ClockSampler(local)
     sampler.start()
-    time.sleep(0.3)
-    step_ms = timed(wl.step)
+    if not hasattr(sampler, "mark"):
+        time.sleep(0.3)   # nvidia-smi needs a moment before its first sample
+    step_ms = timed(wl.step, sampler)
     # end to end through the C ABI: pinned host inputs -> device -> path ->
     # pinned host result, all inside the events
     for _ in range(3):
         wl.e2e()
-    e2e_ms = timed(wl.e2e)
+    e2e_ms = timed(wl.e2e, sampler)
     clocks = sampler.stop()
 
     from paper_1702_07482_gb300.shard import global_rate
@@ -814,8 +976,9 @@ def run_ours(args):
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak_tf = _fp32_peak_tflops(sm_max, n_sm)
         achieved_tf = wl.flops / (ms / 1e3) / 1e12
+        # accuracy first: its whole-image oracle run is the all-core CPU sample
+        acc = wl.accuracy() if (hasattr(wl, "accuracy") and not args.no_accuracy) else None
         cpu = None if args.no_cpu_baseline else wl.cpu_baseline()
-        acc = wl.accuracy() if hasattr(wl, "accuracy") else None
         out = {
             "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -840,6 +1003,9 @@ def run_ours(args):
         }
         if acc is not None:
             out["accuracy"] = acc
+        tc = getattr(wl, "tensor_dtype", None)
+        if tc:
+            out["roofline"] = _split_roofline(wl, tc, ms, peaks, src, peak_tf, n_sm, sm_max)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -860,6 +1026,8 @@ def main():
                              "fit", "fwd512_gauss", "fwd512_proj", "quality", "mixed_tf32",
                              "mixed_bf16", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the whole-image comparison with the FP64 oracle")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -256,7 +256,9 @@ TNRD_API tnrd_status tnrd_quality(const float* ref, const float* img, const floa
  *  - N * H * pitch above TNRD_NOALLOC_MAX_FLOATS returns TNRD_ERR_INVALID_ARG
  *    and launches nothing;
  *  - the first call on a device looks up the array's device address with
- *    that device current; make that first call before any stream capture;
+ *    that device current, and so does the first call in a new context of that
+ *    device (after cudaDeviceReset the array may sit at another address); make
+ *    that first call before any stream capture;
  *  - every call shares the one array, so calls that overlap on the GPU (two
  *    streams, two host threads) race and give wrong results: serialise them;
  *  - it calls no cudaMalloc, cudaFree or other allocating routine. */

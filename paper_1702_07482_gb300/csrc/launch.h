@@ -36,8 +36,13 @@ cudaError_t launch_tc_fwd(int ks, int nk, int nb, bool bf16, const StageArgs& a,
                           cudaStream_t s);
 cudaError_t tc_take_error(int* out);
 // Address of that word on the current device (null if it cannot be had); the
-// fused stages record a tile copy that never landed there too.
+// fused stages record a tile copy that never landed there too.  Looked up
+// again whenever the current context changes (after a device reset the
+// module, and with it the word, can sit at another address).
 int* device_status_word();
+// Unique id of the current CUDA context (cuCtxGetId), 0 if there is none or
+// it cannot be read.
+unsigned long long current_context_id();
 
 // Bulk-tensor-copy staging of u_{t-1} tiles: TNRD_TMA=0 turns it off (the
 // kernels gather instead); a 3-D [N][H][pitch] float32 tensor map with a

@@ -17,7 +17,15 @@ __device__ __align__(256) float g_noalloc_scratch[TNRD_NOALLOC_MAX_FLOATS];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-float* g_scratch_ptr[kMaxDevices] = {};
+// Per device: the array's device address and the id of the context it was
+// looked up in.  A device reset (cudaDeviceReset) ends that context and may
+// load the module, and with it the array, at another address; a call in a new
+// context therefore looks the address up again instead of using a stale one.
+struct ScratchSlot {
+    unsigned long long ctx;
+    float* ptr;
+};
+ScratchSlot g_scratch[kMaxDevices] = {};
 
 }  // namespace
 
@@ -42,22 +50,35 @@ extern "C" tnrd_status tnrd_forward_noalloc(const tnrd_params* params, int N, in
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return tnrd::set_error(TNRD_ERR_CUDA, "tnrd_forward_noalloc: cudaGetDevice failed");
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return tnrd::set_error(TNRD_ERR_CUDA, "tnrd_forward_noalloc: cudaGetDevice failed");
+    }
     if (dev < 0 || dev >= kMaxDevices)
         return tnrd::set_error(TNRD_ERR_UNSUPPORTED, "tnrd_forward_noalloc: device index too large");
     float* scratch;
     {
-        // Set-up, once per device, with that device current.
+        // Set-up, once per device (and again in a new context), with that
+        // device current.
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        ScratchSlot& slot = g_scratch[dev];
+        const unsigned long long ctx = tnrd::current_context_id();
+        if (!slot.ptr || ctx == 0 || ctx != slot.ctx) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p)
-                return tnrd::set_error(TNRD_ERR_CUDA,
-                                       "tnrd_forward_noalloc: cudaGetSymbolAddress of the scratch failed");
-            g_scratch_ptr[dev] = static_cast<float*>(p);
+            if (e != cudaSuccess || !p) {
+                (void)cudaGetLastError();   // leave no stale error for the caller's next check
+                slot.ptr = nullptr;
+                char msg[256];
+                snprintf(msg, sizeof msg,
+                         "tnrd_forward_noalloc: cudaGetSymbolAddress of the scratch failed: %s (%s)",
+                         cudaGetErrorName(e), cudaGetErrorString(e));
+                return tnrd::set_error(TNRD_ERR_CUDA, msg);
+            }
+            slot.ptr = static_cast<float*>(p);
+            slot.ctx = tnrd::current_context_id();   // the lookup may have made it current
         }
-        scratch = g_scratch_ptr[dev];
+        scratch = slot.ptr;
     }
     // The scratch holds the image between stages; it is always written before
     // it is read, so it needs no clearing.

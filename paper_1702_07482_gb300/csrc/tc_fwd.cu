@@ -1,5 +1,5 @@
 // Instantiations and launcher of the tensor-core forward stage.
-#include <atomic>
+#include <mutex>
 
 #include "launch.h"
 #include "tc_fwd.cuh"
@@ -64,21 +64,34 @@ cudaError_t launch_tc_batch(int ks, int nk, int nb, bool bf16, const BatchArgs& 
 
 int* device_status_word()
 {
+    // Per device: the word's address and the context it was looked up in.  A
+    // new context (e.g. after cudaDeviceReset) means a new lookup.
     constexpr int MAXDEV = 64;
-    static std::atomic<int*> words[MAXDEV] = {};   // per device, filled on first use
+    struct Slot {
+        unsigned long long ctx;
+        int* word;
+    };
+    static std::mutex mu;
+    static Slot slots[MAXDEV] = {};
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return nullptr;
-    int* w = words[dev].load(std::memory_order_acquire);
-    if (!w) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    const unsigned long long ctx = current_context_id();
+    Slot& s = slots[dev];
+    if (!s.word || ctx == 0 || ctx != s.ctx) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_tc_error) != cudaSuccess) {
+        if (cudaGetSymbolAddress(&p, g_tc_error) != cudaSuccess || !p) {
             (void)cudaGetLastError();
+            s.word = nullptr;
             return nullptr;
         }
-        w = static_cast<int*>(p);
-        words[dev].store(w, std::memory_order_release);   // every thread stores the same address
+        s.word = static_cast<int*>(p);
+        s.ctx = current_context_id();   // the lookup may have made the context current
     }
-    return w;
+    return s.word;
 }
 
 cudaError_t tc_take_error(int* out)

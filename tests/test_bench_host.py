@@ -41,3 +41,31 @@ def test_traffic_pin_follows_the_captured_kernel(bench, monkeypatch):
     assert bench._measured_traffic(pin["kernel"]) is None
     # at least one full plane read, below all three planes read and written
     assert 1 << 20 < pin["bytes_per_launch"] < 4 * (1 << 20)
+
+
+def test_split_roofline_of_the_tensor_core_stage(bench):
+    """Mixed precision: T_min = max(conv flops / tensor peak, (phi + prox) flops /
+    FP32 peak), the binding term reported with frac = T_min / T."""
+    class Wl:
+        flops_per_px_stage = bench.FLOPS_PER_PX_STAGE
+        flops = 1e9 * bench.FLOPS_PER_PX_STAGE     # 1e9 pixel-stages
+        traffic, kernel, launches = None, "tc", 8
+    assert bench.CONV_FLOPS_PER_PX_STAGE + bench.ALU_FLOPS_PER_PX_STAGE == bench.FLOPS_PER_PX_STAGE
+    peaks = {"bf16_tflops_sustained": 1700.0}
+    ms = 200.0
+    r = bench._split_roofline(Wl, "tf32", ms, peaks, "measured", 80.0, 152, 2070.0)
+    t_alu = 1e9 * 6060 / 80e12
+    t_tc = 1e9 * 9408 / (1700e12 * 1.1 / 2.25)
+    assert r["bound"] == "alu" and t_alu > t_tc
+    assert r["frac"] == pytest.approx(t_alu / (ms / 1e3))
+    assert r["achieved"] / r["peak"] == pytest.approx(r["frac"])
+    assert r["terms"]["tensor"]["frac"] == pytest.approx(t_tc / (ms / 1e3))
+    # BF16 doubles the tensor peak: the ALU term binds all the more
+    r2 = bench._split_roofline(Wl, "bf16", ms, peaks, "measured", 80.0, 152, 2070.0)
+    assert r2["terms"]["tensor"]["peak"] == pytest.approx(1700.0)
+
+
+def test_reference_arm_config_equals_the_default_workload_config(bench):
+    # the driver compares the two arms' config: the reference line must name
+    # the same workload keys as the GPU arm's default line
+    assert bench.CONFIG["data_term"] == "idiv" and bench.CONFIG["H"] == bench.H == 512

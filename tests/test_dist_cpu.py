@@ -1,5 +1,6 @@
 """Multi-rank host logic on CPU (gloo, world size 2): image sharding and the
 whole-job rate reduction that bench.py uses with one process per GPU."""
+import dataclasses
 import os
 import socket
 
@@ -182,3 +183,86 @@ def test_row_bands_reproduce_the_whole_image(world):
         cut = H // 2
         short = oracle.forward(f[max(0, cut - ghost):].copy(), p)[-1][min(cut, ghost):]
         assert not np.array_equal(short[0], ref[cut])
+
+
+# Data-parallel training on the oracle: a batch of 4 crops, loss
+# L = sum_s 1/2 |u_T^s - clean^s|^2 (Eq. learning), split 2 + 2 over the ranks.
+_DP = dict(H=20, W=23, ks=3, nk=4, T=2, n=4, cfg=41)
+
+
+def _dp_case():
+    import synth
+    d = _DP
+    p = synth.params(d["T"], d["ks"], d["nk"], seed=synth.seed_for(d["cfg"], 0, "params"))
+    pairs = [synth.single_image(d["H"], d["W"], 1, d["cfg"], index=s) for s in range(d["n"])]
+    return p, pairs
+
+
+def _crop_grads(p, clean, f):
+    import oracle
+    u = oracle.forward(f, p)
+    _, gk, gw, gl = oracle.backward(f, p, u, u[-1] - clean)
+    return gk, gw, gl
+
+
+def _dp_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    from paper_1702_07482_gb300.shard import allreduce_gradients
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    p, pairs = _dp_case()
+    mine = range(rank * _DP["n"] // world, (rank + 1) * _DP["n"] // world)
+    acc = None
+    for s in mine:   # this rank's loss sums its own crops
+        g = _crop_grads(p, *pairs[s])
+        acc = list(g) if acc is None else [a + b for a, b in zip(acc, g)]
+    ts = []
+    for a in acc:
+        t = torch.zeros(a.shape, dtype=torch.float64, requires_grad=True)
+        t.grad = torch.from_numpy(np.ascontiguousarray(a))
+        ts.append(t)
+    allreduce_gradients(ts)
+    q.put((rank, [t.grad.numpy().copy() for t in ts]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_oracle_gradients_sum_to_the_whole_batch_gradient():
+    """Each gloo rank takes the oracle gradient (filters, RBF weights, lambda)
+    of its half of the batch; after allreduce_gradients both ranks hold the
+    oracle gradient of the whole batch's loss (to FP64 rounding) and agree bit
+    for bit.  The loss-sum convention is pinned by a finite difference of the
+    whole-batch loss in one lambda."""
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dp_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    out = dict(q.get(timeout=300) for _ in range(2))
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    p, pairs = _dp_case()
+    whole = None
+    for s in range(_DP["n"]):
+        g = _crop_grads(p, *pairs[s])
+        whole = list(g) if whole is None else [a + b for a, b in zip(whole, g)]
+    for k in range(3):
+        np.testing.assert_array_equal(out[0][k], out[1][k])
+        np.testing.assert_allclose(out[0][k], whole[k], rtol=1e-12,
+                                   atol=1e-12 * np.abs(whole[k]).max())
+
+    def loss(lam1):
+        lam = p.lam.copy()
+        lam[1] = lam1
+        pp = dataclasses.replace(p, lam=lam)
+        return sum(0.5 * float(((oracle.forward(f, pp)[-1] - c) ** 2).sum()) for c, f in pairs)
+
+    h = 1e-4 * p.lam[1]
+    fd = (loss(p.lam[1] + h) - loss(p.lam[1] - h)) / (2 * h)
+    assert abs(fd - out[0][2][1]) <= 1e-6 * max(1.0, abs(fd))
