@@ -326,8 +326,11 @@ struct BatchArgs {
 };
 
 // ---------------------------------------------------------------------------
-// Tensor-core stage (TNRD_ALGO_TC_TF32): filter bank and adjoint as implicit
-// GEMMs on tcgen05, phi and the prox on the CUDA cores.
+// Tensor-core stage (TNRD_ALGO_TC_TF32 / _BF16): filter bank and adjoint as
+// implicit GEMMs on tcgen05, phi and the prox on the CUDA cores.  One
+// persistent CTA per SM of NWG independent warpgroups; each warpgroup works
+// through its own tiles, the GEMMs' filter operands and the RBF weights are
+// staged once per CTA (per parameter set) and shared.
 // ---------------------------------------------------------------------------
 template <int KS, int NK, int NB, bool BF>
 struct TcCfg {
@@ -341,7 +344,7 @@ struct TcCfg {
     static constexpr int NPAD = (NK + 15) / 16 * 16;                 // N of the filter-bank GEMM
     static constexpr int NKP = (NK + KMMA - 1) / KMMA * KMMA;        // K of the adjoint GEMM
     static constexpr int NT = (KS * KS + 15) / 16 * 16;  // N of the adjoint GEMM (taps)
-    static_assert(NPAD <= 64 && NT <= 64, "TMEM columns: z at 0, Y at 64");
+    static_assert(NPAD <= 64 && NT <= 64, "TMEM: one 64-column buffer holds z or Y");
     static constexpr int UROWS = ZR + 2 * R;     // u rows from y0 - 2R
     // u operand row of one residue class r, in bytes:
     //  TF32: a copy shifted by r columns, 36 floats (A core row m = floats 4m..4m+3);
@@ -350,20 +353,34 @@ struct TcCfg {
     static constexpr int UPITCH = 36;            // TF32 floats per row
     static constexpr int UCHUNKS = 10;           // BF16 chunks per row
     static constexpr int UROWB = BF ? UCHUNKS * 16 : UPITCH * 4;
+    // raw u rows of the tile (columns x0 - 2R ..), staged once per tile and
+    // copied into the residue operands: TF32 reads 39 columns, BF16 47
+    static constexpr int RAWC = BF ? 47 : 39;
+    static constexpr int RAWP = BF ? 48 : 40;
     static constexpr int HROWS = ZR + 2 * R;     // h rows from y0 - 2R
     static constexpr int HPITCH = 41;            // h columns from x0 - 2R (41 = 1 mod 4: no bank conflicts)
     static constexpr int WPADN = MAX_NRBF + 2 * RBF_WPAD;
-    static constexpr int NTHREADS = 128;
     static constexpr size_t al(size_t x) { return (x + 127) / 128 * 128; }
-    static constexpr size_t OFF_U = 0;
-    static constexpr size_t OFF_BZ = al(OFF_U + 4ull * UROWS * UROWB);
+    static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
+    // shared by the CTA's warpgroups
+    static constexpr size_t OFF_BZ = 0;
     static constexpr size_t OFF_KM = al(OFF_BZ + (size_t)ESZ * KS * NPAD * KMMA);
-    static constexpr size_t OFF_V = al(OFF_KM + (size_t)ESZ * NT * NKP);
-    static constexpr size_t OFF_W = al(OFF_V + (size_t)ESZ * 128 * NKP);
-    static constexpr size_t OFF_H = al(OFF_W + 4ull * NK * WPADN);
-    static constexpr size_t OFF_MISC = al(OFF_H + 4ull * 4 * HROWS * HPITCH);
-    static constexpr size_t SMEM_BYTES = OFF_MISC + 128;
-    static constexpr uint32_t TMEM_COLS = 256;   // z double buffer (2 x 64) + Y (64), 2 CTAs per SM
+    static constexpr size_t OFF_W = al(OFF_KM + (size_t)ESZ * NT * NKP);
+    static constexpr size_t OFF_WG = al(OFF_W + 4ull * NK * WPADN);
+    // per warpgroup: u operands, V (the raw u rows before the first group), h, barriers
+    static constexpr size_t WG_U = 0;
+    static constexpr size_t WG_V = al(WG_U + 4ull * UROWS * UROWB);
+    static constexpr size_t WG_H = al(WG_V + mx((size_t)ESZ * 128 * NKP, 4ull * UROWS * RAWP));
+    static constexpr size_t WG_MISC = al(WG_H + 4ull * HROWS * HPITCH);
+    static constexpr size_t WG_BYTES = al(WG_MISC + 32);
+    static constexpr size_t SMEM_MAX = 227 * 1024;
+    static constexpr int fit_wg(int n) { return (n > 1 && OFF_WG + (size_t)n * WG_BYTES + 16 > SMEM_MAX) ? fit_wg(n - 1) : n; }
+    static constexpr int NWG = fit_wg(4);        // warpgroups per CTA (TMEM: 128 columns each)
+    static constexpr int NTHREADS = 128 * NWG;
+    static constexpr size_t OFF_TMEM = OFF_WG + (size_t)NWG * WG_BYTES;
+    static constexpr size_t SMEM_BYTES = OFF_TMEM + 16;
+    static constexpr uint32_t TMEM_COLS = NWG <= 2 ? 256 : 512;
+    static_assert(SMEM_BYTES <= SMEM_MAX, "shared memory");
 };
 
 }  // namespace tnrd

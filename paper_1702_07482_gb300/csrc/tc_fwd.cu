@@ -1,4 +1,5 @@
 // Instantiations and launcher of the tensor-core forward stage.
+#include <algorithm>
 #include <mutex>
 
 #include "launch.h"
@@ -8,6 +9,23 @@ namespace tnrd {
 
 namespace {
 
+int sm_count()
+{
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return nsm > 0 ? nsm : 1;
+}
+
+// Persistent grid: at most one CTA per SM, and no more CTAs than there are
+// tiles for their warpgroups.
+template <int KS, int NK, int NB, bool BF>
+int tc_grid(long long ntiles)
+{
+    using C = TcCfg<KS, NK, NB, BF>;
+    const long long need = (ntiles + C::NWG - 1) / C::NWG;
+    return (int)std::max(1LL, std::min((long long)sm_count(), need));
+}
+
 template <int KS, int NK, int NB, bool BF>
 cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
 {
@@ -16,7 +34,8 @@ cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    tc_stage_fwd<KS, NK, NB, BF><<<dim3(a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(a);
+    const int grid = tc_grid<KS, NK, NB, BF>((long long)N * a.tiles_x * a.tiles_y);
+    tc_stage_fwd<KS, NK, NB, BF><<<grid, C::NTHREADS, C::SMEM_BYTES, s>>>(a, N);
     return cudaGetLastError();
 }
 
@@ -28,7 +47,7 @@ cudaError_t launch_batch_one(const BatchArgs& a, int t, int ntiles, cudaStream_t
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    tc_batch_fwd<KS, NK, NB, BF><<<ntiles, C::NTHREADS, C::SMEM_BYTES, s>>>(a, t);
+    tc_batch_fwd<KS, NK, NB, BF><<<tc_grid<KS, NK, NB, BF>(ntiles), C::NTHREADS, C::SMEM_BYTES, s>>>(a, t);
     return cudaGetLastError();
 }
 

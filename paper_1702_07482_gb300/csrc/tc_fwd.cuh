@@ -1,9 +1,16 @@
-// Tensor-core forward stage (TNRD_ALGO_TC_TF32):
-//   z = K u      as an implicit GEMM  D_z[pixel][filter] (tcgen05, TF32 in, FP32 acc)
+// Tensor-core forward stage (TNRD_ALGO_TC_TF32 / _BF16) of Eq. diffusionprocessfinal:
+//   z = K u      as an implicit GEMM  D_z[pixel][filter] (tcgen05, FP32 accumulation)
 //   v = phi(z)   on the CUDA cores (FP32), each thread one pixel, all filters
 //   Y = V Kmat   as a GEMM            D_Y[pixel][tap] = sum_i v_i(pixel) k_i[tap]
 //   h(q) = sum_tap Y[q + off(tap)][tap]   (adjoint; scattered on the CUDA cores)
 //   u_t = prox(u_{t-1} - fold(h))         (FP32, IEEE sqrt/div)
+//
+// Launch: one persistent CTA per SM made of NWG independent warpgroups (three
+// for TF32, four for BF16).  The CTA takes a contiguous run of the launch's
+// tiles; its warpgroups work through them in turn, each with its own tile
+// buffers, TMEM columns and mbarriers and its own elected thread issuing the
+// MMAs.  The filter operands of both GEMMs and the RBF weights are staged once
+// per CTA and parameter set (a batch may change sets between images).
 //
 // Tile: TH = 16 NB - 2R rows x TW = 32 - 2R columns of output; its z-region is
 // 16 NB rows x 32 columns.  One MMA group = 128 z positions: 16 rows of one
@@ -18,14 +25,30 @@
 // (leading offset 16 B, overlapping the first); the next 8-pixel group is the
 // next image row (stride offset = the copy's row pitch).  Kernel row a is one
 // MMA of K = 8 with the start row shifted by a; taps b' >= ksize are zero in B.
+// The raw u rows of the tile are read from global memory once and the four
+// residue copies built from them in shared memory.
 //
-// TNRD_ALGO_TC_BF16 (BF = true) runs the same tile and groups with BF16
-// operands (kind::f16, K = 16 per MMA, FP32 accumulation).  A BF16 core-matrix
-// row is 8 values, so residue r of u is kept as overlapping chunks of 8:
-// chunk c of a row holds u columns 4c + r .. 4c + r + 7.  Core row m is chunk
-// m (pixel column r + 4m, taps 0..7) and the second K core (taps 8..15) is
-// chunk m + 2, 32 bytes on.  V and the adjoint's filter matrix are BF16 too;
-// phi, the scatter, the fold and the prox stay FP32.
+// BF16 (BF = true) runs the same tile and groups with BF16 operands
+// (kind::f16, K = 16 per MMA, FP32 accumulation).  A BF16 core-matrix row is 8
+// values, so residue r of u is kept as overlapping chunks of 8: chunk c of a
+// row holds u columns 4c + r .. 4c + r + 7.  Core row m is chunk m (pixel
+// column r + 4m, taps 0..7) and the second K core (taps 8..15) is chunk m + 2,
+// 32 bytes on.  V and the adjoint's filter matrix are BF16 too; phi, the
+// scatter, the fold and the prox stay FP32.
+//
+// TMEM: each warpgroup owns 128 columns, two buffers of 64.  Group g's z lands
+// in buffer g & 1; once phi has read it, the same buffer receives group g's Y,
+// and once Y has been read, group g + 2's z.  So the filter bank of the next
+// group always runs on the tensor core while phi of this one runs on the SM.
+//
+// Adjoint scatter into ONE h buffer per warpgroup, in kernel-row phases: lane
+// (g, mp) of warp w (pixel row 4w + g' of the row block, g = 4w + g') adds its
+// tap (a, b) value at h row (row - a).  In one phase all warps use the same a,
+// so their rows are disjoint; a warpgroup barrier separates the phases.  Within
+// a warp two lanes reach the same element only through taps b and b +- 4 of the
+// same row, so a warp barrier before each run of taps with b in [0, 4) or
+// [4, 8) keeps every read-modify-write whole.  The sums are in a fixed order:
+// repeated runs give the same bits.
 #pragma once
 #include "args.cuh"
 #include "tc_ptx.cuh"
@@ -37,147 +60,265 @@ namespace tnrd {
 // header (the library is built without relocatable device code).
 __device__ int g_tc_error = 0;
 
-// One stage on one tile (the whole CTA).  err receives TNRD_ERR_TIMEOUT (4)
-// when a wait on the tensor core gives up (the tile's output is then not written).
+// What one tile needs besides the shared filter operands.
+struct TcTile {
+    const float* u_in;
+    float* u_out;
+    const float* f;
+    int H, W, pitch;
+    int tiles_x, tiles_y, ty, tx;
+    const float* lam;
+    int dterm;
+    float proj_c;
+};
+
+// One parameter set of the stage.
+struct TcSet {
+    const float* k;       // [NK][KS][KS]
+    const float* w;       // [NK][nrbf]
+    int nrbf;
+    const RbfConst* rc;
+};
+
+// Tiles of a per-call stage: N images of tiles_x * tiles_y tiles, one set.
+struct TcCallSrc {
+    const StageArgs* a;
+    int n_img;
+    __device__ int ntiles() const { return n_img * a->tiles_x * a->tiles_y; }
+    __device__ int set_of(int) const { return 0; }
+    __device__ int seg_end(int, int c1) const { return c1; }
+    __device__ TcSet params(int) const { return TcSet{a->k, a->w, a->nrbf, &a->rc}; }
+    __device__ TcTile tile(int s) const
+    {
+        const int tpi = a->tiles_x * a->tiles_y;
+        const int n = s / tpi, ti = s - n * tpi;
+        TcTile j;
+        j.u_in = a->u_in + (size_t)n * a->img_stride;
+        j.u_out = a->u_out + (size_t)n * a->img_stride;
+        j.f = a->f + (size_t)n * a->img_stride;
+        j.H = a->H;
+        j.W = a->W;
+        j.pitch = a->pitch;
+        j.tiles_x = a->tiles_x;
+        j.tiles_y = a->tiles_y;
+        j.ty = ti / a->tiles_x;
+        j.tx = ti - j.ty * a->tiles_x;
+        j.lam = a->lam;
+        j.dterm = a->dterm;
+        j.proj_c = a->proj_c;
+        return j;
+    }
+};
+
+// Tiles of stage t of a batched plan: the plan's tile table gives each global
+// tile its (image, tile); each image its buffers, parameter set and data
+// term.  Stage t writes u when (T-1-t) is even and the plan's inter-stage
+// image otherwise, so the last stage lands in u.
+template <int KS, int NK>
+struct TcBatchSrc {
+    const BatchArgs* a;
+    int t;
+    __device__ int ntiles() const { return a->ntiles; }
+    __device__ int set_of(int s) const { return a->imgs[a->tile_img[s].x].set; }
+    __device__ int seg_end(int s, int c1) const
+    {
+        const int set = set_of(s);
+        int e = s + 1;
+        while (e < c1 && set_of(e) == set) ++e;
+        return e;
+    }
+    __device__ TcSet params(int set) const
+    {
+        const BatchSet& ps = a->sets[set];
+        return TcSet{ps.k + (size_t)t * NK * KS * KS, ps.w + (size_t)t * NK * a->nrbf, a->nrbf, &ps.rc};
+    }
+    __device__ TcTile tile(int s) const
+    {
+        const int2 ti = a->tile_img[s];
+        const BatchImg& im = a->imgs[ti.x];
+        const BatchSet& ps = a->sets[im.set];
+        TcTile j;
+        j.u_out = ((a->T - 1 - t) % 2 == 0) ? im.u : im.tmp;
+        j.u_in = (t == 0) ? im.f : (((a->T - t) % 2 == 0) ? im.u : im.tmp);
+        j.f = im.f;
+        j.H = im.H;
+        j.W = im.W;
+        j.pitch = im.pitch;
+        j.tiles_x = im.tiles_x;
+        j.tiles_y = im.tiles_y;
+        j.ty = ti.y / im.tiles_x;
+        j.tx = ti.y - j.ty * im.tiles_x;
+        j.lam = ps.lam + t;
+        j.dterm = ps.dterm;
+        j.proj_c = ps.proj_c;
+        return j;
+    }
+};
+
+// Filter operands of both GEMMs and the padded RBF weights of one parameter
+// set, by all threads of the CTA.
 template <int KS, int NK, int NB, bool BF>
-__device__ __forceinline__ void tc_tile(const TileJob& a, unsigned char* smem, int* err)
+__device__ __forceinline__ void tc_stage_consts(const TcSet& ps, unsigned char* smem, int tid)
 {
     using C = TcCfg<KS, NK, NB, BF>;
-    constexpr int R = C::R, TW = C::TW, TH = C::TH;
-    constexpr long long WAIT_LIMIT = 1ll << 31;   // SM cycles, about one second
-    float* sU = reinterpret_cast<float*>(smem + C::OFF_U);
-    float* sBz = reinterpret_cast<float*>(smem + C::OFF_BZ);
-    float* sKm = reinterpret_cast<float*>(smem + C::OFF_KM);
-    float* sV = reinterpret_cast<float*>(smem + C::OFF_V);
-    float* sW = reinterpret_cast<float*>(smem + C::OFF_W);
-    float* sH = reinterpret_cast<float*>(smem + C::OFF_H);
-    uint64_t* mbz = reinterpret_cast<uint64_t*>(smem + C::OFF_MISC);       // 2 barriers
-    uint64_t* mby = reinterpret_cast<uint64_t*>(smem + C::OFF_MISC + 16);
-    uint32_t* tbase = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC + 24);
-
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int ty = a.ty, tx = a.tx;
-    const int H = a.H, W = a.W;
-    const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
-    const bool border = (ty == 0) || (ty == a.tiles_y - 1) || (tx == 0) || (tx == a.tiles_x - 1);
-    const float* uin = a.u_in;
-
-    // ---- stage operands in shared memory ----------------------------------
+    constexpr int NTH = C::NTHREADS;
     if constexpr (!BF) {
-        constexpr int UCOPY = C::UROWS * C::UPITCH;
-        for (int idx = tid; idx < 4 * UCOPY; idx += 128) {
-            const int r = idx / UCOPY, rem = idx - r * UCOPY;
-            const int i = rem / C::UPITCH, j = rem - i * C::UPITCH;
-            const int yy = sym_idx(y0 - 2 * R + i, H), xx = sym_idx(x0 - 2 * R + j + r, W);
-            sU[idx] = tc::to_tf32(__ldcg(uin + (size_t)yy * a.pitch + xx));
-        }
+        float* sBz = reinterpret_cast<float*>(smem + C::OFF_BZ);
+        float* sKm = reinterpret_cast<float*>(smem + C::OFF_KM);
         // B of the filter bank, per kernel row ka: B[nn][b'] = k_nn[ka][KS-1-b'],
         // K-major core matrices [nn/8][b'/4][nn%8][b'%4]
-        for (int e = tid; e < KS * C::NPAD * 8; e += 128) {
+        for (int e = tid; e < KS * C::NPAD * 8; e += NTH) {
             const int ka = e / (C::NPAD * 8), rem = e - ka * (C::NPAD * 8);
             const int nn = rem / 8, k = rem - nn * 8;
-            const float v = (nn < NK && k < KS) ? __ldg(a.k + (nn * KS + ka) * KS + (KS - 1 - k)) : 0.0f;
+            const float v = (nn < NK && k < KS) ? __ldg(ps.k + (nn * KS + ka) * KS + (KS - 1 - k)) : 0.0f;
             sBz[ka * C::NPAD * 8 + ((nn / 8) * 2 + k / 4) * 32 + (nn % 8) * 4 + (k % 4)] = tc::to_tf32(v);
         }
         // B of the adjoint GEMM: B[tap][i] = k_i[tap], core matrices [i/4][tap/8][tap%8][i%4]
-        for (int e = tid; e < C::NT * C::NKP; e += 128) {
+        for (int e = tid; e < C::NT * C::NKP; e += NTH) {
             const int tap = e / C::NKP, i = e - tap * C::NKP;
-            const float v = (tap < KS * KS && i < NK) ? __ldg(a.k + i * KS * KS + tap) : 0.0f;
+            const float v = (tap < KS * KS && i < NK) ? __ldg(ps.k + i * KS * KS + tap) : 0.0f;
             sKm[((i / 4) * (C::NT / 8) + tap / 8) * 32 + (tap % 8) * 4 + (i % 4)] = tc::to_tf32(v);
         }
     } else {
-        // u chunks, two values per 32-bit store: [r][row][chunk][8]
-        uint32_t* sU2 = reinterpret_cast<uint32_t*>(sU);
-        constexpr int PAIRS = 4 * C::UROWS * C::UCHUNKS * 4;
-        for (int idx = tid; idx < PAIRS; idx += 128) {
-            const int e2 = idx & 3, c = (idx >> 2) % C::UCHUNKS, ri = (idx >> 2) / C::UCHUNKS;
-            const int r = ri / C::UROWS, i = ri - r * C::UROWS;
-            const int yy = sym_idx(y0 - 2 * R + i, H);
-            const int x = x0 - 2 * R + 4 * c + r + 2 * e2;
-            const float* ur = uin + (size_t)yy * a.pitch;
-            sU2[idx] = tc::pack_bf16x2(__ldcg(ur + sym_idx(x, W)), __ldcg(ur + sym_idx(x + 1, W)));
-        }
         // B of the filter bank, per kernel row ka: B[nn][b'] = k_nn[ka][KS-1-b'] (b' < 16),
         // core matrices [nn/8][b'/8][nn%8][b'%8]
-        uint32_t* sBz2 = reinterpret_cast<uint32_t*>(sBz);
-        for (int e = tid; e < KS * C::NPAD * 8; e += 128) {
+        uint32_t* sBz2 = reinterpret_cast<uint32_t*>(smem + C::OFF_BZ);
+        for (int e = tid; e < KS * C::NPAD * 8; e += NTH) {
             const int ka = e / (C::NPAD * 8), rem = e - ka * (C::NPAD * 8);
             const int nn = rem / 8, k = 2 * (rem - nn * 8);
-            const float v0 = (nn < NK && k < KS) ? __ldg(a.k + (nn * KS + ka) * KS + (KS - 1 - k)) : 0.0f;
-            const float v1 = (nn < NK && k + 1 < KS) ? __ldg(a.k + (nn * KS + ka) * KS + (KS - 2 - k)) : 0.0f;
+            const float v0 = (nn < NK && k < KS) ? __ldg(ps.k + (nn * KS + ka) * KS + (KS - 1 - k)) : 0.0f;
+            const float v1 = (nn < NK && k + 1 < KS) ? __ldg(ps.k + (nn * KS + ka) * KS + (KS - 2 - k)) : 0.0f;
             sBz2[(ka * C::NPAD * 16 + ((nn / 8) * 2 + k / 8) * 64 + (nn % 8) * 8 + (k % 8)) / 2] =
                 tc::pack_bf16x2(v0, v1);
         }
         // B of the adjoint GEMM: B[tap][i] = k_i[tap], core matrices [i/8][tap/8][tap%8][i%8]
-        uint32_t* sKm2 = reinterpret_cast<uint32_t*>(sKm);
-        for (int e = tid; e < C::NT * C::NKP / 2; e += 128) {
+        uint32_t* sKm2 = reinterpret_cast<uint32_t*>(smem + C::OFF_KM);
+        for (int e = tid; e < C::NT * C::NKP / 2; e += NTH) {
             const int tap = e / (C::NKP / 2), i = 2 * (e - tap * (C::NKP / 2));
             const bool tok = tap < KS * KS;
-            const float v0 = (tok && i < NK) ? __ldg(a.k + i * KS * KS + tap) : 0.0f;
-            const float v1 = (tok && i + 1 < NK) ? __ldg(a.k + (i + 1) * KS * KS + tap) : 0.0f;
+            const float v0 = (tok && i < NK) ? __ldg(ps.k + i * KS * KS + tap) : 0.0f;
+            const float v1 = (tok && i + 1 < NK) ? __ldg(ps.k + (i + 1) * KS * KS + tap) : 0.0f;
             sKm2[(((i / 8) * (C::NT / 8) + tap / 8) * 64 + (tap % 8) * 8 + (i % 8)) / 2] =
                 tc::pack_bf16x2(v0, v1);
         }
     }
-    for (int e = tid; e < NK * C::WPADN; e += 128) {
+    float* sW = reinterpret_cast<float*>(smem + C::OFF_W);
+    for (int e = tid; e < NK * C::WPADN; e += NTH) {
         const int i = e / C::WPADN, jj = e - i * C::WPADN - RBF_WPAD;
-        sW[e] = (jj >= 0 && jj < a.nrbf) ? __ldg(a.w + i * a.nrbf + jj) : 0.0f;
+        sW[e] = (jj >= 0 && jj < ps.nrbf) ? __ldg(ps.w + i * ps.nrbf + jj) : 0.0f;
     }
-    for (int e = tid; e < C::ESZ * 128 * C::NKP / 4; e += 128) sV[e] = 0.0f;
-    for (int e = tid; e < 4 * C::HROWS * C::HPITCH; e += 128) sH[e] = 0.0f;
-    if (tid == 0) {
-        tc::mbar_init(mbz + 0, 1);
-        tc::mbar_init(mbz + 1, 1);
-        tc::mbar_init(mby, 1);
+}
+
+// Per-warpgroup pipeline state: parity of each mbarrier's next phase (bit 0, 1:
+// z buffers, bit 2: Y) and which of them have a commit outstanding.
+struct TcPipe {
+    uint32_t ph = 0, pend = 0;
+};
+
+// One stage on one tile, by one warpgroup (bar: its named barrier).  Returns
+// 0 if a wait on the tensor core gave up (the tile's output is then not
+// written); uniform over the warpgroup.
+template <int KS, int NK, int NB, bool BF>
+__device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsigned char* smem,
+                                       unsigned char* wgs, uint32_t tmem, uint64_t* mb, TcPipe& pp,
+                                       int wt, int bar)
+{
+    using C = TcCfg<KS, NK, NB, BF>;
+    constexpr int R = C::R, TW = C::TW, TH = C::TH;
+    constexpr long long WAIT_LIMIT = 1ll << 31;   // SM cycles, about one second
+    float* sU = reinterpret_cast<float*>(wgs + C::WG_U);
+    float* sV = reinterpret_cast<float*>(wgs + C::WG_V);
+    float* sH = reinterpret_cast<float*>(wgs + C::WG_H);
+    const float* sW = reinterpret_cast<const float*>(smem + C::OFF_W);
+    const uint32_t sBz = tc::smem_u32(smem + C::OFF_BZ);
+    const uint32_t sKm = tc::smem_u32(smem + C::OFF_KM);
+
+    const int warp = wt >> 5;
+    const int H = a.H, W = a.W;
+    const int y0 = tile_origin(a.ty, TH, H), x0 = tile_origin(a.tx, TW, W);
+    const bool border = (a.ty == 0) || (a.ty == a.tiles_y - 1) || (a.tx == 0) || (a.tx == a.tiles_x - 1);
+    const float* uin = a.u_in;
+
+    // ---- stage u: raw rows (in the V area), then the residue operands --------
+    tc::wg_sync(bar);   // the previous tile's epilogue has read h
+    {
+        float* raw = sV;
+        const int ry = y0 - 2 * R, rx = x0 - 2 * R;
+        const bool inner = ry >= 0 && ry + C::UROWS <= H && rx >= 0 && rx + C::RAWC <= W;
+        for (int idx = wt; idx < C::UROWS * C::RAWC; idx += 128) {
+            const int i = idx / C::RAWC, j = idx - i * C::RAWC;
+            const int yy = inner ? ry + i : sym_idx(ry + i, H);
+            const int xx = inner ? rx + j : sym_idx(rx + j, W);
+            raw[i * C::RAWP + j] = __ldcg(uin + (size_t)yy * a.pitch + xx);
+        }
+        for (int e = wt; e < C::HROWS * C::HPITCH; e += 128) sH[e] = 0.0f;
+        tc::wg_sync(bar);
+        if constexpr (!BF) {
+            constexpr int UCOPY = C::UROWS * C::UPITCH;
+            for (int idx = wt; idx < 4 * UCOPY; idx += 128) {
+                const int r = idx / UCOPY, rem = idx - r * UCOPY;
+                const int i = rem / C::UPITCH, j = rem - i * C::UPITCH;
+                sU[idx] = tc::to_tf32(raw[i * C::RAWP + j + r]);
+            }
+        } else {
+            // u chunks, two values per 32-bit store: [r][row][chunk][8]
+            uint32_t* sU2 = reinterpret_cast<uint32_t*>(sU);
+            constexpr int PAIRS = 4 * C::UROWS * C::UCHUNKS * 4;
+            for (int idx = wt; idx < PAIRS; idx += 128) {
+                const int e2 = idx & 3, c = (idx >> 2) % C::UCHUNKS, ri = (idx >> 2) / C::UCHUNKS;
+                const int r = ri / C::UROWS, i = ri - r * C::UROWS;
+                const float* rr = raw + i * C::RAWP + 4 * c + r + 2 * e2;
+                sU2[idx] = tc::pack_bf16x2(rr[0], rr[1]);
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        tc::wg_sync(bar);   // operands complete; the raw rows are no longer needed
+        tc::fence_after();
     }
-    if (warp == 0) tc::tmem_alloc(tbase, C::TMEM_COLS);
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = *tbase;
-    // TMEM columns: z of even groups at 0, z of odd groups at 64, Y at 128
-    const uint32_t tyv = tmem + 128;
+
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     constexpr uint32_t FMT = BF ? tc::FMT_BF16 : tc::FMT_TF32;
     constexpr uint32_t ID_Z = tc::idesc(FMT, 128, C::NPAD);
     constexpr uint32_t ID_Y = tc::idesc(FMT, 128, C::NT);
     constexpr uint32_t LBO_KM = (C::NT / 8) * 128;
-    const RbfConst& rc = *a.rc;
-
-    const int g = tid >> 3, mp = tid & 7;       // this thread's pixel in every group
-    float* myh = sH + warp * (C::HROWS * C::HPITCH);
-    uint32_t phz = 0u, phy = 0u;   // bit b of phz: parity of z buffer b's next phase
-    int ok = 1;
     constexpr int NG = 4 * NB;                  // groups (row block, residue) per tile
+    const int g = wt >> 3, mp = wt & 7;         // this thread's pixel in every group
 
-    // z = K u of group gi into TMEM buffer zb: one MMA (K = 32 bytes) per kernel row
-    auto issue_z = [&](int gi, int zb) {
-        const int nb = gi >> 2, r = gi & 3;
+    // z = K u of group gi into TMEM buffer gi & 1: one MMA (K = 32 bytes) per kernel row
+    auto issue_z = [&](int gi) {
+        const int nb = gi >> 2, r = gi & 3, zb = gi & 1;
         const uint32_t ur = tc::smem_u32(sU) + (uint32_t)(r * C::UROWS * C::UROWB);
 #pragma unroll
         for (int ka = 0; ka < KS; ++ka) {
             const uint64_t da = tc::sdesc(ur + (uint32_t)((16 * nb + 2 * R - ka) * C::UROWB),
                                           BF ? 32 : 16, C::UROWB);
-            const uint64_t db = tc::sdesc(tc::smem_u32(sBz) + (uint32_t)(ka * C::NPAD * 32), 128, 256);
+            const uint64_t db = tc::sdesc(sBz + (uint32_t)(ka * C::NPAD * 32), 128, 256);
             if constexpr (BF) tc::mma_f16(tmem + 64u * zb, da, db, ID_Z, ka > 0);
             else tc::mma_tf32(tmem + 64u * zb, da, db, ID_Z, ka > 0);
         }
-        tc::commit(mbz + zb);
+        tc::commit(mb + zb);
     };
-    if (tid == 0) issue_z(0, 0);
+    if (wt == 0) {
+        issue_z(0);
+        issue_z(1);
+    }
+    pp.pend |= 3u;
+    int ok = 1;
 
 #pragma unroll 1
     for (int gi = 0; gi < NG; ++gi) {
         const int nb = gi >> 2, r = gi & 3, zb = gi & 1;
-        if (ok) {
-            ok = tc::mbar_wait(mbz + zb, (phz >> zb) & 1u, WAIT_LIMIT);
-            phz ^= 1u << zb;
-            tc::fence_after();
+        const uint32_t tbuf = tmem + 64u * zb;
+        {
+            const bool got = ok && tc::mbar_wait(mb + zb, (pp.ph >> zb) & 1u, WAIT_LIMIT);
+            if (got) {
+                pp.ph ^= 1u << zb;
+                pp.pend &= ~(1u << zb);
+            }
+            ok = tc::wg_and(bar, got);
         }
-        ok = __syncthreads_and(ok);
-        // the next group's filter bank runs on the tensor core during phi
-        if (ok && tid == 0 && gi + 1 < NG) issue_z(gi + 1, zb ^ 1);
+        tc::fence_after();
         // ---- v = phi(z) into the A operand of the adjoint GEMM -------------------
         const int yy = y0 - R + 16 * nb + g, xx = x0 - R + r + 4 * mp;
         const bool inside = (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
@@ -185,7 +326,7 @@ __device__ __forceinline__ void tc_tile(const TileJob& a, unsigned char* smem, i
 #pragma unroll 1
             for (int c8 = 0; c8 < NK; c8 += 8) {
                 float z[8], v[8];
-                tc::tmem_ld8(tmem + 64u * zb + lane_base + c8, z);
+                tc::tmem_ld8(tbuf + lane_base + c8, z);
                 // branch-free: the 8 evaluations are independent and interleave
                 // (z is finite everywhere: u is mirror-loaded), then masked
 #pragma unroll
@@ -210,75 +351,83 @@ __device__ __forceinline__ void tc_tile(const TileJob& a, unsigned char* smem, i
                                      tc::pack_bf16x2(v[4], v[5]), tc::pack_bf16x2(v[6], v[7]));
                 }
             }
+            if constexpr (BF) {
+                // K padding of the adjoint GEMM (filters NK .. NKP-1): zeros, not
+                // whatever the raw u rows left there (a NaN pattern times 0 is NaN)
+#pragma unroll
+                for (int c8 = (NK + 7) / 8 * 8; c8 < C::NKP; c8 += 8)
+                    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(sV) +
+                                              ((c8 / 8) * 16 + g) * 128 + mp * 16) = make_uint4(0, 0, 0, 0);
+            }
         }
         tc::fence_async_smem();
         tc::fence_before();
-        __syncthreads();
+        tc::wg_sync(bar);
         tc::fence_after();
-        // ---- Y = V Kmat ----------------------------------------------------------
-        if (ok) {
-            if (tid == 0) {
-                // one MMA per two K cores (8 filters TF32, 16 filters BF16): 4 KB of V
-                // and 2 LBO_KM of the filter matrix apart
+        // ---- Y = V Kmat into the same buffer (z has been read) -------------------
+        if (ok && wt == 0) {
+            // one MMA per two K cores (8 filters TF32, 16 filters BF16): 4 KB of V
+            // and 2 LBO_KM of the filter matrix apart
 #pragma unroll
-                for (int s = 0; s < C::NKP / C::KMMA; ++s) {
-                    const uint64_t da = tc::sdesc(tc::smem_u32(sV) + (uint32_t)(s * 4096), 16 * 128, 128);
-                    const uint64_t db = tc::sdesc(tc::smem_u32(sKm) + (uint32_t)(s * 2 * LBO_KM), LBO_KM, 128);
-                    if constexpr (BF) tc::mma_f16(tyv, da, db, ID_Y, s > 0);
-                    else tc::mma_tf32(tyv, da, db, ID_Y, s > 0);
-                }
-                tc::commit(mby);
+            for (int s = 0; s < C::NKP / C::KMMA; ++s) {
+                const uint64_t da = tc::sdesc(tc::smem_u32(sV) + (uint32_t)(s * 4096), 16 * 128, 128);
+                const uint64_t db = tc::sdesc(sKm + (uint32_t)(s * 2 * LBO_KM), LBO_KM, 128);
+                if constexpr (BF) tc::mma_f16(tbuf, da, db, ID_Y, s > 0);
+                else tc::mma_tf32(tbuf, da, db, ID_Y, s > 0);
             }
-            ok = tc::mbar_wait(mby, phy & 1, WAIT_LIMIT);
-            ++phy;
-            tc::fence_after();
+            tc::commit(mb + 2);
         }
-        ok = __syncthreads_and(ok);
-        // ---- scatter: h(p - off(tap)) += Y[p][tap] into this warp's partial ------
+        if (ok) pp.pend |= 4u;
+        {
+            const bool got = ok && tc::mbar_wait(mb + 2, (pp.ph >> 2) & 1u, WAIT_LIMIT);
+            if (got) {
+                pp.ph ^= 4u;
+                pp.pend &= ~4u;
+            }
+            ok = tc::wg_and(bar, got);
+        }
+        tc::fence_after();
+        // ---- this pixel's Y row, then the buffer takes group gi + 2's z ----------
         // (tcgen05.ld is warp-collective: every lane loads; lanes outside the
         // image have v = 0, hence Y = 0, and add zeros at in-range indices)
-        // Two lanes of a warp, (g, mp) and (g', mp'), update the same h element
-        // through taps (a, b) and (a', b') when g - a = g' - a' and
-        // 4 mp - b = 4 mp' - b', i.e. only for taps with different kernel rows,
-        // or with the same row and b - b' = +-4.  Taps of one row with b in
-        // [0, 4) or in [4, 8) never collide, so a warp barrier (which also
-        // orders the lanes' shared-memory accesses) before each such run keeps
-        // every read-modify-write of h whole.
+        constexpr int NY8 = (KS * KS + 7) / 8;
+        uint32_t yr[NY8][8];
+        if (ok) {
+#pragma unroll
+            for (int c = 0; c < NY8; ++c) tc::tmem_ld8_nowait(tbuf + lane_base + 8 * c, yr[c]);
+            tc::tmem_wait_ld();
+        }
+        tc::fence_before();
+        tc::wg_sync(bar);
+        tc::fence_after();
+        if (ok && gi + 2 < NG) {
+            if (wt == 0) issue_z(gi + 2);
+            pp.pend |= 1u << zb;
+        }
+        // ---- scatter h(p - off(tap)) += Y[p][tap], one kernel row per phase ------
         if (ok) {
             const int base = (16 * nb + g + 2 * R) * C::HPITCH + (r + 4 * mp + 2 * R);
 #pragma unroll
-            for (int c8 = 0; c8 < KS * KS; c8 += 8) {
-                float y[8];
-                tc::tmem_ld8(tyv + lane_base + c8, y);
+            for (int ka = 0; ka < KS; ++ka) {
+                if (ka > 0) tc::wg_sync(bar);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int t = c8 + q;
-                    if (t < KS * KS) {
-                        if ((t % KS) % 4 == 0) __syncwarp();
-                        myh[base - (t / KS) * C::HPITCH - (t % KS)] += y[q];
-                    }
+                for (int b = 0; b < KS; ++b) {
+                    if (b % 4 == 0) __syncwarp();
+                    const int t = ka * KS + b;
+                    sH[base - ka * C::HPITCH - b] += __uint_as_float(yr[t / 8][t % 8]);
                 }
             }
             __syncwarp();
         }
-        tc::fence_before();
-        __syncthreads();
-        tc::fence_after();
-    }
-    if (!ok) {
-        // give the MMAs in flight a bounded chance to finish before TMEM is freed
-        tc::mbar_wait(mbz + 0, phz & 1u, WAIT_LIMIT);
-        tc::mbar_wait(mbz + 1, (phz >> 1) & 1u, WAIT_LIMIT);
     }
 
-    // ---- epilogue: g = fold(sum of the warps' h), u_t = prox(u_{t-1} - g) ------
+    // ---- epilogue: g = fold(h), u_t = prox(u_{t-1} - g) ---------------------------
+    tc::wg_sync(bar);
     if (ok) {
         const float lam = __ldg(a.lam);
-        const int wy0 = tile_split(ty, TH, H, a.tiles_y, R), wy1 = tile_split(ty + 1, TH, H, a.tiles_y, R);
-        const int wx0 = tile_split(tx, TW, W, a.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, a.tiles_x, R);
-        const float* fimg = a.f;
-        float* uout = a.u_out;
-        for (int idx = tid; idx < TH * TW; idx += 128) {
+        const int wy0 = tile_split(a.ty, TH, H, a.tiles_y, R), wy1 = tile_split(a.ty + 1, TH, H, a.tiles_y, R);
+        const int wx0 = tile_split(a.tx, TW, W, a.tiles_x, R), wx1 = tile_split(a.tx + 1, TW, W, a.tiles_x, R);
+        for (int idx = wt; idx < TH * TW; idx += 128) {
             const int qy = y0 + idx / TW, qx = x0 + idx % TW;
             if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
             int sy[2], sx[2];
@@ -292,84 +441,95 @@ __device__ __forceinline__ void tc_tile(const TileJob& a, unsigned char* smem, i
                 else if (qx >= W - R) sx[nsx++] = 2 * W - 1 - qx;
             }
             float gsum = 0.0f;
-            for (int p = 0; p < nsy; ++p) {
-                for (int q = 0; q < nsx; ++q) {
-                    const int hi = sy[p] - (y0 - 2 * R), hj = sx[q] - (x0 - 2 * R);
-                    float hs = 0.0f;
-#pragma unroll
-                    for (int wq = 0; wq < 4; ++wq) hs += sH[wq * (C::HROWS * C::HPITCH) + hi * C::HPITCH + hj];
-                    gsum += hs;
-                }
-            }
+            for (int p = 0; p < nsy; ++p)
+                for (int q = 0; q < nsx; ++q)
+                    gsum += sH[(sy[p] - (y0 - 2 * R)) * C::HPITCH + sx[q] - (x0 - 2 * R)];
             const float up = __ldcg(uin + (size_t)qy * a.pitch + qx);
-            const float fv = __ldg(fimg + (size_t)qy * a.pitch + qx);
-            uout[(size_t)qy * a.pitch + qx] = stage_out(up, gsum, fv, lam, a.dterm, a.proj_c);
+            const float fv = __ldg(a.f + (size_t)qy * a.pitch + qx);
+            a.u_out[(size_t)qy * a.pitch + qx] = stage_out(up, gsum, fv, lam, a.dterm, a.proj_c);
         }
-    } else if (tid == 0) {
-        atomicExch(err, 4);
+    }
+    return ok;
+}
+
+// The persistent CTA: a contiguous run of the source's tiles, split into runs
+// of one parameter set; per run the CTA stages the set's operands and its
+// warpgroups take the run's tiles in turn.  err receives TNRD_ERR_TIMEOUT (4)
+// when a warpgroup gave up waiting for its MMAs (it then skips its remaining
+// tiles, waits a bounded time for the MMAs still in flight, and the CTA frees
+// its TMEM as usual).
+template <int KS, int NK, int NB, bool BF, class Src>
+__device__ __forceinline__ void tc_run(const Src& src, unsigned char* smem, int* err)
+{
+    using C = TcCfg<KS, NK, NB, BF>;
+    constexpr long long WAIT_LIMIT = 1ll << 31;
+    const int tid = threadIdx.x, wg = tid >> 7, wt = tid & 127;
+    const int bar = 1 + wg;   // named barrier of this warpgroup (0 is the CTA's)
+    unsigned char* wgs = smem + C::OFF_WG + (size_t)wg * C::WG_BYTES;
+    uint64_t* mb = reinterpret_cast<uint64_t*>(wgs + C::WG_MISC);   // z buffers 0, 1; Y
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_TMEM);
+    if (wt == 0) {
+        tc::mbar_init(mb + 0, 1);
+        tc::mbar_init(mb + 1, 1);
+        tc::mbar_init(mb + 2, 1);
+    }
+    if (tid < 32) tc::tmem_alloc(tslot, C::TMEM_COLS);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t tmem = tbase + (uint32_t)(128 * wg);
+
+    TcPipe pp;
+    int ok = 1;
+    const int nt = src.ntiles();
+    const int per = (nt + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int c0 = min(nt, (int)blockIdx.x * per), c1 = min(nt, c0 + per);
+#pragma unroll 1
+    for (int s0 = c0; s0 < c1;) {
+        const int set = src.set_of(s0);
+        const int s1 = src.seg_end(s0, c1);
+        const TcSet ps = src.params(set);
+        __syncthreads();   // every warpgroup's MMAs of the previous set have completed
+        tc_stage_consts<KS, NK, NB, BF>(ps, smem, tid);
+        tc::fence_async_smem();
+        __syncthreads();
+        const RbfConst rc = *ps.rc;
+#pragma unroll 1
+        for (int s = s0 + wg; s < s1 && ok; s += C::NWG)
+            ok = tc_tile<KS, NK, NB, BF>(src.tile(s), rc, smem, wgs, tmem, mb, pp, wt, bar);
+        s0 = s1;
+    }
+    if (!ok) {
+        // give the MMAs in flight a bounded chance to finish before TMEM is freed
+        for (int b = 0; b < 3; ++b)
+            if (pp.pend & (1u << b)) tc::mbar_wait(mb + b, (pp.ph >> b) & 1u, WAIT_LIMIT);
+        if (wt == 0) atomicExch(err, 4);
     }
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+    if (tid < 32) tc::tmem_dealloc(tbase, C::TMEM_COLS);
 }
 
-// Per-call stage: grid (tiles_x * tiles_y, N), one tile per CTA.
+// Per-call stage: a persistent grid of at most one CTA per SM over the N
+// images' tiles.
 template <int KS, int NK, int NB, bool BF>
-__global__ void __launch_bounds__(128, 2) tc_stage_fwd(const __grid_constant__ StageArgs a)
+__global__ void __launch_bounds__(TcCfg<KS, NK, NB, BF>::NTHREADS, 1)
+tc_stage_fwd(const __grid_constant__ StageArgs a, int n_img)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int n = blockIdx.y;
-    TileJob j;
-    j.u_in = a.u_in + (size_t)n * a.img_stride;
-    j.u_out = a.u_out + (size_t)n * a.img_stride;
-    j.f = a.f + (size_t)n * a.img_stride;
-    j.H = a.H;
-    j.W = a.W;
-    j.pitch = a.pitch;
-    j.tiles_x = a.tiles_x;
-    j.tiles_y = a.tiles_y;
-    j.ty = blockIdx.x / a.tiles_x;
-    j.tx = blockIdx.x - j.ty * a.tiles_x;
-    j.k = a.k;
-    j.w = a.w;
-    j.lam = a.lam;
-    j.nrbf = a.nrbf;
-    j.dterm = a.dterm;
-    j.proj_c = a.proj_c;
-    j.rc = &a.rc;
-    tc_tile<KS, NK, NB, BF>(j, smem, &g_tc_error);
+    const TcCallSrc src{&a, n_img};
+    tc_run<KS, NK, NB, BF>(src, smem, &g_tc_error);
 }
 
-// Stage t of a batched plan: grid (all images' tiles), the tile table of the
-// plan gives each CTA its (image, tile); each image's parameter set, buffers
-// and data term come from the plan.  Stage t writes u when (T-1-t) is even
-// and the plan's inter-stage image otherwise, so the last stage lands in u.
+// Stage t of a batched plan over every image's tiles.
 template <int KS, int NK, int NB, bool BF>
-__global__ void __launch_bounds__(128, 2) tc_batch_fwd(const __grid_constant__ BatchArgs a, int t)
+__global__ void __launch_bounds__(TcCfg<KS, NK, NB, BF>::NTHREADS, 1)
+tc_batch_fwd(const __grid_constant__ BatchArgs a, int t)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int2 ti = a.tile_img[blockIdx.x];
-    const BatchImg& im = a.imgs[ti.x];
-    const BatchSet& ps = a.sets[im.set];
-    TileJob j;
-    j.u_out = ((a.T - 1 - t) % 2 == 0) ? im.u : im.tmp;
-    j.u_in = (t == 0) ? im.f : (((a.T - t) % 2 == 0) ? im.u : im.tmp);
-    j.f = im.f;
-    j.H = im.H;
-    j.W = im.W;
-    j.pitch = im.pitch;
-    j.tiles_x = im.tiles_x;
-    j.tiles_y = im.tiles_y;
-    j.ty = ti.y / im.tiles_x;
-    j.tx = ti.y - j.ty * im.tiles_x;
-    j.k = ps.k + (size_t)t * NK * KS * KS;
-    j.w = ps.w + (size_t)t * NK * a.nrbf;
-    j.lam = ps.lam + t;
-    j.nrbf = a.nrbf;
-    j.dterm = ps.dterm;
-    j.proj_c = ps.proj_c;
-    j.rc = &ps.rc;
-    tc_tile<KS, NK, NB, BF>(j, smem, a.status);
+    const TcBatchSrc<KS, NK> src{&a, t};
+    tc_run<KS, NK, NB, BF>(src, smem, a.status);
 }
 
 }  // namespace tnrd

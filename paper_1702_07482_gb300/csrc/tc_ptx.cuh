@@ -122,6 +122,31 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// As tmem_ld8 without the wait: several loads can be in flight before one
+// tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Barrier of the 128 threads of one warpgroup (named barrier `id`, 1..15).
+__device__ __forceinline__ void wg_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+// As wg_sync, returning 1 iff v != 0 in every thread of the warpgroup.
+__device__ __forceinline__ int wg_and(int id, int v)
+{
+    int r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+                 "bar.red.and.pred q, %2, 128, p;\n\tselp.s32 %0, 1, 0, q;\n\t}\n"
+                 : "=r"(r) : "r"(v), "r"(id) : "memory");
+    return r;
+}
+
 // fp32 -> tf32 (round to nearest, ties away), returned as fp32 bits.
 __device__ __forceinline__ float to_tf32(float x)
 {
