@@ -488,7 +488,8 @@ class Batched(Workload):
             self.tensor_dtype = algo
         sched = "batch_persistent_fwd" if self.launches == 1 else "batch_stage_fwd"
         self.kernel = (f"{sched}<7,48,{self.plan.tile_height}>" if algo == "fused" else
-                       f"tc_batch_fwd<7,48,2,{algo}> (tcgen05 {algo.upper()} filter bank and "
+                       f"tc_batch_fwd<7,48,{(self.plan.tile_height + 2 * (KS // 2)) // 16},{algo}> "
+                       f"(tcgen05 {algo.upper()} filter bank and "
                        f"adjoint, FP32 phi/prox; one launch per stage)")
         self.h2d = self.d2h = int(self.f_host.numel() * 4)
         self.config = {"workload": f"TRDMD batched forward, {n} images with sides U[{lo},{hi}] "

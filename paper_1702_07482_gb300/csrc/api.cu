@@ -108,6 +108,7 @@ tnrd::RbfConst make_rbf(const tnrd_params* p)
     rc.c_q2 = (float)(log2e * d / (g * g));
     rc.c_p2a = (float)(log2e / (2.0 * g * g));
     rc.c_p2b = (float)(log2e * W * d / (g * g));
+    rc.c_p2b_tc = (float)(log2e * tnrd::TC_WIN * d / (g * g));
     rc.cq = (float)(d / (g * g));
     rc.half_inv_g2 = (float)(1.0 / (2.0 * g * g));
     rc.inv_g2 = (float)(1.0 / (g * g));
@@ -240,6 +241,19 @@ FusedChoice pick_fused(int ks, int nk, int N, int H, int W)
     return c;
 }
 
+// Row blocks of 16 z rows per tensor-core tile: 3 for BF16 (its smaller
+// operands leave room for three warpgroups with the taller tile), 2 for TF32
+// (three warpgroups fit only with the shorter one).  TNRD_TC_NB=2|3 overrides.
+int pick_tc_nb(tnrd_algo algo)
+{
+    int nb = (algo == TNRD_ALGO_TC_BF16) ? 3 : 2;
+    if (const char* env = std::getenv("TNRD_TC_NB")) {
+        const int v = std::atoi(env);
+        if (v == 2 || v == 3) nb = v;
+    }
+    return nb;
+}
+
 struct FwdLayout {
     size_t pingpong = 0;   // offset of the ping-pong image batch
     size_t v = 0, g = 0;   // unfused response planes and adjoint plane
@@ -353,11 +367,7 @@ tnrd_status tnrd_forward_kernel(const tnrd_params* p, int N, int H, int W, tnrd_
     } else if (algo == TNRD_ALGO_UNFUSED) {
         std::snprintf(buf, len, "unf_bank_phi + unf_adjoint + unf_prox <%d,%d>", ks, nk);
     } else if (algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16) {
-        int nb = 2;
-        if (const char* env = std::getenv("TNRD_TC_NB")) {
-            const int v = std::atoi(env);
-            if (v == 2 || v == 3) nb = v;
-        }
+        const int nb = pick_tc_nb(algo);
         std::snprintf(buf, len, "tc_stage_fwd<%d,%d,%d,%s> tiles %dx%d", ks, nk, nb,
                       algo == TNRD_ALGO_TC_BF16 ? "bf16" : "tf32", tnrd::tc_tile_h(ks, nb), 32 - 2 * R);
     } else {
@@ -399,11 +409,7 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
     const tnrd::RbfConst rc = make_rbf(p);
     const int ks = p->ksize, nk = p->nfilt;
     const FusedChoice fc = (algo == TNRD_ALGO_FUSED) ? pick_fused(ks, nk, N, H, W) : FusedChoice{};
-    int tc_nb = 2;
-    if (const char* env = std::getenv("TNRD_TC_NB")) {   // tuning override
-        const int v = std::atoi(env);
-        if (v == 2 || v == 3) tc_nb = v;
-    }
+    const int tc_nb = pick_tc_nb(algo);
 
     for (int t = 0; t < p->T; ++t) {
         const float* in;
@@ -796,6 +802,7 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
     P->imgs.assign(images, images + nimg);
     P->sets.assign(sets, sets + nsets);
     P->algo = algo;
+    P->tc_nb = pick_tc_nb(algo);
     // tensor-core plans: the stage kernel's one tile height; fused plans: the list
     const int tc_th[2] = {tnrd::tc_tile_h(ks, P->tc_nb), 0};
     const int* ths = (algo == TNRD_ALGO_FUSED) ? tnrd::fused_th_list(ks) : tc_th;

@@ -15,6 +15,12 @@ namespace tnrd {
 constexpr int RBF_WIN = 6;
 constexpr int RBF_TERMS = 2 * RBF_WIN + 1;
 constexpr int MAX_NRBF = 64;
+// The tensor-core stages sum the 2*TC_WIN+1 = 11 nearest centres: every dropped
+// centre is at least (TC_WIN + 1/2) delta = 5.5 gamma away, so the dropped
+// terms total less than 2 * exp(-15.1) * max|w| < 5.4e-7 * max|w|, three
+// orders of magnitude below the rounding of v to the adjoint GEMM's operand
+// precision (TF32: 2^-11 relative, BF16: 2^-8).
+constexpr int TC_WIN = 5;
 // w is staged in shared memory with 2*RBF_WIN zeros on each side, so that the
 // 13-term window never needs a bounds test: wp[j + 2*RBF_WIN] = w_j.
 constexpr int RBF_WPAD = 2 * RBF_WIN;
@@ -32,6 +38,7 @@ struct RbfConst {
     float c_q2;         // log2(e) delta / gamma^2
     float c_p2a;        // log2(e) / (2 gamma^2)
     float c_p2b;        // log2(e) RBF_WIN delta / gamma^2
+    float c_p2b_tc;     // log2(e) TC_WIN delta / gamma^2 (window of the tensor-core stages)
     int jmax;           // nrbf - 1 + RBF_WIN
     float E[RBF_WIN + 1];  // exp(-m^2 delta^2 / (2 gamma^2)), m = 0..RBF_WIN
 };
@@ -210,6 +217,66 @@ __device__ __forceinline__ void rbf_phi_dphi_w(float z, const float* __restrict_
     phi = win.pre * p;
     const float m1 = win.pre * fmaf(-(float)RBF_WIN, p, win.q * dp);
     dphi = -rc.inv_g2 * fmaf(win.s, phi, -rc.delta * m1);
+}
+
+// RBF weights of the tensor-core stages, laid out so that the 16 lanes of a
+// half-warp never collide on a shared-memory bank.  Filters go in rounds of 16
+// (filter f = 16 r + c, column c); filter f's padded weights wp (wp[j +
+// RBF_WPAD] = w_j, zeros elsewhere) are stored as 8-byte pairs, pair k of
+// parity p holding (wp[2k + p], wp[2k + p + 1]), at pair index
+//   ((p * NR + r) * TC_PAIRS + k) * 16 + c        (NR rounds).
+// Pair k of every filter of a round lies in bank pair c, so when the lanes of a
+// half-warp evaluate 16 different filters of one round (lane j filter
+// 16 r + ((j + s) mod 16) at step s), their loads hit 16 distinct bank pairs
+// whatever their window rows: no conflicts.  The window's 11 weights start at
+// wp index row = j0 + RBF_WPAD - TC_WIN, i.e. at pair row >> 1 of parity
+// row & 1, and are read as 6 pairs.
+constexpr int TC_PAIRS = (MAX_NRBF + 2 * RBF_WPAD) / 2;
+
+// phi(z) over the TC_WIN window of the filter in column `col` of the round
+// whose parity-0 plane starts at tab_r (tab + r * TC_PAIRS * 16); the parity-1
+// plane is plane_stride pairs further.  Horner in q as rbf_phi_w.
+__device__ __forceinline__ float rbf_phi_col(float z, const float2* __restrict__ tab_r,
+                                             int plane_stride, int col, const RbfConst& rc)
+{
+    const float zc = fminf(fmaxf(z, rc.zlo), rc.zhi);
+    const float t = fmaf(zc, rc.inv_delta, rc.t_off);
+    const float tm = t + 12582912.0f;
+    const float jf = tm - 12582912.0f;
+    const int row = __float_as_int(tm) - 0x4B400000 + (RBF_WPAD - TC_WIN);   // wp index of w_{j0-TC_WIN}
+    const float s = zc - fmaf(jf, rc.delta, rc.mu0);
+    const float q = ex2_approx(s * rc.c_q2);
+    const float pre = ex2_approx(-s * fmaf(s, rc.c_p2a, rc.c_p2b_tc));
+    const float2* wr = tab_r + (row & 1) * plane_stride + (row >> 1) * 16 + col;
+    float c[2 * TC_WIN + 2];
+#pragma unroll
+    for (int k = 0; k <= TC_WIN; ++k) {
+        const float2 v = wr[16 * k];
+        c[2 * k] = v.x;
+        c[2 * k + 1] = v.y;
+    }
+    float p = c[2 * TC_WIN] * rc.E[TC_WIN];
+#pragma unroll
+    for (int n = 2 * TC_WIN - 1; n >= 0; --n) {
+        const int m = n - TC_WIN;
+        p = fmaf(p, q, c[n] * rc.E[m < 0 ? -m : m]);
+    }
+    return pre * p;
+}
+
+// x[s] <- x[(s + k) mod 16] for a per-thread k in [0, 16): four stages of
+// selects (no register indexing, no memory).
+__device__ __forceinline__ void rotl16(float (&x)[16], int k)
+{
+#pragma unroll
+    for (int b = 8; b >= 1; b >>= 1) {
+        const bool on = (k & b) != 0;
+        float y[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) y[s] = on ? x[(s + b) & 15] : x[s];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) x[s] = y[s];
+    }
 }
 
 // phi(z) from a coefficient table.

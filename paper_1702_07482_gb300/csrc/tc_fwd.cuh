@@ -202,10 +202,16 @@ __device__ __forceinline__ void tc_stage_consts(const TcSet& ps, unsigned char* 
                 tc::pack_bf16x2(v0, v1);
         }
     }
-    float* sW = reinterpret_cast<float*>(smem + C::OFF_W);
-    for (int e = tid; e < NK * C::WPADN; e += NTH) {
-        const int i = e / C::WPADN, jj = e - i * C::WPADN - RBF_WPAD;
-        sW[e] = (jj >= 0 && jj < ps.nrbf) ? __ldg(ps.w + i * ps.nrbf + jj) : 0.0f;
+    // RBF weights in the bank-conflict-free pair table of rbf_phi_col:
+    // [parity][round][pair][column], filters beyond NK all zeros
+    float2* sW2 = reinterpret_cast<float2*>(smem + C::OFF_W);
+    for (int e = tid; e < 2 * C::NR * TC_PAIRS * 16; e += NTH) {
+        const int c = e & 15, k = (e >> 4) % TC_PAIRS, pr = (e >> 4) / TC_PAIRS;
+        const int r = pr % C::NR, p = pr / C::NR, f = 16 * r + c;
+        const int j0 = 2 * k + p - RBF_WPAD;   // weight index of the pair's first element
+        const bool ok0 = f < NK && j0 >= 0 && j0 < ps.nrbf, ok1 = f < NK && j0 + 1 >= 0 && j0 + 1 < ps.nrbf;
+        sW2[e] = make_float2(ok0 ? __ldg(ps.w + f * ps.nrbf + j0) : 0.0f,
+                             ok1 ? __ldg(ps.w + f * ps.nrbf + j0 + 1) : 0.0f);
     }
 }
 
@@ -245,11 +251,25 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
         float* raw = sV;
         const int ry = y0 - 2 * R, rx = x0 - 2 * R;
         const bool inner = ry >= 0 && ry + C::UROWS <= H && rx >= 0 && rx + C::RAWC <= W;
-        for (int idx = wt; idx < C::UROWS * C::RAWC; idx += 128) {
-            const int i = idx / C::RAWC, j = idx - i * C::RAWC;
-            const int yy = inner ? ry + i : sym_idx(ry + i, H);
-            const int xx = inner ? rx + j : sym_idx(rx + j, W);
-            raw[i * C::RAWP + j] = __ldcg(uin + (size_t)yy * a.pitch + xx);
+        constexpr int NRAW = C::UROWS * C::RAWC;
+        // four loads in flight per thread before their stores
+#pragma unroll 1
+        for (int i0 = 0; i0 < NRAW; i0 += 4 * 128) {
+            float v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int idx = i0 + k * 128 + wt;
+                const int i = idx / C::RAWC, j = idx - i * C::RAWC;
+                const int yy = inner ? ry + i : sym_idx(ry + i, H);
+                const int xx = inner ? rx + j : sym_idx(rx + j, W);
+                v[k] = idx < NRAW ? __ldcg(uin + (size_t)yy * a.pitch + xx) : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int idx = i0 + k * 128 + wt;
+                const int i = idx / C::RAWC, j = idx - i * C::RAWC;
+                if (idx < NRAW) raw[i * C::RAWP + j] = v[k];
+            }
         }
         for (int e = wt; e < C::HROWS * C::HPITCH; e += 128) sH[e] = 0.0f;
         tc::wg_sync(bar);
@@ -323,41 +343,58 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
         const int yy = y0 - R + 16 * nb + g, xx = x0 - R + r + 4 * mp;
         const bool inside = (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
         if (ok) {
+            // Rounds of 16 filters; lane j of each half-warp takes them in the
+            // rotated order 16 r + ((j + s) mod 16), s = 0..15, so that the
+            // half-warp's weight loads fall in 16 distinct bank pairs.  Filters
+            // beyond NK have zero weights (v = 0).
+            const int jr = (wt & 15);
+            const float2* sW2 = reinterpret_cast<const float2*>(smem + C::OFF_W);
 #pragma unroll 1
-            for (int c8 = 0; c8 < NK; c8 += 8) {
-                float z[8], v[8];
-                tc::tmem_ld8(tbuf + lane_base + c8, z);
-                // branch-free: the 8 evaluations are independent and interleave
-                // (z is finite everywhere: u is mirror-loaded), then masked
+            for (int rr = 0; rr < C::NR; ++rr) {
+                float x[16];
+                {
+                    uint32_t zr0[8], zr1[8];
+                    tc::tmem_ld8_nowait(tbuf + lane_base + 16 * rr, zr0);
+                    tc::tmem_ld8_nowait(tbuf + lane_base + 16 * rr + 8, zr1);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int i = c8 + q;
-                    const float ph = rbf_phi_w(z[q], sW + (i < NK ? i : 0) * C::WPADN, rc);
-                    v[q] = (i < NK && inside) ? ph : 0.0f;
+                    for (int k = 0; k < 8; ++k) {
+                        x[k] = __uint_as_float(zr0[k]);
+                        x[k + 8] = __uint_as_float(zr1[k]);
+                    }
                 }
+                rotl16(x, jr);                       // x[s] = z of filter 16 rr + ((jr + s) & 15)
+                const float2* tab_r = sW2 + rr * TC_PAIRS * 16;
+#pragma unroll
+                for (int s = 0; s < 16; ++s)
+                    x[s] = rbf_phi_col(x[s], tab_r, C::NR * TC_PAIRS * 16, (jr + s) & 15, rc);
+                rotl16(x, (16 - jr) & 15);           // back to filter order: x[m] = v of 16 rr + m
+#pragma unroll
+                for (int m = 0; m < 16; ++m) x[m] = inside ? x[m] : 0.0f;
                 if constexpr (!BF) {
                     // A layout [filter/4][g][mp][filter%4]: core matrices of 8 positions x 4 filters
-                    float4* d0 = reinterpret_cast<float4*>(sV + ((c8 / 4) * 16 + g) * 32 + mp * 4);
-                    *d0 = make_float4(tc::to_tf32(v[0]), tc::to_tf32(v[1]), tc::to_tf32(v[2]), tc::to_tf32(v[3]));
-                    if (c8 + 4 < C::NKP) {
-                        float4* d1 = reinterpret_cast<float4*>(sV + ((c8 / 4 + 1) * 16 + g) * 32 + mp * 4);
-                        *d1 = make_float4(tc::to_tf32(v[4]), tc::to_tf32(v[5]), tc::to_tf32(v[6]), tc::to_tf32(v[7]));
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const int f0 = 16 * rr + 4 * q4;
+                        if (f0 < C::NKP)
+                            *reinterpret_cast<float4*>(sV + ((f0 / 4) * 16 + g) * 32 + mp * 4) =
+                                make_float4(tc::to_tf32(x[4 * q4]), tc::to_tf32(x[4 * q4 + 1]),
+                                            tc::to_tf32(x[4 * q4 + 2]), tc::to_tf32(x[4 * q4 + 3]));
                     }
                 } else {
                     // A layout [filter/8][g][mp][filter%8]: core matrices of 8 positions x 8 filters
-                    uint4* d0 = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(sV) +
-                                                         ((c8 / 8) * 16 + g) * 128 + mp * 16);
-                    *d0 = make_uint4(tc::pack_bf16x2(v[0], v[1]), tc::pack_bf16x2(v[2], v[3]),
-                                     tc::pack_bf16x2(v[4], v[5]), tc::pack_bf16x2(v[6], v[7]));
-                }
-            }
-            if constexpr (BF) {
-                // K padding of the adjoint GEMM (filters NK .. NKP-1): zeros, not
-                // whatever the raw u rows left there (a NaN pattern times 0 is NaN)
 #pragma unroll
-                for (int c8 = (NK + 7) / 8 * 8; c8 < C::NKP; c8 += 8)
-                    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(sV) +
-                                              ((c8 / 8) * 16 + g) * 128 + mp * 16) = make_uint4(0, 0, 0, 0);
+                    for (int q8 = 0; q8 < 2; ++q8) {
+                        const int f0 = 16 * rr + 8 * q8;
+                        if (f0 < C::NKP)
+                            *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(sV) +
+                                                      ((f0 / 8) * 16 + g) * 128 + mp * 16) =
+                                make_uint4(tc::pack_bf16x2(x[8 * q8], x[8 * q8 + 1]),
+                                           tc::pack_bf16x2(x[8 * q8 + 2], x[8 * q8 + 3]),
+                                           tc::pack_bf16x2(x[8 * q8 + 4], x[8 * q8 + 5]),
+                                           tc::pack_bf16x2(x[8 * q8 + 6], x[8 * q8 + 7]));
+                    }
+                }
             }
         }
         tc::fence_async_smem();

@@ -153,3 +153,16 @@ def test_full_size_2048_T8_sampled_windows(algo):
         ref = oracle.forward(f[0, y0:y1, x0:x1], p)[-1][y - y0, x - x0]
         errs.append(abs(got[y, x] - ref))
     assert max(errs) <= TOL[algo][0], errs
+
+
+@pytest.mark.parametrize("algo", ["tf32", "bf16"])
+@pytest.mark.parametrize("nb", ["2", "3"])
+def test_both_tile_heights_within_bound(algo, nb, monkeypatch):
+    """Tiles of 2 and 3 row blocks (TNRD_TC_NB; the defaults are 2 for TF32, 3 for
+    BF16) on a ragged multi-tile image: every stage within the stated bound."""
+    monkeypatch.setenv("TNRD_TC_NB", nb)
+    p, f = case(101, 83, 7, 48, 2, N=1, cfg=197)
+    got = _run(p, f, algo)
+    ref = oracle.forward(f[0], p)[:, None]
+    err = np.abs(got - ref).max(axis=(1, 2, 3))
+    assert np.all(err <= TOL[algo][0]), err
