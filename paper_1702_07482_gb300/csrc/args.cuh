@@ -367,7 +367,7 @@ struct TcCfg {
     static constexpr size_t OFF_KM = al(OFF_BZ + (size_t)ESZ * KS * NPAD * KMMA);
     static constexpr size_t OFF_W = al(OFF_KM + (size_t)ESZ * NT * NKP);
     static constexpr int NR = (NK + 15) / 16;    // rounds of 16 filters (RBF weight table)
-    static constexpr size_t OFF_WG = al(OFF_W + 8ull * 2 * NR * TC_PAIRS * 16);
+    static constexpr size_t OFF_WG = al(OFF_W + 8ull * NR * TC_ROWS * 16);
     // per warpgroup: u operands, V (the raw u rows before the first group), h, barriers
     static constexpr size_t WG_U = 0;
     static constexpr size_t WG_V = al(WG_U + 4ull * UROWS * UROWB);

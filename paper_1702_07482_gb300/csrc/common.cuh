@@ -221,23 +221,21 @@ __device__ __forceinline__ void rbf_phi_dphi_w(float z, const float* __restrict_
 
 // RBF weights of the tensor-core stages, laid out so that the 16 lanes of a
 // half-warp never collide on a shared-memory bank.  Filters go in rounds of 16
-// (filter f = 16 r + c, column c); filter f's padded weights wp (wp[j +
-// RBF_WPAD] = w_j, zeros elsewhere) are stored as 8-byte pairs, pair k of
-// parity p holding (wp[2k + p], wp[2k + p + 1]), at pair index
-//   ((p * NR + r) * TC_PAIRS + k) * 16 + c        (NR rounds).
-// Pair k of every filter of a round lies in bank pair c, so when the lanes of a
-// half-warp evaluate 16 different filters of one round (lane j filter
-// 16 r + ((j + s) mod 16) at step s), their loads hit 16 distinct bank pairs
-// whatever their window rows: no conflicts.  The window's 11 weights start at
-// wp index row = j0 + RBF_WPAD - TC_WIN, i.e. at pair row >> 1 of parity
-// row & 1, and are read as 6 pairs.
-constexpr int TC_PAIRS = (MAX_NRBF + 2 * RBF_WPAD) / 2;
+// (filter f = 16 r + c, column c); with wp filter f's padded weights (wp[j +
+// RBF_WPAD] = w_j, zeros elsewhere), entry (r, row, c) holds the 8-byte pair
+// (wp[row], wp[row + 1]) at pair index (r * TC_ROWS + row) * 16 + c.  Every
+// entry of column c lies in bank pair c, so when the lanes of a half-warp
+// evaluate 16 different filters of one round at once, their loads hit 16
+// distinct bank pairs whatever their window rows: no conflicts.  The window's
+// 11 weights start at wp index row = j0 + RBF_WPAD - TC_WIN and are the pairs
+// of rows row, row + 2, .., row + 10.
+constexpr int TC_ROWS = MAX_NRBF + 2 * RBF_WPAD;
 
 // phi(z) over the TC_WIN window of the filter in column `col` of the round
-// whose parity-0 plane starts at tab_r (tab + r * TC_PAIRS * 16); the parity-1
-// plane is plane_stride pairs further.  Horner in q as rbf_phi_w.
-__device__ __forceinline__ float rbf_phi_col(float z, const float2* __restrict__ tab_r,
-                                             int plane_stride, int col, const RbfConst& rc)
+// whose entries start at tab_r (tab + r * TC_ROWS * 16).  Horner in q as
+// rbf_phi_w.
+__device__ __forceinline__ float rbf_phi_col(float z, const float2* __restrict__ tab_r, int col,
+                                             const RbfConst& rc)
 {
     const float zc = fminf(fmaxf(z, rc.zlo), rc.zhi);
     const float t = fmaf(zc, rc.inv_delta, rc.t_off);
@@ -247,11 +245,11 @@ __device__ __forceinline__ float rbf_phi_col(float z, const float2* __restrict__
     const float s = zc - fmaf(jf, rc.delta, rc.mu0);
     const float q = ex2_approx(s * rc.c_q2);
     const float pre = ex2_approx(-s * fmaf(s, rc.c_p2a, rc.c_p2b_tc));
-    const float2* wr = tab_r + (row & 1) * plane_stride + (row >> 1) * 16 + col;
+    const float2* wr = tab_r + row * 16 + col;
     float c[2 * TC_WIN + 2];
 #pragma unroll
     for (int k = 0; k <= TC_WIN; ++k) {
-        const float2 v = wr[16 * k];
+        const float2 v = wr[32 * k];
         c[2 * k] = v.x;
         c[2 * k + 1] = v.y;
     }
@@ -262,6 +260,21 @@ __device__ __forceinline__ float rbf_phi_col(float z, const float2* __restrict__
         p = fmaf(p, q, c[n] * rc.E[m < 0 ? -m : m]);
     }
     return pre * p;
+}
+
+// Within each aligned group of four: x[4q + t] <- x[4q + ((t + k) mod 4)]
+// for a per-thread k in [0, 4) (two stages of selects).
+__device__ __forceinline__ void rotl4x4(float (&x)[16], int k)
+{
+#pragma unroll
+    for (int b = 2; b >= 1; b >>= 1) {
+        const bool on = (k & b) != 0;
+        float y[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) y[s] = on ? x[(s & ~3) | ((s + b) & 3)] : x[s];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) x[s] = y[s];
+    }
 }
 
 // x[s] <- x[(s + k) mod 16] for a per-thread k in [0, 16): four stages of

@@ -203,12 +203,11 @@ __device__ __forceinline__ void tc_stage_consts(const TcSet& ps, unsigned char* 
         }
     }
     // RBF weights in the bank-conflict-free pair table of rbf_phi_col:
-    // [parity][round][pair][column], filters beyond NK all zeros
+    // [round][row][column], filters beyond NK all zeros
     float2* sW2 = reinterpret_cast<float2*>(smem + C::OFF_W);
-    for (int e = tid; e < 2 * C::NR * TC_PAIRS * 16; e += NTH) {
-        const int c = e & 15, k = (e >> 4) % TC_PAIRS, pr = (e >> 4) / TC_PAIRS;
-        const int r = pr % C::NR, p = pr / C::NR, f = 16 * r + c;
-        const int j0 = 2 * k + p - RBF_WPAD;   // weight index of the pair's first element
+    for (int e = tid; e < C::NR * TC_ROWS * 16; e += NTH) {
+        const int c = e & 15, row = (e >> 4) % TC_ROWS, r = (e >> 4) / TC_ROWS, f = 16 * r + c;
+        const int j0 = row - RBF_WPAD;   // weight index of the pair's first element
         const bool ok0 = f < NK && j0 >= 0 && j0 < ps.nrbf, ok1 = f < NK && j0 + 1 >= 0 && j0 + 1 < ps.nrbf;
         sW2[e] = make_float2(ok0 ? __ldg(ps.w + f * ps.nrbf + j0) : 0.0f,
                              ok1 ? __ldg(ps.w + f * ps.nrbf + j0 + 1) : 0.0f);
@@ -243,6 +242,8 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
     const int H = a.H, W = a.W;
     const int y0 = tile_origin(a.ty, TH, H), x0 = tile_origin(a.tx, TW, W);
     const bool border = (a.ty == 0) || (a.ty == a.tiles_y - 1) || (a.tx == 0) || (a.tx == a.tiles_x - 1);
+    // the whole z-region inside the image: no v needs masking
+    const bool zin = y0 - R >= 0 && y0 - R + C::ZR <= H && x0 - R >= 0 && x0 - R + 32 <= W;
     const float* uin = a.u_in;
 
     // ---- stage u: raw rows (in the V area), then the residue operands --------
@@ -343,11 +344,12 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
         const int yy = y0 - R + 16 * nb + g, xx = x0 - R + r + 4 * mp;
         const bool inside = (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
         if (ok) {
-            // Rounds of 16 filters; lane j of each half-warp takes them in the
-            // rotated order 16 r + ((j + s) mod 16), s = 0..15, so that the
-            // half-warp's weight loads fall in 16 distinct bank pairs.  Filters
-            // beyond NK have zero weights (v = 0).
-            const int jr = (wt & 15);
+            // Rounds of 16 filters.  Lane j = 4a + b of each half-warp takes
+            // the round's filter 4((q + a) mod 4) + ((t + b) mod 4) at step
+            // s = 4q + t: at every step the half-warp's 16 lanes evaluate 16
+            // different filters, so their weight loads fall in 16 distinct
+            // bank pairs.  Filters beyond NK have zero weights (v = 0).
+            const int ja = (wt >> 2) & 3, jb = wt & 3;
             const float2* sW2 = reinterpret_cast<const float2*>(smem + C::OFF_W);
 #pragma unroll 1
             for (int rr = 0; rr < C::NR; ++rr) {
@@ -363,25 +365,34 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
                         x[k + 8] = __uint_as_float(zr1[k]);
                     }
                 }
-                rotl16(x, jr);                       // x[s] = z of filter 16 rr + ((jr + s) & 15)
-                const float2* tab_r = sW2 + rr * TC_PAIRS * 16;
+                rotl16(x, 4 * ja);                   // groups of four rotated by a
+                rotl4x4(x, jb);                      // within the group by b
+                const float2* tab_r = sW2 + rr * TC_ROWS * 16;
 #pragma unroll
-                for (int s = 0; s < 16; ++s)
-                    x[s] = rbf_phi_col(x[s], tab_r, C::NR * TC_PAIRS * 16, (jr + s) & 15, rc);
-                rotl16(x, (16 - jr) & 15);           // back to filter order: x[m] = v of 16 rr + m
+                for (int s = 0; s < 16; ++s) {
+                    const int col = (4 * ((s >> 2) + ja) & 12) | (((s & 3) + jb) & 3);
+                    x[s] = rbf_phi_col(x[s], tab_r, col, rc);
+                }
+                rotl4x4(x, (4 - jb) & 3);            // x[4q + t] = v of filter 4((q + a) mod 4) + t
+                if (!zin) {
 #pragma unroll
-                for (int m = 0; m < 16; ++m) x[m] = inside ? x[m] : 0.0f;
+                    for (int m = 0; m < 16; ++m) x[m] = inside ? x[m] : 0.0f;
+                }
                 if constexpr (!BF) {
-                    // A layout [filter/4][g][mp][filter%4]: core matrices of 8 positions x 4 filters
+                    // A layout [filter/4][g][mp][filter%4]: core matrices of 8 positions x 4
+                    // filters; group q of this lane is the round's filter group (q + a) mod 4
+                    // (16-byte stores at lane-dependent groups: 8 lanes of a quarter-warp
+                    // differ in mp, so they still hit 8 distinct 16-byte bank groups)
 #pragma unroll
                     for (int q4 = 0; q4 < 4; ++q4) {
-                        const int f0 = 16 * rr + 4 * q4;
-                        if (f0 < C::NKP)
+                        const int f0 = 16 * rr + 4 * ((q4 + ja) & 3);
+                        if (16 * rr + 16 <= C::NKP || f0 < C::NKP)
                             *reinterpret_cast<float4*>(sV + ((f0 / 4) * 16 + g) * 32 + mp * 4) =
                                 make_float4(tc::to_tf32(x[4 * q4]), tc::to_tf32(x[4 * q4 + 1]),
                                             tc::to_tf32(x[4 * q4 + 2]), tc::to_tf32(x[4 * q4 + 3]));
                     }
                 } else {
+                    rotl16(x, (16 - 4 * ja) & 15);   // filter order: x[m] = v of filter 16 rr + m
                     // A layout [filter/8][g][mp][filter%8]: core matrices of 8 positions x 8 filters
 #pragma unroll
                     for (int q8 = 0; q8 < 2; ++q8) {
