@@ -199,8 +199,10 @@ int device_sm_count()
 // (fused_stage_fwd) is the default.  When it cannot give every SM two CTAs
 // (a single small image), the column-pair kernel on two-CTA clusters
 // (fused_pair2_fwd, half of the filters per CTA) spreads the same work over
-// more CTAs.  Either way the row tiling minimises the estimated duration
-// (pick_rows).  TNRD_FUSED_KERNEL=lane|pair|pair2, TNRD_FUSED_TH and
+// more CTAs; when even that leaves SMs without a CTA (a small image), clusters
+// of four or eight CTAs per tile (fused_pairc_fwd) are weighed against it.
+// Either way the row tiling minimises the estimated duration (pick_rows).
+// TNRD_FUSED_KERNEL=lane|pair|pair2|pair4|pair8, TNRD_FUSED_TH and
 // TNRD_FUSED_ROWS override the choice (tuning and measurement).
 struct FusedChoice {
     int pair = 0;     // 0: one column per lane; 1: column pairs
@@ -211,15 +213,32 @@ struct FusedChoice {
     int tw = 0;
 };
 
+// Estimated duration, in filter-walk steps, of a column-pair launch on
+// clusters of `split` CTAs with row tiling rc: the longer of the longest
+// CTA's sequential walks (fused_cost counts steps, each warp walks fpw
+// filters) and the whole launch's warp-steps over the SMs at ten warps' worth
+// of issue each (plus a per-CTA overhead of 8 steps per warp: staging, the
+// cluster barriers and the epilogue).
+double pair_split_cost(int nk, int split, const RowChoice& rc, int R, int N, int H, int W, int tw,
+                       int nsm)
+{
+    const int nw = tnrd::pair_nwarp(nk / split), fpw = nk / split / nw;
+    const long long tiles = (long long)N * tnrd::row_tiles(H, rc.th, rc.te) * ((W + tw - 1) / tw);
+    const double walk = fused_cost(N, H, W, rc.th, rc.te, tw, R, split, 2 * nsm) * fpw;
+    const double issue = (double)tiles * split * nw * (fpw * (rc.th + 4.0 * R) + 8.0) / (10.0 * nsm);
+    return std::max(walk, issue);
+}
+
 FusedChoice pick_fused(int ks, int nk, int N, int H, int W)
 {
-    (void)nk;
     FusedChoice c;
-    int force = -1;   // -1 auto, 0 lane, 1 pair, 2 pair2
+    int force = -1;   // -1 auto, 0 lane, 1 pair, 2 pair2, 4 pair4, 8 pair8
     if (const char* env = std::getenv("TNRD_FUSED_KERNEL")) {
         if (!std::strcmp(env, "lane")) force = 0;
         else if (!std::strcmp(env, "pair")) force = 1;
         else if (!std::strcmp(env, "pair2")) force = 2;
+        else if (!std::strcmp(env, "pair4") && nk % 4 == 0) force = 4;
+        else if (!std::strcmp(env, "pair8") && nk % 8 == 0) force = 8;
     }
     const int R = ks / 2;
     const int nsm = device_sm_count();
@@ -230,11 +249,30 @@ FusedChoice pick_fused(int ks, int nk, int N, int H, int W)
     c.kth = rc.kth;
     const long long lane_ctas = (long long)N * tnrd::row_tiles(H, c.th, c.te) * ((W + c.tw - 1) / c.tw);
     if (force == 0 || (force < 0 && lane_ctas >= 2LL * nsm)) return c;
-    const int ns = (force == 1) ? 1 : 2;
     c.pair = 1;
-    c.nsplit = ns;
     c.tw = 64 - 2 * R;
-    rc = pick_rows(tnrd::pair_th_list(ks), R, N, H, W, c.tw, ns, nsm);
+    if (force == 4 || force == 8) {
+        c.nsplit = force;
+        rc = pick_rows(tnrd::pair_cluster_th_list(ks), R, N, H, W, c.tw, force, nsm);
+    } else {
+        c.nsplit = (force == 1) ? 1 : 2;
+        rc = pick_rows(tnrd::pair_th_list(ks), R, N, H, W, c.tw, c.nsplit, nsm);
+        const long long ctas2 = 2LL * N * tnrd::row_tiles(H, rc.th, rc.te) * ((W + c.tw - 1) / c.tw);
+        if (force < 0 && ctas2 < nsm) {
+            double best = pair_split_cost(nk, 2, rc, R, N, H, W, c.tw, nsm);
+            for (int split : {4, 8}) {
+                if (nk % split) continue;
+                const RowChoice rs = pick_rows(tnrd::pair_cluster_th_list(ks), R, N, H, W, c.tw, split, nsm);
+                if (rs.kth == 0) continue;
+                const double cost = pair_split_cost(nk, split, rs, R, N, H, W, c.tw, nsm);
+                if (cost < 0.85 * best) {
+                    best = cost;
+                    rc = rs;
+                    c.nsplit = split;
+                }
+            }
+        }
+    }
     c.th = rc.th;
     c.te = rc.te;
     c.kth = rc.kth;
@@ -362,7 +400,8 @@ tnrd_status tnrd_forward_kernel(const tnrd_params* p, int N, int H, int W, tnrd_
         char rows[40] = "";
         if (c.te > 0) std::snprintf(rows, sizeof rows, " (border rows %d)", c.te);
         std::snprintf(buf, len, "%s<%d,%d,%d> tiles %dx%d%s, %s staging",
-                      !c.pair ? "fused_stage_fwd" : c.nsplit == 2 ? "fused_pair2_fwd" : "fused_pair_fwd",
+                      !c.pair ? "fused_stage_fwd" : c.nsplit == 2 ? "fused_pair2_fwd"
+                      : c.nsplit == 4 ? "fused_pair4_fwd" : c.nsplit == 8 ? "fused_pair8_fwd" : "fused_pair_fwd",
                       ks, nk, c.kth, c.th, c.tw, rows, staging);
     } else if (algo == TNRD_ALGO_UNFUSED) {
         std::snprintf(buf, len, "unf_bank_phi + unf_adjoint + unf_prox <%d,%d>", ks, nk);
@@ -447,7 +486,8 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.dterm = p->data_term;
             a.proj_c = p->proj_c;
             a.rc = rc;
-            e = fc.pair ? tnrd::launch_pair_fwd(ks, nk, fc.kth, fc.nsplit, a, N, stream)
+            e = (fc.pair && fc.nsplit > 2) ? tnrd::launch_pair_cluster_fwd(ks, nk, fc.kth, fc.nsplit, a, N, stream)
+              : fc.pair ? tnrd::launch_pair_fwd(ks, nk, fc.kth, fc.nsplit, a, N, stream)
                         : tnrd::launch_fused_fwd(ks, nk, fc.kth, a, N, stream);
         } else if (algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16) {
             tnrd::StageArgs a{};

@@ -50,6 +50,14 @@ struct TileJob {
     int tx_extra = 0;                    // test hook: extra bytes the copy's mbarrier expects
 };
 
+// Warps of a column-pair CTA holding nk_cta filters (each warp walks
+// nk_cta / warps of them).
+__host__ __device__ constexpr int pair_nwarp(int nk_cta)
+{
+    return nk_cta % 8 == 0 ? 8 : nk_cta % 6 == 0 ? 6 : nk_cta % 4 == 0 ? 4 : nk_cta % 3 == 0 ? 3
+         : nk_cta % 2 == 0 ? 2 : 1;
+}
+
 template <int KS, int NK, int TH>
 struct FusedCfg {
     static constexpr int R = KS / 2;

@@ -19,17 +19,15 @@
 // filters; the epilogue of each CTA covers half of the tile and adds the
 // other CTA's h buffers through distributed shared memory.  This doubles the
 // CTAs of small images (one 512 x 512 image is ~150 tiles for 152 SMs).
+// NSPLIT = 4 or 8 (fused_pairc_fwd) spreads one tile over a cluster of four or
+// eight CTAs in the same way, for images too small to give every SM a CTA
+// otherwise; each CTA's epilogue adds all ranks' h buffers in rank order.
 #pragma once
 #include <cooperative_groups.h>
 #include "args.cuh"
 #include "fused_fwd.cuh"   // shfl_rel
 
 namespace tnrd {
-
-__host__ __device__ constexpr int pair_nwarp(int nk_cta)
-{
-    return nk_cta % 8 == 0 ? 8 : nk_cta % 6 == 0 ? 6 : nk_cta % 4 == 0 ? 4 : nk_cta % 2 == 0 ? 2 : 1;
-}
 
 template <int KS, int NK, int TH, int NSPLIT>
 struct PairCfg {
@@ -293,6 +291,61 @@ __device__ __forceinline__ void pair_tile_epilogue(const TileJob& j, const float
     }
 }
 
+// As pair_tile_epilogue for a cluster of NS CTAs: g sums the h buffers of
+// every rank (hb[r], rank r's buffers) in rank order, so a pixel's bits do not
+// depend on which CTA of the cluster finishes it.
+template <int KS, int NK, int TH, int NS>
+__device__ __forceinline__ void pair_tile_epilogue_cluster(const TileJob& j, const float* smem,
+                                                           const float* const (&hb)[NS],
+                                                           int first, int step, int xoff)
+{
+    using C = PairCfg<KS, NK, TH, NS>;
+    constexpr int R = C::R;
+    constexpr int TW = C::TW;
+    const float* sU = smem;
+    const int ty = j.ty, tx = j.tx;
+    const int H = j.H, W = j.W;
+    const RowTile rt = row_tile(ty, j.tiles_y, H, min(j.th, TH), min(j.te, TH), R);
+    const int y0 = rt.y0, x0 = tile_origin(tx, TW, W);
+    const bool ext = (ty == 0) || (ty == j.tiles_y - 1);
+    const bool border = ext || (tx == 0) || (tx == j.tiles_x - 1);
+    const float lam = __ldg(j.lam);
+    const int wy0 = rt.wy0, wy1 = rt.wy1;
+    const int wx0 = tile_split(tx, TW, W, j.tiles_x, R), wx1 = tile_split(tx + 1, TW, W, j.tiles_x, R);
+    for (int idx = first; idx < rt.h * TW; idx += step) {
+        const int qy = y0 + idx / TW, qx = x0 + idx % TW;
+        if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
+        int sy[2], sx[2];
+        int nsy = 1, nsx = 1;
+        sy[0] = qy;
+        sx[0] = qx;
+        if (border) {
+            if (qy < R) sy[nsy++] = -1 - qy;
+            else if (qy >= H - R) sy[nsy++] = 2 * H - 1 - qy;
+            if (qx < R) sx[nsx++] = -1 - qx;
+            else if (qx >= W - R) sx[nsx++] = 2 * W - 1 - qx;
+        }
+        float g = 0.0f;
+        for (int p = 0; p < nsy; ++p) {
+            for (int q = 0; q < nsx; ++q) {
+                const int o = (sy[p] - (y0 - R)) * 64 + sx[q] - (x0 - R);
+                float hs = 0.0f;
+#pragma unroll
+                for (int r = 0; r < NS; ++r) {
+                    float hr = 0.0f;
+#pragma unroll
+                    for (int wq = 0; wq < C::NWARP; ++wq) hr += hb[r][wq * C::PW_FL + o];
+                    hs += hr;
+                }
+                g += hs;
+            }
+        }
+        const float up = sU[(qy - y0 + 3 * R) * C::UP + (qx - x0 + 2 * R) + xoff];
+        const float fv = __ldg(j.f + (size_t)qy * j.pitch + qx);
+        j.u_out[(size_t)qy * j.pitch + qx] = stage_out(up, g, fv, lam, j.dterm, j.proj_c);
+    }
+}
+
 __device__ __forceinline__ TileJob pair_job(const StageArgs& a, int tile, int th_kernel)
 {
     const int n = blockIdx.y;
@@ -359,6 +412,35 @@ fused_pair2_fwd(const __grid_constant__ StageArgs a)
         pair_tile_epilogue<KS, NK, TH, 2>(j, smem, remote, rank * C::NTHREADS + threadIdx.x,
                                           2 * C::NTHREADS, xoff);
     cl.sync();   // keep this CTA's shared memory alive until the other has read it
+}
+
+// A cluster of NS (4 or 8) CTAs per tile; grid (NS * tiles_x * tiles_y, N).
+template <int KS, int NK, int TH, int NS>
+__global__ void __cluster_dims__(NS, 1, 1) __launch_bounds__(PairCfg<KS, NK, TH, NS>::NTHREADS, 2)
+fused_pairc_fwd(const __grid_constant__ StageArgs a)
+{
+    namespace cg = cooperative_groups;
+    using C = PairCfg<KS, NK, TH, NS>;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ int s_xoff;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const TileJob j = pair_job(a, blockIdx.x / NS, TH);
+    const int xoff = pair_tile_walk<KS, NK, TH, NS>(j, smem, rank);
+    if (threadIdx.x == 0) s_xoff = xoff;
+    cl.sync();   // every CTA's h buffers complete and visible in the cluster
+    const float* hb[NS];
+    bool all = xoff >= 0;
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+        hb[r] = cl.map_shared_rank(smem, r) + ((C::U_FL + 3) & ~3);
+        all = all && *cl.map_shared_rank(&s_xoff, r) >= 0;
+    }
+    // every CTA passes both cluster barriers; the epilogue runs only if all tiles staged
+    if (all)
+        pair_tile_epilogue_cluster<KS, NK, TH, NS>(j, smem, hb, rank * C::NTHREADS + threadIdx.x,
+                                                   NS * C::NTHREADS, xoff);
+    cl.sync();   // keep this CTA's shared memory alive until the others have read it
 }
 
 }  // namespace tnrd

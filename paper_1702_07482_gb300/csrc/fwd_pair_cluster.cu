@@ -1,0 +1,56 @@
+// Instantiations and launcher of the column-pair fused FP32 forward stage on
+// clusters of four or eight CTAs per tile (small images; see fused_pair.cuh).
+#include "launch.h"
+#include "fused_pair.cuh"
+
+namespace tnrd {
+
+namespace {
+
+template <int KS, int NK, int TH, int NS>
+cudaError_t launch_ns(const StageArgs& a, int N, cudaStream_t s)
+{
+    if constexpr (NK % NS != 0) {
+        return cudaErrorInvalidValue;
+    } else {
+        using C = PairCfg<KS, NK, TH, NS>;
+        if (a.th > TH || a.te > a.th || a.te < 0) return cudaErrorInvalidValue;   // buffers hold TH rows
+        cudaError_t e = cudaFuncSetAttribute(fused_pairc_fwd<KS, NK, TH, NS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        StageArgs b = a;
+        stage_args_tma(b, N, C::UP, C::UH);
+        fused_pairc_fwd<KS, NK, TH, NS>
+            <<<dim3(NS * a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(b);
+        return cudaGetLastError();
+    }
+}
+
+// Tile heights compiled for the cluster splits (the small tiles small images need).
+#define TNRD_PAIRC_CASES(X) \
+    X(3, 4, 17) X(3, 4, 23) X(5, 24, 17) X(5, 24, 22) X(7, 48, 16) X(7, 48, 23)
+
+}  // namespace
+
+const int* pair_cluster_th_list(int ks)
+{
+    static const int l3[] = {17, 23, 0}, l5[] = {17, 22, 0}, l7[] = {16, 23, 0};
+    static const int none[] = {0};
+    return ks == 3 ? l3 : ks == 5 ? l5 : ks == 7 ? l7 : none;
+}
+
+cudaError_t launch_pair_cluster_fwd(int ks, int nk, int th, int nsplit, const StageArgs& a, int N,
+                                    cudaStream_t s)
+{
+#define X(K, NN, T)                                                          \
+    if (ks == K && nk == NN && th == T) {                                    \
+        if (nsplit == 4) return launch_ns<K, NN, T, 4>(a, N, s);             \
+        if (nsplit == 8) return launch_ns<K, NN, T, 8>(a, N, s);             \
+    }
+    TNRD_PAIRC_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace tnrd

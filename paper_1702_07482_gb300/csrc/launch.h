@@ -65,6 +65,11 @@ cudaError_t launch_tc_batch(int ks, int nk, int nb, bool bf16, const BatchArgs& 
 const int* pair_th_list(int ks);
 cudaError_t launch_pair_fwd(int ks, int nk, int th, int nsplit, const StageArgs& a, int N,
                             cudaStream_t s);
+// The same kernel on clusters of nsplit = 4 or 8 CTAs per tile (small images),
+// compiled for the tile heights of pair_cluster_th_list.
+const int* pair_cluster_th_list(int ks);
+cudaError_t launch_pair_cluster_fwd(int ks, int nk, int th, int nsplit, const StageArgs& a, int N,
+                                    cudaStream_t s);
 
 // Persistent batched forward.
 cudaError_t launch_batch_fwd(int ks, int nk, int th, const BatchArgs& a, int grid, cudaStream_t s);

@@ -38,10 +38,11 @@ def _images(region, N, H, P):
     return region.view(N, H, P)
 
 
-@pytest.mark.parametrize("algo", ["fused", "lane", "pair", "pair2", "unfused", "tf32", "bf16"])
+@pytest.mark.parametrize("algo", ["fused", "lane", "pair", "pair2", "pair4", "pair8", "unfused", "tf32",
+                                  "bf16"])
 @pytest.mark.parametrize("keep", [0, 1])
 def test_forward_writes_only_its_output(algo, keep, monkeypatch):
-    if algo in ("lane", "pair", "pair2"):
+    if algo in ("lane", "pair", "pair2", "pair4", "pair8"):
         monkeypatch.setenv("TNRD_FUSED_KERNEL", algo)
         algo = "fused"
     from paper_1702_07482_gb300 import binding as B

@@ -111,13 +111,13 @@ def test_512_full_size_sampled_windows():
         assert abs(got[y, x] - ref) <= TOL_U_FP32, (y, x, got[y, x], ref)
 
 
-@pytest.mark.parametrize("variant", ["lane", "pair", "pair2"])
+@pytest.mark.parametrize("variant", ["lane", "pair", "pair2", "pair4", "pair8"])
 @pytest.mark.parametrize("H,W,ks,nk,T,N", [(97, 65, 7, 48, 2, 1), (33, 130, 7, 48, 2, 2),
                                            (64, 35, 3, 4, 3, 2), (50, 100, 5, 24, 2, 1),
                                            (7, 7, 7, 48, 1, 1)])
 def test_each_fused_kernel_matches_oracle(variant, H, W, ks, nk, T, N, monkeypatch):
     """Every fused forward kernel (one column per lane, column pairs, column
-    pairs on two-CTA clusters) on ragged shapes: several tiles, a last tile of
+    pairs on clusters of two, four and eight CTAs) on ragged shapes: several tiles, a last tile of
     fewer than R rows or columns, images narrower than one tile."""
     monkeypatch.setenv("TNRD_FUSED_KERNEL", variant)
     p, f = case(H, W, ks, nk, T, L=1, N=N, cfg=131 + H + W)
@@ -128,12 +128,12 @@ def test_each_fused_kernel_matches_oracle(variant, H, W, ks, nk, T, N, monkeypat
 
 
 def test_fused_kernels_agree_and_repeat():
-    """The three fused kernels add the filters' adjoint terms in different
+    """The fused kernels add the filters' adjoint terms in different
     orders: they agree to rounding, and each is bitwise repeatable."""
     import os
     p, f = case(90, 120, 7, 48, 2, cfg=140)
     outs = {}
-    for v in ("lane", "pair", "pair2"):
+    for v in ("lane", "pair", "pair2", "pair4", "pair8"):
         os.environ["TNRD_FUSED_KERNEL"] = v
         try:
             a = _gpu_forward(p, f, keep=False)
@@ -143,4 +143,5 @@ def test_fused_kernels_agree_and_repeat():
         np.testing.assert_array_equal(a, b)
         outs[v] = a
     assert np.abs(outs["lane"] - outs["pair"]).max() <= TOL_U_FP32
-    assert np.abs(outs["lane"] - outs["pair2"]).max() <= TOL_U_FP32
+    for v in ("pair2", "pair4", "pair8"):
+        assert np.abs(outs["lane"] - outs[v]).max() <= TOL_U_FP32

@@ -55,7 +55,7 @@ SIZES = [(99, 70, 1), (100, 129, 1), (150, 61, 1), (241, 90, 1), (77, 50, 3)]
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("kernel", ["lane", "pair", "pair2"])
+@pytest.mark.parametrize("kernel", ["lane", "pair", "pair2", "pair8"])
 @pytest.mark.parametrize("H,W,N", SIZES)
 def test_row_tilings_give_the_same_bits(kernel, H, W, N):
     p, f = case(H, W, 7, 48, 2, L=1, N=N, cfg=501 + H + W)
@@ -112,7 +112,7 @@ def test_tiling_choice_host_only(N, H, W, ks, nk):
     old = {k: os.environ.pop(k, None) for k in ENV}
     try:
         name = B.tnrd_forward_kernel(prm, N, H, W, B.ALGO["fused"])
-        m = re.match(r"(fused_stage_fwd|fused_pair2_fwd|fused_pair_fwd)<(\d+),(\d+),(\d+)> "
+        m = re.match(r"(fused_stage_fwd|fused_pair[248]_fwd|fused_pair_fwd)<(\d+),(\d+),(\d+)> "
                      r"tiles (\d+)x(\d+)(?: \(border rows (\d+)\))?, (tma|gather) staging$", name)
         assert m, name
         kth, th, tw = int(m.group(4)), int(m.group(5)), int(m.group(6))

@@ -51,7 +51,7 @@ def _run(p, f, kernel, tma, keep=True):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("kernel", ["lane", "pair", "pair2"])
+@pytest.mark.parametrize("kernel", ["lane", "pair", "pair2", "pair4", "pair8"])
 @pytest.mark.parametrize("H,W,ks,nk,T,N", SIZES)
 def test_tma_staging_matches_gather_bit_for_bit(kernel, H, W, ks, nk, T, N):
     from paper_1702_07482_gb300 import binding as B
