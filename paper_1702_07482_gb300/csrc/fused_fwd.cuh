@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(FusedCfg<KS, NK, TH>::NTHREADS, FusedCfg<KS, N
 fused_stage_fwd(const __grid_constant__ StageArgs a)
 {
     extern __shared__ __align__(128) float smem[];
+    tc::pdl_launch_dependents();   // the next stage may launch; it waits before touching u
     const int n = blockIdx.y;
     TileJob j;
     j.u_in = a.u_in + (size_t)n * a.img_stride;

@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(PairCfg<KS, NK, TH, 1>::NTHREADS, 2)
 fused_pair_fwd(const __grid_constant__ StageArgs a)
 {
     extern __shared__ __align__(128) float smem[];
+    tc::pdl_launch_dependents();   // the next stage may launch; it waits before touching u
     const TileJob j = pair_job(a, blockIdx.x, TH);
     const int xoff = pair_tile_walk<KS, NK, TH, 1>(j, smem, 0);
     if (xoff < 0) return;
@@ -400,6 +401,7 @@ fused_pair2_fwd(const __grid_constant__ StageArgs a)
     using C = PairCfg<KS, NK, TH, 2>;
     extern __shared__ __align__(128) float smem[];
     __shared__ int s_xoff;
+    tc::pdl_launch_dependents();   // the next stage may launch; it waits before touching u
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const TileJob j = pair_job(a, blockIdx.x >> 1, TH);
@@ -423,6 +425,7 @@ fused_pairc_fwd(const __grid_constant__ StageArgs a)
     using C = PairCfg<KS, NK, TH, NS>;
     extern __shared__ __align__(128) float smem[];
     __shared__ int s_xoff;
+    tc::pdl_launch_dependents();   // the next stage may launch; it waits before touching u
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const TileJob j = pair_job(a, blockIdx.x / NS, TH);

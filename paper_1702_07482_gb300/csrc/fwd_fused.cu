@@ -18,8 +18,7 @@ cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
     StageArgs b = a;
     stage_args_tma(b, N, C::UP, C::UH);
     dim3 grid(a.tiles_x * a.tiles_y, N);
-    fused_stage_fwd<KS, NK, TH><<<grid, C::NTHREADS, smem, s>>>(b);
-    return cudaGetLastError();
+    return launch_pdl(fused_stage_fwd<KS, NK, TH>, grid, dim3(C::NTHREADS), smem, s, b);
 }
 
 template <int KS, int NK, int TH>

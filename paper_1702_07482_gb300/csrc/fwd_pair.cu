@@ -19,8 +19,9 @@ cudaError_t launch_one(const StageArgs& a, int N, int nsplit, cudaStream_t s)
         if (e != cudaSuccess) return e;
         StageArgs b = a;
         stage_args_tma(b, N, C::UP, C::UH);
-        fused_pair2_fwd<KS, NK, TH>
-            <<<dim3(2 * a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(b);
+        e = launch_pdl(fused_pair2_fwd<KS, NK, TH>, dim3(2 * a.tiles_x * a.tiles_y, N),
+                       dim3(C::NTHREADS), C::SMEM_BYTES, s, b);
+        if (e != cudaSuccess) return e;
     } else {
         using C = PairCfg<KS, NK, TH, 1>;
         cudaError_t e = cudaFuncSetAttribute(fused_pair_fwd<KS, NK, TH>,
@@ -29,7 +30,9 @@ cudaError_t launch_one(const StageArgs& a, int N, int nsplit, cudaStream_t s)
         if (e != cudaSuccess) return e;
         StageArgs b = a;
         stage_args_tma(b, N, C::UP, C::UH);
-        fused_pair_fwd<KS, NK, TH><<<dim3(a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(b);
+        e = launch_pdl(fused_pair_fwd<KS, NK, TH>, dim3(a.tiles_x * a.tiles_y, N), dim3(C::NTHREADS),
+                       C::SMEM_BYTES, s, b);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

@@ -21,9 +21,8 @@ cudaError_t launch_ns(const StageArgs& a, int N, cudaStream_t s)
         if (e != cudaSuccess) return e;
         StageArgs b = a;
         stage_args_tma(b, N, C::UP, C::UH);
-        fused_pairc_fwd<KS, NK, TH, NS>
-            <<<dim3(NS * a.tiles_x * a.tiles_y, N), C::NTHREADS, C::SMEM_BYTES, s>>>(b);
-        return cudaGetLastError();
+        return launch_pdl(fused_pairc_fwd<KS, NK, TH, NS>, dim3(NS * a.tiles_x * a.tiles_y, N),
+                          dim3(C::NTHREADS), C::SMEM_BYTES, s, b);
     }
 }
 

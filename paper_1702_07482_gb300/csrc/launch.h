@@ -10,6 +10,28 @@ namespace tnrd {
 // Records `msg` for tnrd_last_error() on this host thread and returns s.
 tnrd_status set_error(tnrd_status s, const char* msg);
 
+// Launches a forward stage kernel with programmatic stream serialization, so
+// that it may start while the previous kernel of the stream finishes (the
+// stage kernels wait with griddepcontrol.wait before touching u).
+// TNRD_PDL=0 launches plainly (comparison runs).
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Tile heights compiled for the fused forward stage, per filter size (tiles are
 // TH x (32 - 2R)); 0 terminates a list.
 inline const int* fused_th_list(int ks)

@@ -35,8 +35,7 @@ cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
                                          (int)C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = tc_grid<KS, NK, NB, BF>((long long)N * a.tiles_x * a.tiles_y);
-    tc_stage_fwd<KS, NK, NB, BF><<<grid, C::NTHREADS, C::SMEM_BYTES, s>>>(a, N);
-    return cudaGetLastError();
+    return launch_pdl(tc_stage_fwd<KS, NK, NB, BF>, dim3(grid), dim3(C::NTHREADS), C::SMEM_BYTES, s, a, N);
 }
 
 template <int KS, int NK, int NB, bool BF>

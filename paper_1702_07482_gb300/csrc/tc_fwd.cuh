@@ -542,6 +542,9 @@ __device__ __forceinline__ void tc_run(const Src& src, unsigned char* smem, int*
         tc_stage_consts<KS, NK, NB, BF>(ps, smem, tid);
         tc::fence_async_smem();
         __syncthreads();
+        // the tiles read u_{t-1} (the previous stage's output) and overwrite the
+        // buffer that stage read: wait for it (programmatic dependent launch)
+        tc::pdl_wait();
         const RbfConst rc = *ps.rc;
 #pragma unroll 1
         for (int s = s0 + wg; s < s1 && ok; s += C::NWG)
@@ -566,6 +569,7 @@ __global__ void __launch_bounds__(TcCfg<KS, NK, NB, BF>::NTHREADS, 1)
 tc_stage_fwd(const __grid_constant__ StageArgs a, int n_img)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
+    tc::pdl_launch_dependents();   // the next stage may launch; it waits before touching u
     const TcCallSrc src{&a, n_img};
     tc_run<KS, NK, NB, BF>(src, smem, &g_tc_error);
 }

@@ -147,6 +147,14 @@ __device__ __forceinline__ int wg_and(int id, int v)
     return r;
 }
 
+// Programmatic dependent launch.  launch_dependents lets the next kernel of
+// the stream (launched with programmatic stream serialization) start now; that
+// kernel calls pdl_wait before it touches memory this grid writes or reads,
+// which returns once this grid has completed and its writes are visible.
+// Without such a launch both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // fp32 -> tf32 (round to nearest, ties away), returned as fp32 bits.
 __device__ __forceinline__ float to_tf32(float x)
 {

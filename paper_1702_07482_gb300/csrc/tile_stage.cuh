@@ -55,6 +55,9 @@ __device__ __forceinline__ int stage_u_tile(const TileJob& j, float* sU, int ys,
 {
     constexpr int UP = staged_pitch(UW);
     __shared__ uint64_t bar;
+    // u_{t-1} is the previous stage's output, and u_t overwrites the buffer that
+    // stage read: wait for it to complete (programmatic dependent launch)
+    tc::pdl_wait();
     const int H = j.H, W = j.W;
     const int xs = xl & ~3;
     const int xoff = xl - xs;

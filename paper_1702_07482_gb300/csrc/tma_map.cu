@@ -60,6 +60,12 @@ unsigned long long current_context_id()
     return id;
 }
 
+bool pdl_enabled()
+{
+    const char* env = std::getenv("TNRD_PDL");   // "0": plain launches (comparison runs)
+    return !(env && std::strcmp(env, "0") == 0);
+}
+
 bool tma_staging_enabled()
 {
     const char* env = std::getenv("TNRD_TMA");   // "0": symmetric gather instead (comparison runs)
