@@ -248,7 +248,29 @@ FusedChoice pick_fused(int ks, int nk, int N, int H, int W)
     c.te = rc.te;
     c.kth = rc.kth;
     const long long lane_ctas = (long long)N * tnrd::row_tiles(H, c.th, c.te) * ((W + c.tw - 1) / c.tw);
-    if (force == 0 || (force < 0 && lane_ctas >= 2LL * nsm)) return c;
+    if (force == 0) return c;
+    if (force < 0 && lane_ctas >= 2LL * nsm) {
+        // Enough tiles for the one-column kernel.  The two-CTA column-pair kernel
+        // does the same work in fewer instructions (a pair step, two columns a
+        // lane, costs 1.9 one-column steps: fitted to 16 x 2048^2 and 32 x 180^2 at
+        // 7x7x48, where it measured 0.89x and 1.10x the one-column time) but its
+        // 64 - 2R column tiles waste more of narrow images; the estimated
+        // durations (walk steps x filters per warp x step cost) decide.
+        if (ks != 7) return c;
+        const int tw2 = 64 - 2 * R;
+        const RowChoice r2 = pick_rows(tnrd::pair_th_list(ks), R, N, H, W, tw2, 2, nsm);
+        const int fpw_lane = nk / std::min(8, nk);
+        const int fpw_pair = nk / 2 / tnrd::pair_nwarp(nk / 2);
+        const double lane_cost = rc.cost * fpw_lane, pair_cost = r2.cost * fpw_pair * 1.9;
+        if (r2.kth == 0 || !(pair_cost < 0.95 * lane_cost)) return c;
+        c.pair = 1;
+        c.nsplit = 2;
+        c.tw = tw2;
+        c.th = r2.th;
+        c.te = r2.te;
+        c.kth = r2.kth;
+        return c;
+    }
     c.pair = 1;
     c.tw = 64 - 2 * R;
     if (force == 4 || force == 8) {

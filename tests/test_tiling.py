@@ -138,3 +138,27 @@ def test_tiling_choice_host_only(N, H, W, ks, nk):
         for k, v in old.items():
             if v is not None:
                 os.environ[k] = v
+
+
+@pytest.mark.parametrize("N,H,W,want", [(16, 2048, 2048, "fused_pair2_fwd"),
+                                        (32, 180, 180, "fused_stage_fwd"),
+                                        (1, 512, 512, "fused_pair2_fwd"),
+                                        (1, 128, 128, "fused_pair4_fwd")])
+def test_kernel_choice_host_only(N, H, W, want):
+    """Host-only: the kernel tnrd_forward picks where it was measured -- the
+    two-CTA pair kernel on wide images (16 x 2048^2: 318.8 against 284.4
+    Mpixel/s), one column per lane on the 180-wide training crops (127.4 against
+    122.6), four-CTA clusters on the 128^2, 5x5x24 image."""
+    import synth
+    from paper_1702_07482_gb300 import binding as B
+    from paper_1702_07482_gb300 import ops
+    ks, nk = (5, 24) if H == 128 else (7, 48)
+    q = synth.params(1, ks, nk, seed=5)
+    prm = ops.Model.create(q.filters, q.rbf_w, q.lam, device="cpu").params()
+    old = {k: os.environ.pop(k, None) for k in ENV}
+    try:
+        assert B.tnrd_forward_kernel(prm, N, H, W, B.ALGO["fused"]).startswith(want)
+    finally:
+        for k, v in old.items():
+            if v is not None:
+                os.environ[k] = v
