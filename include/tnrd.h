@@ -273,8 +273,11 @@ TNRD_API tnrd_status tnrd_forward_noalloc(const tnrd_params* params, int N, int 
 TNRD_API tnrd_status tnrd_device_status(void);
 
 /* Test hook for the bounded waits of the fused stages' tile copies (the
- * one-column, pair and cluster-pair kernels of tnrd_forward): `cycles` is the
- * limit of each wait in SM cycles (default 2^31, about one second; >= 0), and
+ * one-column, pair and cluster-pair kernels of tnrd_forward) and of the grid
+ * barriers between the stages of a small image's one-launch cascade: `cycles`
+ * is the limit of each wait in SM cycles (default 2^31, about one second; >= 0;
+ * a barrier wait that runs out records TNRD_ERR_TIMEOUT, the CTAs still run
+ * every stage and barrier, and the output is not valid), and
  * never_complete != 0 arms each copy's mbarrier for 16 bytes more than the copy
  * brings, so that every wait runs out: each tile records TNRD_ERR_TIMEOUT (read
  * by tnrd_device_status), waits the limit once more for its copy still in

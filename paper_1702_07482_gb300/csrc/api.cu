@@ -314,13 +314,32 @@ int pick_tc_nb(tnrd_algo algo)
     return nb;
 }
 
+// Whether tnrd_forward runs all T stages in one launch (fused_pairc_cascade):
+// the fused algorithm on images small enough for the cluster splits, T >= 2,
+// and every cluster of the launch resident at once (occupancy query; false
+// without a GPU).  TNRD_CASCADE=0 turns it off (comparison runs).
+bool use_cascade(const tnrd_params* p, int N, int H, int W, tnrd_algo algo, FusedChoice* out)
+{
+    if (algo != TNRD_ALGO_FUSED || p->T < 2) return false;
+    if (const char* env = std::getenv("TNRD_CASCADE"))
+        if (!std::strcmp(env, "0")) return false;
+    const FusedChoice fc = pick_fused(p->ksize, p->nfilt, N, H, W);
+    if (!fc.pair || fc.nsplit <= 2) return false;
+    const long long clusters = (long long)N * tnrd::row_tiles(H, fc.th, fc.te) * ((W + fc.tw - 1) / fc.tw);
+    if (!tnrd::pair_cascade_fits(p->ksize, p->nfilt, fc.kth, fc.nsplit, clusters)) return false;
+    if (out) *out = fc;
+    return true;
+}
+
 struct FwdLayout {
     size_t pingpong = 0;   // offset of the ping-pong image batch
     size_t v = 0, g = 0;   // unfused response planes and adjoint plane
+    size_t counter = 0;    // grid-barrier counter of the one-launch cascade
+    bool cascade = false;
     size_t total = 0;
 };
 
-FwdLayout fwd_layout(const tnrd_params* p, int N, int H, int pitch, int keep, tnrd_algo algo)
+FwdLayout fwd_layout(const tnrd_params* p, int N, int H, int W, int pitch, int keep, tnrd_algo algo)
 {
     FwdLayout L;
     const size_t batch = sizeof(float) * (size_t)N * H * pitch;
@@ -328,6 +347,11 @@ FwdLayout fwd_layout(const tnrd_params* p, int N, int H, int pitch, int keep, tn
     if (!keep && p->T >= 2) {
         L.pingpong = off;
         off = align_up(off + batch, 256);
+    }
+    if (N > 0 && use_cascade(p, N, H, W, algo, nullptr)) {
+        L.cascade = true;
+        L.counter = off;
+        off = align_up(off + sizeof(int), 256);
     }
     if (algo == TNRD_ALGO_UNFUSED) {
         L.v = off;
@@ -401,7 +425,7 @@ size_t tnrd_workspace_size(tnrd_op op, const tnrd_params* params, int N, int H, 
 {
     if (check_params(params) != TNRD_OK) return 0;
     if (check_images(N, H, W, pitch, params->ksize) != TNRD_OK) return 0;
-    if (op == TNRD_OP_FORWARD) return fwd_layout(params, N, H, pitch, keep_stages, algo).total;
+    if (op == TNRD_OP_FORWARD) return fwd_layout(params, N, H, W, pitch, keep_stages, algo).total;
     if (op == TNRD_OP_BACKWARD) return bwd_layout(params, N, H, W, pitch).total;
     return 0;
 }
@@ -421,10 +445,16 @@ tnrd_status tnrd_forward_kernel(const tnrd_params* p, int N, int H, int W, tnrd_
         const char* staging = tnrd::tma_staging_enabled() ? "tma" : "gather";
         char rows[40] = "";
         if (c.te > 0) std::snprintf(rows, sizeof rows, " (border rows %d)", c.te);
-        std::snprintf(buf, len, "%s<%d,%d,%d> tiles %dx%d%s, %s staging",
-                      !c.pair ? "fused_stage_fwd" : c.nsplit == 2 ? "fused_pair2_fwd"
-                      : c.nsplit == 4 ? "fused_pair4_fwd" : c.nsplit == 8 ? "fused_pair8_fwd" : "fused_pair_fwd",
-                      ks, nk, c.kth, c.th, c.tw, rows, staging);
+        if (use_cascade(p, N, H, W, algo, nullptr)) {
+            std::snprintf(buf, len, "fused_pairc_cascade<%d,%d,%d,%d> tiles %dx%d%s, all %d stages in "
+                          "one launch, gather staging", ks, nk, c.kth, c.nsplit, c.th, c.tw, rows, p->T);
+        } else {
+            std::snprintf(buf, len, "%s<%d,%d,%d> tiles %dx%d%s, %s staging",
+                          !c.pair ? "fused_stage_fwd" : c.nsplit == 2 ? "fused_pair2_fwd"
+                          : c.nsplit == 4 ? "fused_pair4_fwd" : c.nsplit == 8 ? "fused_pair8_fwd"
+                          : "fused_pair_fwd",
+                          ks, nk, c.kth, c.th, c.tw, rows, staging);
+        }
     } else if (algo == TNRD_ALGO_UNFUSED) {
         std::snprintf(buf, len, "unf_bank_phi + unf_adjoint + unf_prox <%d,%d>", ks, nk);
     } else if (algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16) {
@@ -456,7 +486,7 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
     const size_t u_len = keep_stages ? batch * (size_t)(p->T + 1) : batch;
     if ((const float*)u < f + batch && f < (const float*)u + u_len)
         return fail(TNRD_ERR_INVALID_ARG, "u overlaps f");
-    const FwdLayout L = fwd_layout(p, N, H, pitch, keep_stages, algo);
+    const FwdLayout L = fwd_layout(p, N, H, W, pitch, keep_stages, algo);
     if (L.total > 0 && (!workspace || workspace_bytes < L.total))
         return fail(TNRD_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", L.total,
                     workspace ? workspace_bytes : (size_t)0);
@@ -471,6 +501,43 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
     const int ks = p->ksize, nk = p->nfilt;
     const FusedChoice fc = (algo == TNRD_ALGO_FUSED) ? pick_fused(ks, nk, N, H, W) : FusedChoice{};
     const int tc_nb = pick_tc_nb(algo);
+
+    if (L.cascade) {
+        // all stages in one launch: zero the grid-barrier counter, then launch
+        const FusedChoice& cc = fc;
+        int* counter = (int*)(ws + L.counter);
+        cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cascade counter");
+        tnrd::CascadeArgs c{};
+        c.f = f;
+        c.u = u;
+        c.pp = pp;
+        c.img_stride = (long long)plane;
+        c.batch = (long long)batch;
+        c.H = H;
+        c.W = W;
+        c.pitch = pitch;
+        c.tiles_x = (W + cc.tw - 1) / cc.tw;
+        c.tiles_y = tnrd::row_tiles(H, cc.th, cc.te);
+        c.th = cc.th;
+        c.te = cc.te;
+        c.T = p->T;
+        c.keep = keep_stages ? 1 : 0;
+        c.k = p->filters;
+        c.w = p->rbf_w;
+        c.lam = p->lambda;
+        c.nrbf = p->nrbf;
+        c.dterm = p->data_term;
+        c.proj_c = p->proj_c;
+        c.rc = rc;
+        c.counter = counter;
+        c.err = tnrd::device_status_word();
+        c.wait_limit = tnrd::stage_wait_limit();
+        if (!c.err) return fail(TNRD_ERR_CUDA, "device status word unavailable");
+        e = tnrd::launch_pair_cascade(ks, nk, cc.kth, cc.nsplit, c, N, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cascade launch");
+        return TNRD_OK;
+    }
 
     for (int t = 0; t < p->T; ++t) {
         const float* in;

@@ -28,6 +28,32 @@ struct StageArgs {
     CUtensorMap umap;      // [N][H][pitch] float32 view of u_in, box of the kernel's staged tile
 };
 
+// All T stages of a small image batch in one launch (fused_pairc_cascade):
+// stage t reads u_{t-1} (f for t = 0) and writes u_t to `stage_out(t)`; the
+// CTAs meet at a grid-wide barrier (counter, zeroed before the launch)
+// between stages.
+struct CascadeArgs {
+    const float* f;        // [N][H][pitch]  u_0
+    float* u;              // u_T, or [T+1][N][H][pitch] all stages (keep)
+    float* pp;             // ping-pong batch (keep == 0, T >= 2)
+    long long img_stride;  // floats between images
+    long long batch;       // floats of one [N][H][pitch] batch
+    int H, W, pitch;
+    int tiles_x, tiles_y;
+    int th, te;
+    int T, keep;
+    const float* k;        // [T][nfilt][ks][ks]
+    const float* w;        // [T][nfilt][nrbf]
+    const float* lam;      // [T]
+    int nrbf;
+    int dterm;
+    float proj_c;
+    RbfConst rc;
+    int* counter;          // grid barrier (one int, zero at launch)
+    int* err;              // status word: TNRD_ERR_TIMEOUT if a barrier wait ran out
+    long long wait_limit;  // SM cycles per barrier wait
+};
+
 // One tile of one stage for stage_tile(): pointers already offset to the image.
 struct TileJob {
     const float* u_in;

@@ -446,4 +446,106 @@ fused_pairc_fwd(const __grid_constant__ StageArgs a)
     cl.sync();   // keep this CTA's shared memory alive until the others have read it
 }
 
+// Grid-wide barrier of a single-launch cascade: every CTA adds one to
+// *counter and waits until it reaches `target` (all CTAs of the launch are
+// resident: the host checks that before it uses the cascade).  The wait is
+// bounded by `limit` SM cycles; false if it ran out.  Writes before the barrier
+// are visible to loads through L2 after it (fence, then release/acquire on the
+// counter).
+__device__ __forceinline__ bool cascade_barrier(int* counter, int target, long long limit)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counter, 1);
+        const long long t0 = clock64();
+        int ok = 1;
+        for (;;) {
+            int v;
+            asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+            if (v >= target) break;
+            if (clock64() - t0 > limit) {
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// All T stages on clusters of NS CTAs per tile (grid NS * tiles_x * tiles_y,
+// N), one launch: the small images whose per-stage launches are dominated by
+// start-up (cold instruction cache, tile copy, cluster barriers).  Each stage
+// is the column-pair walk and the cluster epilogue of fused_pairc_fwd with the
+// tile gathered through L2 (its u was written by other CTAs in this launch);
+// a grid barrier separates the stages.  If a barrier wait runs out, the status
+// word gets TNRD_ERR_TIMEOUT and the CTAs still run every stage and barrier
+// (each wait bounded), so that no cluster barrier is left waiting.
+template <int KS, int NK, int TH, int NS>
+__global__ void __cluster_dims__(NS, 1, 1) __launch_bounds__(PairCfg<KS, NK, TH, NS>::NTHREADS, 2)
+fused_pairc_cascade(const __grid_constant__ CascadeArgs c)
+{
+    namespace cg = cooperative_groups;
+    using C = PairCfg<KS, NK, TH, NS>;
+    extern __shared__ __align__(128) float smem[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int n = blockIdx.y;
+    const int tile = blockIdx.x / NS;
+    const int nctas = (int)(gridDim.x * gridDim.y);
+    const float* hb[NS];
+#pragma unroll
+    for (int r = 0; r < NS; ++r) hb[r] = cl.map_shared_rank(smem, r) + ((C::U_FL + 3) & ~3);
+    bool ok = true;
+#pragma unroll 1
+    for (int t = 0; t < c.T; ++t) {
+        const float* in;
+        float* out;
+        if (c.keep) {
+            in = (t == 0) ? c.f : c.u + (size_t)t * c.batch;
+            out = c.u + (size_t)(t + 1) * c.batch;
+        } else {
+            // stage t writes u when (T-1-t) is even, so the last stage lands in u
+            float* cur = ((c.T - 1 - t) % 2 == 0) ? c.u : c.pp;
+            float* prev = ((c.T - t) % 2 == 0) ? c.u : c.pp;
+            in = (t == 0) ? c.f : prev;
+            out = cur;
+        }
+        TileJob j;
+        j.u_in = in + (size_t)n * c.img_stride;
+        j.u_out = out + (size_t)n * c.img_stride;
+        j.f = c.f + (size_t)n * c.img_stride;
+        j.H = c.H;
+        j.W = c.W;
+        j.pitch = c.pitch;
+        j.tiles_x = c.tiles_x;
+        j.tiles_y = c.tiles_y;
+        j.th = c.th > 0 ? c.th : TH;
+        j.te = c.te;
+        j.ty = tile / c.tiles_x;
+        j.tx = tile - j.ty * c.tiles_x;
+        j.k = c.k + (size_t)t * NK * KS * KS;
+        j.w = c.w + (size_t)t * NK * c.nrbf;
+        j.lam = c.lam + t;
+        j.nrbf = c.nrbf;
+        j.dterm = c.dterm;
+        j.proj_c = c.proj_c;
+        j.rc = &c.rc;
+        j.umap = nullptr;   // gather through L2: the tile was written in this launch
+        j.img = n;
+        j.err = c.err;
+        const int xoff = pair_tile_walk<KS, NK, TH, NS>(j, smem, rank);
+        cl.sync();   // every CTA's h buffers complete and visible in the cluster
+        pair_tile_epilogue_cluster<KS, NK, TH, NS>(j, smem, hb, rank * C::NTHREADS + threadIdx.x,
+                                                   NS * C::NTHREADS, xoff);
+        cl.sync();   // the other CTAs have read this CTA's h buffers
+        if (t + 1 < c.T) ok = cascade_barrier(c.counter, (t + 1) * nctas, c.wait_limit) && ok;
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(c.err, 4 /* TNRD_ERR_TIMEOUT */);
+}
+
 }  // namespace tnrd

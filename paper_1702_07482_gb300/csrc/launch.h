@@ -74,8 +74,10 @@ bool tma_staging_enabled();
 bool encode_tile_map(CUtensorMap* map, const float* base, int W, int H, int N, int pitch,
                      long long img_stride, int box_w, int box_h);
 void stage_args_tma(StageArgs& a, int N, int box_w, int box_h);
-// Test hook behind tnrd_stage_wait_test (process-wide).
+// Test hook behind tnrd_stage_wait_test (process-wide), and the wait limit it
+// sets (SM cycles per bounded wait of the fused stages).
 void set_stage_wait_test(long long cycles, int never_complete);
+long long stage_wait_limit();
 // Staged tile (columns x rows) of the fused forward kernel of tile height th.
 bool fused_fwd_box(int ks, int nk, int th, int* box_w, int* box_h);
 // One stage t of a batched plan on the tensor cores (all images' tiles in one launch).
@@ -92,6 +94,11 @@ cudaError_t launch_pair_fwd(int ks, int nk, int th, int nsplit, const StageArgs&
 const int* pair_cluster_th_list(int ks);
 cudaError_t launch_pair_cluster_fwd(int ks, int nk, int th, int nsplit, const StageArgs& a, int N,
                                     cudaStream_t s);
+// All T stages of that kernel in one launch with grid barriers between them,
+// and whether all `clusters` clusters of such a launch can be resident at once.
+cudaError_t launch_pair_cascade(int ks, int nk, int th, int nsplit, const CascadeArgs& c, int N,
+                                cudaStream_t s);
+bool pair_cascade_fits(int ks, int nk, int th, int nsplit, long long clusters);
 
 // Persistent batched forward.
 cudaError_t launch_batch_fwd(int ks, int nk, int th, const BatchArgs& a, int grid, cudaStream_t s);

@@ -102,6 +102,8 @@ void set_stage_wait_test(long long cycles, int never_complete)
     g_tx_extra.store(never_complete ? 16 : 0);
 }
 
+long long stage_wait_limit() { return g_wait_limit.load(); }
+
 void stage_args_tma(StageArgs& a, int N, int box_w, int box_h)
 {
     a.wait_limit = g_wait_limit.load();

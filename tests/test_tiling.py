@@ -148,7 +148,9 @@ def test_kernel_choice_host_only(N, H, W, want):
     """Host-only: the kernel tnrd_forward picks where it was measured -- the
     two-CTA pair kernel on wide images (16 x 2048^2: 318.8 against 284.4
     Mpixel/s), one column per lane on the 180-wide training crops (127.4 against
-    122.6), four-CTA clusters on the 128^2, 5x5x24 image."""
+    122.6), four-CTA clusters of 12-row tiles on the 128^2, 5x5x24 image (259.8
+    against 212.0 with 17 rows and 223.6 on eight-CTA clusters).  (Without a GPU
+    the one-launch cascade is never chosen: its co-residency check needs one.)"""
     import synth
     from paper_1702_07482_gb300 import binding as B
     from paper_1702_07482_gb300 import ops
