@@ -486,7 +486,8 @@ class Batched(Workload):
         if algo != "fused":
             self.dtype = f"{algo} operands, f32 accumulate"
             self.tensor_dtype = algo
-        sched = "batch_persistent_fwd" if self.launches == 1 else "batch_stage_fwd"
+        sched = ("batch_persistent_fwd" if self.launches == 1 else
+                 "batch_pair2_fwd" if self.plan.tile_width == 64 - 2 * (KS // 2) else "batch_stage_fwd")
         self.kernel = (f"{sched}<7,48,{self.plan.tile_height}>" if algo == "fused" else
                        f"tc_batch_fwd<7,48,{(self.plan.tile_height + 2 * (KS // 2)) // 16},{algo}> "
                        f"(tcgen05 {algo.upper()} filter bank and "
@@ -496,8 +497,8 @@ class Batched(Workload):
                                    f"({self.px / 1e6:.1f} Mpx), L in {{1,2,4,8}} with one "
                                    f"7x7x48 63-RBF parameter set each, T={T_}, " +
                                    (f"{'one persistent launch' if self.launches == 1 else 'one launch per stage'} "
-                                    f"per step (CUDA graph), autotuned tile height and schedule "
-                                    f"(tile height {self.plan.tile_height})" if algo == "fused" else
+                                    f"per step (CUDA graph), autotuned tile geometry and schedule "
+                                    f"(tiles {self.plan.tile_height}x{self.plan.tile_width})" if algo == "fused" else
                                     f"{algo.upper()} tensor-core stage, one launch per stage over "
                                     f"all images' tiles (CUDA graph)"),
                        "images": n, "pixels": self.px, "ksize": KS, "nfilt": NK, "nrbf": 63,

@@ -158,8 +158,12 @@ TNRD_API tnrd_status tnrd_backward(const tnrd_params* params, int N, int H, int 
  * tile) items from a stage-major queue; a tile of stage t waits until the 3 x 3
  * neighbouring tiles of its image have finished stage t-1 (each wait bounded,
  * see tnrd_plan_set_wait_limit) -- or in one launch per stage over all images'
- * tiles, whichever the autotuner measured faster (tnrd_plan_launches; the
- * persistent launch without autotune).  Both schedules give the same bits.
+ * tiles, or in one launch per stage over tiles of the column-pair kernel (two
+ * z-columns per lane, 64 - 2R columns per tile, a cluster of two CTAs per
+ * tile), whichever the autotuner measured faster (tnrd_plan_launches,
+ * tnrd_plan_tile_width; the persistent launch without autotune).  The first
+ * two give the same bits; the third the bits of tnrd_forward's column-pair
+ * kernel at the same tile height.
  * With TNRD_ALGO_TC_TF32 / _BF16 it runs one
  * tensor-core launch per stage over all images' tiles (mixed precision as in
  * tnrd_forward).  The launches are recorded in a CUDA graph at plan creation
@@ -179,7 +183,7 @@ typedef struct tnrd_plan tnrd_plan;
  * (TNRD_ALGO_UNFUSED is not batched).  This is the one
  * call that allocates device memory (work lists, per-tile stage counters, the
  * inter-stage images, a status word).  With autotune != 0 it times each
- * compiled tile height (and, for TNRD_ALGO_FUSED, both schedules) on the
+ * compiled tile height (and, for TNRD_ALGO_FUSED, all three schedules) on the
  * actual images (running the forward, which writes the outputs) on `stream`
  * and keeps the fastest; otherwise a size heuristic picks the tile height.
  * Synchronises `stream`. */
@@ -204,9 +208,11 @@ TNRD_API tnrd_status tnrd_plan_status(const tnrd_plan* plan);
  * tests the error path.  Synchronous. */
 TNRD_API tnrd_status tnrd_plan_set_wait_limit(tnrd_plan* plan, long long cycles);
 
-/* Tile height the plan uses (tiles are TH x (32 - 2 * (ksize / 2)) pixels;
- * tensor-core plans: 16 NB - 2 (ksize / 2), NB = 2). */
+/* Tile height the plan uses (tensor-core plans: 16 NB - 2 (ksize / 2), NB = 2
+ * for TF32 and 3 for BF16), and its tile width: 32 - 2 (ksize / 2), or
+ * 64 - 2 (ksize / 2) for the column-pair schedule.  0 for a null plan. */
 TNRD_API int tnrd_plan_tile_height(const tnrd_plan* plan);
+TNRD_API int tnrd_plan_tile_width(const tnrd_plan* plan);
 
 /* Kernel launches per tnrd_batch_forward of the plan: 1 for the persistent
  * schedule, T for one launch per stage (tensor-core plans, and fused plans

@@ -24,7 +24,8 @@ OP_FORWARD, OP_BACKWARD = 0, 1
 # Every symbol include/tnrd.h declares (checked by the tests).
 EXPORTS = ["tnrd_workspace_size", "tnrd_forward", "tnrd_backward", "tnrd_plan_create",
            "tnrd_batch_forward", "tnrd_plan_status", "tnrd_plan_set_wait_limit",
-           "tnrd_plan_tile_height", "tnrd_plan_launches", "tnrd_plan_destroy",
+           "tnrd_plan_tile_height", "tnrd_plan_tile_width", "tnrd_plan_launches",
+           "tnrd_plan_destroy",
            "tnrd_forward_noalloc", "tnrd_forward_kernel", "tnrd_quality_workspace_size",
            "tnrd_quality", "tnrd_device_status", "tnrd_stage_wait_test", "tnrd_last_error",
            "tnrd_version"]
@@ -90,6 +91,8 @@ def load(path: str = LIB_PATH):
         L.tnrd_plan_set_wait_limit.argtypes = [P, ctypes.c_longlong]
         L.tnrd_plan_tile_height.restype = i
         L.tnrd_plan_tile_height.argtypes = [P]
+        L.tnrd_plan_tile_width.restype = i
+        L.tnrd_plan_tile_width.argtypes = [P]
         L.tnrd_plan_launches.restype = i
         L.tnrd_plan_launches.argtypes = [P]
         L.tnrd_plan_destroy.restype = None
@@ -197,6 +200,11 @@ class Plan:
     @property
     def tile_height(self) -> int:
         return load().tnrd_plan_tile_height(self.handle)
+
+    @property
+    def tile_width(self) -> int:
+        """Tile width: 32 - 2R, or 64 - 2R for the column-pair schedule."""
+        return load().tnrd_plan_tile_width(self.handle)
 
     @property
     def launches(self) -> int:

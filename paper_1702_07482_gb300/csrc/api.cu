@@ -768,7 +768,8 @@ struct tnrd_plan {
     int device = 0;
     tnrd_algo algo = TNRD_ALGO_FUSED;   // FUSED: fused stage kernel; TC_*: tensor-core stage
     int tc_nb = 2;
-    int stages = 0;   // FUSED: 0 one persistent launch, 1 one launch per stage (autotuned)
+    int stages = 0;   // FUSED: 0 one persistent launch, 1 one launch per stage, 2 one launch
+                      // per stage on column-pair tiles (autotuned)
     int ks = 0, nk = 0, nrbf = 0, T = 0;
     int th = 0;
     int nimg = 0, nsets = 0, ntiles = 0, ntiles_max = 0;
@@ -786,9 +787,11 @@ struct tnrd_plan {
 
 namespace {
 
-int batch_tiles(const tnrd_image& im, int ks, int th, int* tx, int* ty)
+// Tiles of one image in a plan: th rows x (32 - 2R) columns, or x (64 - 2R)
+// columns for the column-pair schedule.
+int batch_tiles(const tnrd_image& im, int ks, int th, int* tx, int* ty, bool pair = false)
 {
-    const int tw = 32 - 2 * (ks / 2);
+    const int tw = (pair ? 64 : 32) - 2 * (ks / 2);
     *tx = (im.W + tw - 1) / tw;
     *ty = (im.H + th - 1) / th;
     return *tx * *ty;
@@ -803,7 +806,7 @@ tnrd_status plan_build(tnrd_plan* P, int th, cudaStream_t s)
     for (int i = 0; i < P->nimg; ++i) {
         const tnrd_image& im = P->imgs[i];
         int tx, ty;
-        const int n = batch_tiles(im, P->ks, th, &tx, &ty);
+        const int n = batch_tiles(im, P->ks, th, &tx, &ty, P->stages == 2);
         bi[i].f = im.f;
         bi[i].u = im.u;
         bi[i].tmp = (float*)(P->block + P->tmp_off[i]);
@@ -823,8 +826,9 @@ tnrd_status plan_build(tnrd_plan* P, int th, cudaStream_t s)
     // tile copies (boxes of this tile height); none if any cannot be encoded
     std::vector<CUtensorMap> maps;
     int bw = 0, bh = 0;
-    if (P->algo == TNRD_ALGO_FUSED && tnrd::tma_staging_enabled() &&
-        tnrd::fused_fwd_box(P->ks, P->nk, th, &bw, &bh)) {
+    const bool box = P->stages == 2 ? tnrd::pair_fwd_box(P->ks, P->nk, th, &bw, &bh)
+                                    : tnrd::fused_fwd_box(P->ks, P->nk, th, &bw, &bh);
+    if (P->algo == TNRD_ALGO_FUSED && tnrd::tma_staging_enabled() && box) {
         maps.resize(3 * (size_t)P->nimg);
         for (int i = 0; i < P->nimg && !maps.empty(); ++i) {
             const float* src[3] = {bi[i].f, bi[i].u, bi[i].tmp};
@@ -878,7 +882,8 @@ cudaError_t plan_enqueue(const tnrd_plan* P, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(P->block + P->off_counters, 0, sizeof(int) * (2 + (size_t)P->ntiles), s);
     if (e != cudaSuccess) return e;
     if (P->algo == TNRD_ALGO_FUSED)
-        return P->stages ? tnrd::launch_batch_stages(P->ks, P->nk, P->th, P->args, s)
+        return P->stages == 2 ? tnrd::launch_batch_pairs(P->ks, P->nk, P->th, P->args, s)
+             : P->stages ? tnrd::launch_batch_stages(P->ks, P->nk, P->th, P->args, s)
                          : tnrd::launch_batch_fwd(P->ks, P->nk, P->th, P->args, P->grid, s);
     const bool bf16 = P->algo == TNRD_ALGO_TC_BF16;
     for (int t = 0; t < P->T && e == cudaSuccess; ++t)
@@ -936,13 +941,15 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
     const int tc_th[2] = {tnrd::tc_tile_h(ks, P->tc_nb), 0};
     const int* ths = (algo == TNRD_ALGO_FUSED) ? tnrd::fused_th_list(ks) : tc_th;
     int tmax = 0;
-    for (const int* p = ths; *p; ++p) {
-        int n = 0;
-        for (int i = 0; i < nimg; ++i) {
-            int tx, ty;
-            n += batch_tiles(images[i], ks, *p, &tx, &ty);
+    for (int pair = 0; pair < (algo == TNRD_ALGO_FUSED ? 2 : 1); ++pair) {
+        for (const int* p = pair ? tnrd::pair_th_list(ks) : ths; *p; ++p) {
+            int n = 0;
+            for (int i = 0; i < nimg; ++i) {
+                int tx, ty;
+                n += batch_tiles(images[i], ks, *p, &tx, &ty, pair != 0);
+            }
+            tmax = std::max(tmax, n);
         }
-        tmax = std::max(tmax, n);
     }
     P->ntiles_max = tmax;
     size_t off = 0;
@@ -990,12 +997,22 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        const int nmodes = (algo == TNRD_ALGO_FUSED) ? 2 : 1;
+        // candidates: every tile height of the one-column schedules (persistent,
+        // per stage) and of the column-pair schedule (per stage)
+        std::vector<std::pair<int, int>> cand;   // (mode, tile height)
         for (const int* p = ths; *p; ++p) {
+            cand.push_back({0, *p});
+            if (algo == TNRD_ALGO_FUSED) cand.push_back({1, *p});
+        }
+        if (algo == TNRD_ALGO_FUSED)
+            for (const int* p = tnrd::pair_th_list(ks); *p; ++p) cand.push_back({2, *p});
+        for (const auto& cd : cand) {
+            const int mode = cd.first;
+            const int* p = &cd.second;
+            P->stages = mode;
             tnrd_status st = plan_build(P, *p, stream);
             if (st != TNRD_OK) { tnrd_plan_destroy(P); return st; }
-            for (int mode = 0; mode < nmodes; ++mode) {
-                P->stages = mode;
+            {
                 float ms = 0.0f;
                 e = plan_enqueue(P, stream);   // warm-up
                 for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
@@ -1039,8 +1056,29 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
     }
     P->stages = best_stages;
     if (const char* env = std::getenv("TNRD_BATCH_SCHEDULE")) {   // tuning override
-        if (algo == TNRD_ALGO_FUSED && std::strcmp(env, "stages") == 0) P->stages = 1;
-        if (std::strcmp(env, "persistent") == 0) P->stages = 0;
+        int want = -1;
+        if (std::strcmp(env, "persistent") == 0) want = 0;
+        if (algo == TNRD_ALGO_FUSED && std::strcmp(env, "stages") == 0) want = 1;
+        if (algo == TNRD_ALGO_FUSED && std::strcmp(env, "pairs") == 0) want = 2;
+        if (want >= 0 && want != P->stages) {
+            if ((want == 2) != (P->stages == 2)) {
+                // other tile geometry: its tile height of least total work with halos
+                const int R = ks / 2;
+                double best_cost = 1e300;
+                for (const int* p = want == 2 ? tnrd::pair_th_list(ks) : ths; *p; ++p) {
+                    double cost = 0.0;
+                    for (int i = 0; i < nimg; ++i) {
+                        int tx, ty;
+                        cost += (double)batch_tiles(images[i], ks, *p, &tx, &ty, want == 2) * (*p + 4 * R);
+                    }
+                    if (cost < best_cost * 0.999) {
+                        best_cost = cost;
+                        best = *p;
+                    }
+                }
+            }
+            P->stages = want;
+        }
     }
     tnrd_status st = plan_build(P, best, stream);
     if (st != TNRD_OK) { tnrd_plan_destroy(P); return st; }
@@ -1095,6 +1133,12 @@ tnrd_status tnrd_plan_set_wait_limit(tnrd_plan* P, long long cycles)
 }
 
 int tnrd_plan_tile_height(const tnrd_plan* P) { return P ? P->th : 0; }
+
+int tnrd_plan_tile_width(const tnrd_plan* P)
+{
+    if (!P) return 0;
+    return ((P->algo == TNRD_ALGO_FUSED && P->stages == 2) ? 64 : 32) - 2 * (P->ks / 2);
+}
 
 int tnrd_plan_launches(const tnrd_plan* P)
 {

@@ -105,6 +105,10 @@ cudaError_t launch_batch_fwd(int ks, int nk, int th, const BatchArgs& a, int gri
 int batch_fwd_occupancy(int ks, int nk, int th, int nrbf);
 // The same plan one stage per launch (T launches, no waits between tiles).
 cudaError_t launch_batch_stages(int ks, int nk, int th, const BatchArgs& a, cudaStream_t s);
+// One launch per stage on the column-pair kernel's tiles (two-CTA clusters;
+// the plan's tile table in that geometry), and that kernel's staged tile.
+cudaError_t launch_batch_pairs(int ks, int nk, int th, const BatchArgs& a, cudaStream_t s);
+bool pair_fwd_box(int ks, int nk, int th, int* box_w, int* box_h);
 
 // Backward: tile height of bwd_zb / bwd_adj, one stage's prep + zb + adj +
 // filter-gradient launches, and the fixed-order partial reduce (three sets).

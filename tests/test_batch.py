@@ -172,3 +172,41 @@ def test_tensor_core_plan_matches_per_image_forward_and_oracle(algo):
     torch.cuda.synchronize()
     for (H, W, L, s), a, b in zip(SIZES, first, uts):
         assert torch.equal(a[:, :W], b[:, :W])
+
+
+def test_pair_schedule_matches_per_image_pair_kernel_and_oracle():
+    """The column-pair schedule (one launch per stage over tiles of 64 - 2R
+    columns on two-CTA clusters): each image equals tnrd_forward's column-pair
+    kernel at the same tile height bit for bit, stays within the FP32 bound of
+    the oracle, and repeats its bits on a graph replay."""
+    from paper_1702_07482_gb300 import binding as B
+    from paper_1702_07482_gb300 import ops
+    params, models, fs, fts, uts, imgs = _make(T=3, cfg=166)
+    stream = torch.cuda.current_stream().cuda_stream
+    os.environ["TNRD_BATCH_SCHEDULE"] = "pairs"
+    try:
+        plan = B.Plan(imgs, [m.params() for m in models])
+    finally:
+        del os.environ["TNRD_BATCH_SCHEDULE"]
+    assert plan.launches == 3 and plan.tile_width == 64 - 2 * 3
+    plan.forward(stream)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    first = [u.clone() for u in uts]
+    env = {"TNRD_FUSED_KERNEL": "pair2", "TNRD_FUSED_TH": str(plan.tile_height),
+           "TNRD_FUSED_ROWS": "uniform"}
+    os.environ.update(env)
+    try:
+        for (H, W, L, s), f, ft, ut in zip(SIZES, fs, fts, uts):
+            ref = ops.forward(models[s], ft.unsqueeze(0), W=W)[0]
+            torch.cuda.synchronize()
+            assert torch.equal(ut[:, :W], ref[:, :W])
+            u_or = oracle.forward(f, params[s])[-1]
+            assert np.abs(ut[:, :W].double().cpu().numpy() - u_or).max() <= TOL_U_FP32
+    finally:
+        for k in env:
+            del os.environ[k]
+    plan.forward(stream)
+    torch.cuda.synchronize()
+    for (H, W, L, s), a, b in zip(SIZES, first, uts):
+        assert torch.equal(a[:, :W], b[:, :W])

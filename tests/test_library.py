@@ -84,13 +84,20 @@ def test_empty_batch_is_a_noop(lib):
 
 def test_workspace_sizes(lib):
     p = _params(T=5)
-    one = 4 * 64 * 64
-    assert lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 64, 64, 64, 1, 0) == 0
-    assert lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 64, 64, 64, 0, 0) == 2 * one
-    unf = lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 64, 64, 64, 1, 1)
+    # 512^2 images never take the small-image one-launch cascade
+    one = 4 * 512 * 512
+    assert lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 512, 512, 512, 1, 0) == 0
+    assert lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 512, 512, 512, 0, 0) == 2 * one
+    unf = lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 512, 512, 512, 1, 1)
     assert unf == 2 * one * 48 + 2 * one
     assert lib.tnrd_workspace_size(0, ctypes.byref(_params(T=1)), 1, 64, 64, 64, 0, 0) == 0
     assert lib.tnrd_workspace_size(0, ctypes.byref(_params(ks=4)), 1, 64, 64, 64, 0, 0) == 0
+    # small images: the ping-pong batch, plus 256 bytes for the cascade's grid-barrier
+    # counter when the one-launch cascade runs (it needs a GPU to check residency)
+    small = 4 * 64 * 64
+    assert lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 64, 64, 64, 1, 0) in (0, 256)
+    assert lib.tnrd_workspace_size(0, ctypes.byref(p), 2, 64, 64, 64, 0, 0) in (2 * small,
+                                                                                  2 * small + 256)
 
 
 def test_plan_create_rejects_bad_batches_before_touching_the_device(lib):

@@ -75,9 +75,11 @@ def test_tma_staging_matches_oracle():
 
 
 @pytest.mark.gpu
-def test_batched_stage_schedule_tma_matches_gather():
-    """Per-stage batched plan: tiles of every image staged from per-image tensor
-    maps of f, u and the inter-stage buffer give the gather's bits."""
+@pytest.mark.parametrize("schedule", ["stages", "pairs"])
+def test_batched_stage_schedule_tma_matches_gather(schedule):
+    """Per-stage batched plans (one-column and column-pair tiles): tiles of every
+    image staged from per-image tensor maps of f, u and the inter-stage buffer
+    give the gather's bits."""
     import synth
     from paper_1702_07482_gb300 import binding as B
     from paper_1702_07482_gb300 import ops
@@ -95,7 +97,7 @@ def test_batched_stage_schedule_tma_matches_gather():
     stream = torch.cuda.current_stream().cuda_stream
     outs = []
     for tma in ("1", "0"):
-        os.environ["TNRD_BATCH_SCHEDULE"] = "stages"
+        os.environ["TNRD_BATCH_SCHEDULE"] = schedule
         os.environ["TNRD_TMA"] = tma
         try:
             plan = B.Plan(imgs, [m.params() for m in models])
