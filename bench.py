@@ -537,14 +537,18 @@ class Batched(Workload):
 
 
 class Train(Workload):
-    def __init__(self, dev, n=32, S=180, T_=T, cfg=4):
+    """Training step: forward cascade with its checkpoints u_0..u_T (FP32 stage
+    kernels, or the TF32 / BF16 tensor-core stage with algo), then the FP32
+    backward of every stage."""
+
+    def __init__(self, dev, n=32, S=180, T_=T, cfg=4, algo="fused"):
         super().__init__(dev)
         import numpy as np
         import torch
         import synth
         from paper_1702_07482_gb300 import binding as B
         from paper_1702_07482_gb300 import ops
-        self.T, self.n, self.S = T_, n, S
+        self.T, self.n, self.S, self.algo = T_, n, S, algo
         self.p = _p32(synth.params(T_, KS, NK, seed=synth.seed_for(cfg, 0, "params")))
         rank = int(os.environ.get("RANK", "0"))      # each rank its own crops (weak scaling)
         pairs = [synth.single_image(S, S, 1, cfg, index=rank * n + i) for i in range(n)]
@@ -566,20 +570,29 @@ class Train(Workload):
         self.launches = T_ + T_ * 5   # forward stages; prep, zb, adj, dk, reduce per stage
         self.flops = float(self.px) * T_ * (FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE)
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE
-        self.kernel = (B.tnrd_forward_kernel(self.m.params(), n, S, S, B.ALGO["fused"]) +
+        self.kernel = (B.tnrd_forward_kernel(self.m.params(), n, S, S, B.ALGO[algo]) +
                        " + bwd_prep/bwd_zb/bwd_adj/bwd_dk/bwd_reduce <7,48>")
+        if algo != "fused":
+            # the forward's filter bank and adjoint on the tensor cores, the rest FP32
+            self.tensor_dtype = algo
+            self.dtype = f"{algo} operands, f32 accumulate (forward filter bank and adjoint); f32"
+            self.conv_flops_per_px_stage = CONV_FLOPS_PER_PX_STAGE
+            self.alu_flops_per_px_stage = ALU_FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE
         self.h2d = int((self.f_host.numel() + self.c_host.numel()) * 4)
         self.d2h = int(self.g_host.numel() * 4)
+        fwd = {"fused": "", "tf32": ", TF32 tensor-core forward, FP32 backward",
+               "bf16": ", BF16 tensor-core forward, FP32 backward"}[algo]
         self.config = {"workload": f"TRDMD training step (forward + backward), {n} crops of "
                                    f"{S}x{S}, L=1, 7x7x48, 63 RBF, T={T_}, loss 1/2|u_T - clean|^2, "
-                                   "gradients of all filters, RBF weights and lambda",
+                                   "gradients of all filters, RBF weights and lambda" + fwd,
                        "batch": n, "crop": S, "ksize": KS, "nfilt": NK, "nrbf": 63, "T": T_,
                        "l2": f"working set (checkpoints + response planes, "
                              f"{self.ws_bytes / 2 ** 20:.0f} MiB workspace) larger than L2"}
 
     def step(self):
         from paper_1702_07482_gb300 import ops
-        u = ops.forward(self.m, self.f_dev, keep_stages=True, out=self.u_all, W=self.S)
+        u = ops.forward(self.m, self.f_dev, keep_stages=True, algo=self.algo, out=self.u_all,
+                        W=self.S)
         e = u[-1] - self.c_dev
         self.grads = ops.backward(self.m, self.f_dev, u, e, want_grad_u0=False, W=self.S,
                                   workspace=self.ws)
@@ -593,6 +606,37 @@ class Train(Workload):
         flat = torch.cat([gk.reshape(-1), gw.reshape(-1), gl.reshape(-1)])
         self.g_host.copy_(flat, non_blocking=True)
 
+    def accuracy(self):
+        """Gradients of crop 0 alone (the step's kernels on a batch of one)
+        against the FP64 oracle's: relative L2 error of each group (the filters
+        and the RBF weights of each stage, lambda), the largest reported."""
+        import numpy as np
+        import torch
+        import oracle
+        from paper_1702_07482_gb300 import ops
+        f0 = self.f_dev[:1]
+        u = ops.forward(self.m, f0, keep_stages=True, algo=self.algo, W=self.S)
+        _, gk, gw, gl = ops.backward(self.m, f0, u, (u[-1] - self.c_dev[:1]).contiguous(),
+                                     want_grad_u0=False, W=self.S)
+        torch.cuda.synchronize()
+        oracle.build()
+        fo = self.f[0].astype(np.float64)
+        t0 = time.perf_counter()
+        ua = oracle.forward(fo, self.p)
+        _, rk, rw, rl = oracle.backward(fo, self.p, ua, ua[-1] - self.clean[0].astype(np.float64))
+        self._full = (self.S * self.S, time.perf_counter() - t0)
+        rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+        c = lambda t: t.double().cpu().numpy()
+        gk, gw, gl = c(gk), c(gw), c(gl)
+        errs = {"lambda": rel(gl, rl)}
+        for t in range(self.T):
+            errs[f"filters_{t}"] = rel(gk[t], rk[t])
+            errs[f"rbf_w_{t}"] = rel(gw[t], rw[t])
+        worst = max(errs, key=errs.get)
+        return {"vs": "FP64 oracle", "image": f"crop 0 ({self.S}x{self.S}) as a batch of one",
+                "grad_rel_l2_max": errs[worst], "worst_group": worst,
+                "grad_rel_l2": errs}
+
     def cpu_baseline(self):
         import oracle
         oracle.build()
@@ -603,7 +647,8 @@ class Train(Workload):
             ua = oracle.forward(f0[:r].copy(), self.p)
             oracle.backward(f0[:r].copy(), self.p, ua, ua[-1] - c0[:r])
 
-        r = _oracle_baseline(band, 6, self.S, self.S, f"crop 0 ({self.S}x{self.S})")
+        r = _oracle_baseline(band, 6, self.S, self.S, f"crop 0 ({self.S}x{self.S})",
+                             getattr(self, "_full", None))
         r["sample"] = r["sample"].replace("all stages", "forward + backward of all stages")
         r["sample_1thread"] = r["sample_1thread"].replace("all stages",
                                                           "forward + backward of all stages")
@@ -617,8 +662,8 @@ class Fit(Train):
     on its own 32 crops and the gradients are summed over the ranks (one
     all-reduce per step): weak scaling."""
 
-    def __init__(self, dev):
-        super().__init__(dev)
+    def __init__(self, dev, algo="fused"):
+        super().__init__(dev, algo=algo)
         import torch
         from paper_1702_07482_gb300 import train
         self.tp = train.Params.from_model(self.p.filters, self.p.rbf_w, self.p.lam, device=dev)
@@ -637,7 +682,8 @@ class Fit(Train):
         from paper_1702_07482_gb300 import train
         from paper_1702_07482_gb300.shard import allreduce_gradients
         self.opt.zero_grad(set_to_none=False)
-        self.loss = train.loss_sum(train.cascade(self.tp, self.f_img), self.c_img)
+        self.loss = train.loss_sum(train.cascade(self.tp, self.f_img, algo=self.algo),
+                                   self.c_img)
         self.loss.backward()
         allreduce_gradients(self.tp.tensors())   # data-parallel ranks (no-op on one GPU)
         self.opt.step()
@@ -819,8 +865,14 @@ def make_workload(name, dev):
         return Batched(dev, algo="bf16")
     if name == "train":
         return Train(dev)
+    if name == "train_tf32":
+        return Train(dev, algo="tf32")
+    if name == "train_bf16":
+        return Train(dev, algo="bf16")
     if name == "fit":
         return Fit(dev)
+    if name == "fit_tf32":
+        return Fit(dev, algo="tf32")
     if name == "mixed_tf32":
         return Mixed(dev, algo="tf32")
     if name == "mixed_bf16":
@@ -882,7 +934,8 @@ def _split_roofline(wl, tc, ms, peaks, src, peak_fp32, n_sm, sm_max):
     T_min = max(conv flops / tensor peak, (phi + prox) flops / FP32 peak); the
     binding term is reported (frac = T_min / T)."""
     px_st = wl.flops / wl.flops_per_px_stage
-    conv, alu = px_st * CONV_FLOPS_PER_PX_STAGE, px_st * ALU_FLOPS_PER_PX_STAGE
+    conv = px_st * getattr(wl, "conv_flops_per_px_stage", CONV_FLOPS_PER_PX_STAGE)
+    alu = px_st * getattr(wl, "alu_flops_per_px_stage", ALU_FLOPS_PER_PX_STAGE)
     bf = float(peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1700.0)
     tpeak = bf * TENSOR_RATIO[tc]
     t = ms / 1e3
@@ -901,7 +954,9 @@ def _split_roofline(wl, tc, ms, peaks, src, peak_fp32, n_sm, sm_max):
             "frac": b["frac"], "traffic": wl.traffic, "kernel": wl.kernel,
             "launches_per_step": wl.launches,
             "achieved_basis": "split roofline: T_min = max(filter bank + adjoint flops / tensor "
-                              "peak, (phi + prox) flops / FP32 peak); frac = T_min / step time "
+                              "peak, (phi + prox" + (" + FP32 backward" if hasattr(
+                                  wl, "alu_flops_per_px_stage") else "") +
+                              ") flops / FP32 peak); frac = T_min / step time "
                               "of the binding term",
             "terms": terms, "peak_source": b["peak_source"]}
 
@@ -913,7 +968,7 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1 and args.workload not in ("fwd512", "fit"):
+    if world > 1 and args.workload not in ("fwd512", "fit", "fit_tf32"):
         if rank == 0:
             print(json.dumps({"workload": args.workload,
                               "unavailable": "multi-GPU runs use the fwd512 (independent images) "
@@ -1025,8 +1080,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fwd512",
                     choices=["fwd512", "fwd512_unfused", "small128", "batched", "batched_tf32",
-                             "batched_bf16", "train",
-                             "fit", "fwd512_gauss", "fwd512_proj", "quality", "mixed_tf32",
+                             "batched_bf16", "train", "train_tf32", "train_bf16",
+                             "fit", "fit_tf32", "fwd512_gauss", "fwd512_proj", "quality", "mixed_tf32",
                              "mixed_bf16", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",

@@ -1,8 +1,11 @@
 """torch.autograd binding of the TRDMD cascade.
 
 `TNRDFunction.apply(f, filters, rbf_w, lam, mu0, delta, gamma, data_term,
-proj_c)` runs the forward cascade (tnrd_forward, keeping u_0..u_T as
-checkpoints) and, in backward, the library's gradient kernels (tnrd_backward).  The noisy input f
+proj_c, algo)` runs the forward cascade (tnrd_forward, keeping u_0..u_T as
+checkpoints) and, in backward, the library's gradient kernels (tnrd_backward).
+`algo` picks the forward's stage kernels: "fused" (FP32), or "tf32" / "bf16"
+(tensor-core filter bank and adjoint); the backward is FP32 in every case and
+differentiates the cascade at the checkpoints the forward wrote.  The noisy input f
 is data: it gets no gradient.  Training lambda through lam = exp(beta) (Sec.
 3.2, Eq. derv5) is plain torch: pass beta.exp() as `lam`.
 """
@@ -17,13 +20,13 @@ from . import ops
 class TNRDFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, f, filters, rbf_w, lam, mu0=-310.0, delta=10.0, gamma=10.0, data_term=0,
-                proj_c=1.0):
+                proj_c=1.0, algo="fused"):
         model = ops.Model(filters.detach().contiguous(), rbf_w.detach().contiguous(),
                           lam.detach().contiguous(), float(mu0), float(delta), float(gamma),
                           int(data_term), float(proj_c))
         W = f.shape[-1]
         fp = ops.to_pitched(f.detach())
-        u_all = ops.forward(model, fp, keep_stages=True, W=W)
+        u_all = ops.forward(model, fp, keep_stages=True, algo=algo, W=W)
         ctx.model = model
         ctx.W = W
         ctx.save_for_backward(fp, u_all)
@@ -39,10 +42,13 @@ class TNRDFunction(torch.autograd.Function):
         if gp.shape[-1] != fp.shape[-1]:
             gp = torch.nn.functional.pad(gp, (0, fp.shape[-1] - gp.shape[-1]))
         _, gk, gw, gl = ops.backward(ctx.model, fp, u_all, gp, want_grad_u0=False, W=W)
-        return None, gk, gw, gl, None, None, None, None, None
+        return None, gk, gw, gl, None, None, None, None, None, None
 
 
-def trdmd(f, filters, rbf_w, lam, mu0=-310.0, delta=10.0, gamma=10.0, data_term=0, proj_c=1.0):
+def trdmd(f, filters, rbf_w, lam, mu0=-310.0, delta=10.0, gamma=10.0, data_term=0, proj_c=1.0,
+          algo="fused"):
     """u_T of the T-stage cascade, differentiable in filters, rbf_w and lam
-    (data_term as tnrd_data_term: 0 despeckling prox, 1 Gaussian, 2 projection)."""
-    return TNRDFunction.apply(f, filters, rbf_w, lam, mu0, delta, gamma, data_term, proj_c)
+    (data_term as tnrd_data_term: 0 despeckling prox, 1 Gaussian, 2 projection;
+    algo the forward's stage kernels: "fused", "tf32" or "bf16")."""
+    return TNRDFunction.apply(f, filters, rbf_w, lam, mu0, delta, gamma, data_term, proj_c,
+                              algo)

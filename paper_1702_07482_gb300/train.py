@@ -102,12 +102,14 @@ def loss_sum(u: torch.Tensor, clean: torch.Tensor) -> torch.Tensor:
     return 0.5 * ((u - clean) ** 2).sum()
 
 
-def cascade(p: Params, f: torch.Tensor, stages: int | None = None) -> torch.Tensor:
-    """u_t after the first `stages` stages (all T by default), differentiable."""
+def cascade(p: Params, f: torch.Tensor, stages: int | None = None,
+            algo: str = "fused") -> torch.Tensor:
+    """u_t after the first `stages` stages (all T by default), differentiable;
+    `algo` the forward's stage kernels ("fused", "tf32", "bf16")."""
     sl = slice(0, p.T if stages is None else stages)
     return autograd.trdmd(f, p.filters(sl).contiguous(), p.weights(sl).contiguous(),
                           p.lam(sl).contiguous(), p.mu0, p.delta, p.gamma, p.data_term,
-                          p.proj_c)
+                          p.proj_c, algo)
 
 
 def _make_opt(tensors, optimizer: str, lr: float):

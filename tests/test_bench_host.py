@@ -65,6 +65,27 @@ def test_split_roofline_of_the_tensor_core_stage(bench):
     assert r2["terms"]["tensor"]["peak"] == pytest.approx(1700.0)
 
 
+def test_split_roofline_of_the_mixed_training_step(bench):
+    """Training with a tensor-core forward: only the forward's filter bank and
+    adjoint go on the tensor term; phi, the prox and the whole FP32 backward on
+    the ALU term, which binds."""
+    class Wl:
+        flops_per_px_stage = bench.FLOPS_PER_PX_STAGE + bench.BWD_FLOPS_PER_PX_STAGE
+        flops = 1e8 * flops_per_px_stage
+        conv_flops_per_px_stage = bench.CONV_FLOPS_PER_PX_STAGE
+        alu_flops_per_px_stage = bench.ALU_FLOPS_PER_PX_STAGE + bench.BWD_FLOPS_PER_PX_STAGE
+        traffic, kernel, launches = None, "tc + bwd", 30
+    assert (Wl.conv_flops_per_px_stage + Wl.alu_flops_per_px_stage == Wl.flops_per_px_stage)
+    ms = 10.0
+    r = bench._split_roofline(Wl, "tf32", ms, {"bf16_tflops_sustained": 1700.0}, "measured",
+                              80.0, 152, 2070.0)
+    t_alu = 1e8 * Wl.alu_flops_per_px_stage / 80e12
+    assert r["bound"] == "alu"
+    assert r["frac"] == pytest.approx(t_alu / (ms / 1e3))
+    assert r["terms"]["tensor"]["flops"] == pytest.approx(1e8 * bench.CONV_FLOPS_PER_PX_STAGE)
+    assert "FP32 backward" in r["achieved_basis"]
+
+
 def test_reference_arm_config_equals_the_default_workload_config(bench):
     # the driver compares the two arms' config: the reference line must name
     # the same workload keys as the GPU arm's default line

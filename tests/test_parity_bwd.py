@@ -28,12 +28,12 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-def _gpu_grads(p, f, clean):
+def _gpu_grads(p, f, clean, algo="fused"):
     from paper_1702_07482_gb300 import ops
     m = ops.Model.create(p.filters, p.rbf_w, p.lam, p.mu0, p.delta, p.gamma)
     W = f.shape[-1]
     fp = ops.to_pitched(torch.tensor(f, dtype=torch.float32, device="cuda"))
-    u_all = ops.forward(m, fp, keep_stages=True, W=W)
+    u_all = ops.forward(m, fp, keep_stages=True, algo=algo, W=W)
     ct = ops.to_pitched(torch.tensor(clean, dtype=torch.float32, device="cuda"))
     eT = (u_all[-1] - ct).contiguous()
     g0, gk, gw, gl = ops.backward(m, fp, u_all, eT, want_grad_u0=True, W=W)
@@ -58,15 +58,16 @@ def _oracle_grads(p, f, clean, u_gpu=None):
     return np.stack(g0), gk, gw, gl
 
 
-def _check(p, f, clean):
-    _, g0, gk, gw, gl = _gpu_grads(p, f, clean)
+def _check(p, f, clean, algo="fused", tol=TOL_GRAD):
+    _, g0, gk, gw, gl = _gpu_grads(p, f, clean, algo)
     r0, rk, rw, rl = _oracle_grads(p, f, clean)
     errs = {"u0": _rel(g0, r0), "lam": _rel(gl, rl)}
     for t in range(p.T):
         errs[f"k{t}"] = _rel(gk[t], rk[t])
         errs[f"w{t}"] = _rel(gw[t], rw[t])
-    bad = {k: v for k, v in errs.items() if not v <= TOL_GRAD}
-    assert not bad, f"relative L2 errors above {TOL_GRAD}: {bad}"
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"relative L2 errors above {tol}: {bad}"
+    return errs
 
 
 def test_fd_instance_32x32_3x3x4_T2():
@@ -141,3 +142,43 @@ def test_full_size_180_crop_T5():
     p, f = case(180, 180, 7, 48, 5, cfg=4)
     clean = np.stack([_clean(180, 180, 4)])
     _check(p, f, clean)
+
+
+# Mixed-precision training: the forward's filter bank and adjoint on the tensor
+# cores (TF32 or BF16 operands, FP32 accumulation), the backward FP32.  The
+# gradients are those of the cascade at the checkpoints the forward wrote, so
+# they inherit the forward's error.
+TOL_GRAD_TC = {"tf32": 1e-3, "bf16": 1e-2}
+
+
+@pytest.mark.parametrize("algo", ["tf32", "bf16"])
+def test_tensor_core_forward_gradients_180_crop_T5(algo):
+    p, f = case(180, 180, 7, 48, 5, cfg=4)
+    clean = np.stack([_clean(180, 180, 4)])
+    _check(p, f, clean, algo, TOL_GRAD_TC[algo])
+
+
+@pytest.mark.parametrize("algo", ["tf32", "bf16"])
+def test_tensor_core_forward_gradients_ragged_batch(algo):
+    p, f = case(61, 90, 7, 48, 3, N=2, cfg=161)
+    clean = np.stack([_clean(61, 90, 161, n) for n in range(2)])
+    _check(p, f, clean, algo, TOL_GRAD_TC[algo])
+
+
+def test_autograd_tensor_core_forward():
+    """autograd.trdmd(algo="tf32") gives the gradients of ops.forward(tf32) +
+    ops.backward, bit for bit (same kernels, same order)."""
+    from paper_1702_07482_gb300 import autograd
+    p, f = case(64, 64, 7, 48, 2, cfg=162)
+    clean = _clean(64, 64, 162)
+    dev = "cuda"
+    k = torch.tensor(p.filters, dtype=torch.float32, device=dev, requires_grad=True)
+    w = torch.tensor(p.rbf_w, dtype=torch.float32, device=dev, requires_grad=True)
+    lam = torch.tensor(p.lam, dtype=torch.float32, device=dev, requires_grad=True)
+    u = autograd.trdmd(torch.tensor(f[0], dtype=torch.float32, device=dev), k, w, lam,
+                       algo="tf32")
+    (0.5 * ((u - torch.tensor(clean, dtype=torch.float32, device=dev)) ** 2).sum()).backward()
+    _, _, gk, gw, gl = _gpu_grads(p, f, clean[None], "tf32")
+    np.testing.assert_array_equal(k.grad.double().cpu().numpy(), gk)
+    np.testing.assert_array_equal(w.grad.double().cpu().numpy(), gw)
+    np.testing.assert_array_equal(lam.grad.double().cpu().numpy(), gl)
