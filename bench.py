@@ -392,7 +392,11 @@ class Fwd(Workload):
         self.f_host = self.f_dev.cpu().pin_memory()
         self.u_host = torch.empty_like(self.f_host).pin_memory()
         self.px = H * W
-        self.launches = T_ * (1 if algo == "fused" else 3)
+        self.launches = T_ * (3 if algo == "unfused" else 1)
+        if algo in TENSOR_RATIO:
+            self.tensor_dtype = algo
+            self.dtype = ("f32 (split TF32 tensor-core products)" if algo == "tf32x3"
+                          else f"{algo} operands, f32 accumulate")
         fl = 2 * nk * ks * ks * 2 + 2 * nk * 63 + 12
         self.flops = float(H * W) * T_ * fl
         self.flops_per_px_stage = fl
@@ -403,9 +407,11 @@ class Fwd(Workload):
         noise = {0: f"L={L}", 1: "Gaussian sigma=25", 2: f"L={L}"}[data_term]
         dterm = {0: "", 1: ", TNRD Gaussian-denoising reaction (Sec. 2.2.1)",
                  2: ", explicit step with projection max(u, 1) (Eq. diffusion_backP)"}[data_term]
+        kdesc = (f"{algo} FP32 stage kernel" + ("" if algo == "fused" else "s")
+                 if algo in ("fused", "unfused") else
+                 f"tensor-core stage ({PREC_TEXT[algo]}; phi and prox FP32)")
         self.config = {"workload": f"TRDMD forward, 1 x {H}x{W} per GPU, {ks}x{ks}x{nk}, 63 RBF, "
-                                   f"T={T_}, {noise}, {algo} FP32 stage kernel" +
-                                   ("" if algo == "fused" else "s") + dterm,
+                                   f"T={T_}, {noise}, {kdesc}" + dterm,
                        "H": H, "W": W, "images_per_gpu": 1, "ksize": ks, "nfilt": nk,
                        "nrbf": 63, "T": T_, "looks": L if data_term != 1 else None,
                        "data_term": ["idiv", "gauss", "proj"][data_term],
@@ -575,13 +581,15 @@ class Train(Workload):
         if algo != "fused":
             # the forward's filter bank and adjoint on the tensor cores, the rest FP32
             self.tensor_dtype = algo
-            self.dtype = f"{algo} operands, f32 accumulate (forward filter bank and adjoint); f32"
+            self.dtype = ("f32 (forward: split TF32 tensor-core products)" if algo == "tf32x3" else
+                          f"{algo} operands, f32 accumulate (forward filter bank and adjoint); f32")
             self.conv_flops_per_px_stage = CONV_FLOPS_PER_PX_STAGE
             self.alu_flops_per_px_stage = ALU_FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE
         self.h2d = int((self.f_host.numel() + self.c_host.numel()) * 4)
         self.d2h = int(self.g_host.numel() * 4)
         fwd = {"fused": "", "tf32": ", TF32 tensor-core forward, FP32 backward",
-               "bf16": ", BF16 tensor-core forward, FP32 backward"}[algo]
+               "bf16": ", BF16 tensor-core forward, FP32 backward",
+               "tf32x3": ", split-TF32 tensor-core forward, FP32 backward"}[algo]
         self.config = {"workload": f"TRDMD training step (forward + backward), {n} crops of "
                                    f"{S}x{S}, L=1, 7x7x48, 63 RBF, T={T_}, loss 1/2|u_T - clean|^2, "
                                    "gradients of all filters, RBF weights and lambda" + fwd,
@@ -770,9 +778,10 @@ class Mixed(Workload):
         from paper_1702_07482_gb300 import binding as B
         from paper_1702_07482_gb300 import ops
         self.T, self.n, self.S, self.algo = T_, n, S, algo
-        self.tensor_dtype = algo if algo in ("tf32", "bf16") else None
+        self.tensor_dtype = algo if algo in TENSOR_RATIO else None
         self.dtype = {"tf32": "tf32 operands, f32 accumulate",
-                      "bf16": "bf16 operands, f32 accumulate"}.get(algo, "f32")
+                      "bf16": "bf16 operands, f32 accumulate",
+                      "tf32x3": "f32 (split TF32 tensor-core products)"}.get(algo, "f32")
         self.p = _p32(synth.params(T_, KS, NK, seed=synth.seed_for(cfg, 0, "params")))
         self.m = ops.Model.create(self.p.filters, self.p.rbf_w, self.p.lam, device=dev)
         self.prm = self.m.params()
@@ -796,11 +805,11 @@ class Mixed(Workload):
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE
         self.kernel = B.tnrd_forward_kernel(self.prm, n, S, S, self.code) + \
             {"tf32": " (tcgen05 TF32 filter bank and adjoint, FP32 phi/prox)",
-             "bf16": " (tcgen05 BF16 filter bank and adjoint, FP32 phi/prox)"}.get(algo, " (FP32)")
-        prec = {"tf32": "filter bank and adjoint on tensor cores (TF32 operands, FP32 accumulate), "
-                        "phi and prox FP32",
-                "bf16": "filter bank and adjoint on tensor cores (BF16 operands, FP32 accumulate), "
-                        "phi and prox FP32"}.get(algo, "plain FP32 fused stage kernel")
+             "bf16": " (tcgen05 BF16 filter bank and adjoint, FP32 phi/prox)",
+             "tf32x3": " (tcgen05 split-TF32 filter bank and adjoint, FP32 phi/prox)"}.get(
+                algo, " (FP32)")
+        prec = (f"filter bank and adjoint on tensor cores ({PREC_TEXT[algo]}), phi and prox FP32"
+                if algo in PREC_TEXT else "plain FP32 fused stage kernel")
         self.h2d = self.d2h = int(self.f_host.numel() * 4)
         self.config = {"workload": f"TRDMD forward, {n} x {S}x{S}, L=2, 7x7x48, 63 RBF, T={T_}, "
                                    f"{prec}",
@@ -867,6 +876,12 @@ def make_workload(name, dev):
         return Train(dev)
     if name == "train_tf32":
         return Train(dev, algo="tf32")
+    if name == "train_tf32x3":
+        return Train(dev, algo="tf32x3")
+    if name == "fwd512_tf32x3":
+        return Fwd(dev, algo="tf32x3")
+    if name == "mixed_tf32x3":
+        return Mixed(dev, algo="tf32x3")
     if name == "train_bf16":
         return Train(dev, algo="bf16")
     if name == "fit":
@@ -925,8 +940,12 @@ def run_reference(args):
 # contractions (2 x 2 N_k k^2 flops), phi and the prox the rest.
 CONV_FLOPS_PER_PX_STAGE = 2 * 2 * NK * KS * KS
 ALU_FLOPS_PER_PX_STAGE = 2 * NK * 63 + 12
-# dense tensor-core rates relative to BF16 (nominal: TF32 1.1, BF16 2.25 PFLOP/s)
-TENSOR_RATIO = {"tf32": 1.1 / 2.25, "bf16": 1.0}
+# dense tensor-core rates relative to BF16 (nominal: TF32 1.1, BF16 2.25 PFLOP/s);
+# split TF32 spends three TF32 products on each product of the algorithm
+TENSOR_RATIO = {"tf32": 1.1 / 2.25, "bf16": 1.0, "tf32x3": 1.1 / 2.25 / 3}
+PREC_TEXT = {"tf32": "TF32 operands, FP32 accumulate",
+             "bf16": "BF16 operands, FP32 accumulate",
+             "tf32x3": "split TF32 operands (hi + lo, three products), FP32 accumulate"}
 
 
 def _split_roofline(wl, tc, ms, peaks, src, peak_fp32, n_sm, sm_max):
@@ -943,7 +962,9 @@ def _split_roofline(wl, tc, ms, peaks, src, peak_fp32, n_sm, sm_max):
         "tensor": {"flops": conv, "achieved": conv / t / 1e12, "peak": tpeak,
                    "frac": conv / t / 1e12 / tpeak,
                    "peak_source": f"{src} bf16_tflops_sustained {bf:.1f} x nominal {tc}/bf16 "
-                                  f"ratio {TENSOR_RATIO[tc]:.3f}"},
+                                  f"ratio {TENSOR_RATIO[tc]:.3f}" +
+                               (" (TF32 / 3: three TF32 products per product)" if tc == "tf32x3"
+                                else "")},
         "alu": {"flops": alu, "achieved": alu / t / 1e12, "peak": peak_fp32,
                 "frac": alu / t / 1e12 / peak_fp32,
                 "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
@@ -1080,7 +1101,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fwd512",
                     choices=["fwd512", "fwd512_unfused", "small128", "batched", "batched_tf32",
-                             "batched_bf16", "train", "train_tf32", "train_bf16",
+                             "batched_bf16", "train", "train_tf32", "train_bf16", "train_tf32x3",
+                             "fwd512_tf32x3", "mixed_tf32x3",
                              "fit", "fit_tf32", "fwd512_gauss", "fwd512_proj", "quality", "mixed_tf32",
                              "mixed_bf16", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -62,12 +62,18 @@ typedef enum {
  * filters and phi's outputs rounded to TF32, 10-bit mantissa); its error
  * against the FP64 result is larger than the FP32 paths' (see the tests).
  * TNRD_ALGO_TC_BF16: the same GEMMs with BF16 operands (8-bit mantissa, round
- * to nearest even) and FP32 accumulation; error larger again. */
+ * to nearest even) and FP32 accumulation; error larger again.
+ * TNRD_ALGO_TC_TF32X3: the tensor-core GEMMs at FP32 accuracy: every operand x
+ * is split into hi = tf32(x) and lo = tf32(x - hi) and each product taken as
+ * lo*hi + hi*lo + hi*hi (three TF32 MMAs, FP32 accumulation; the dropped
+ * lo*lo term is below 2^-22 of the product), so its error against the FP64
+ * result is that of the FP32 paths (see the tests). */
 typedef enum {
     TNRD_ALGO_FUSED = 0,      /* one kernel per stage, responses kept on chip      */
     TNRD_ALGO_UNFUSED = 1,    /* three kernels per stage, N_k response planes in HBM */
     TNRD_ALGO_TC_TF32 = 2,
-    TNRD_ALGO_TC_BF16 = 3
+    TNRD_ALGO_TC_BF16 = 3,
+    TNRD_ALGO_TC_TF32X3 = 4
 } tnrd_algo;
 
 /* Data term (reaction force) of every stage of a model.  With
@@ -164,7 +170,7 @@ TNRD_API tnrd_status tnrd_backward(const tnrd_params* params, int N, int H, int 
  * tnrd_plan_tile_width; the persistent launch without autotune).  The first
  * two give the same bits; the third the bits of tnrd_forward's column-pair
  * kernel at the same tile height.
- * With TNRD_ALGO_TC_TF32 / _BF16 it runs one
+ * With TNRD_ALGO_TC_TF32 / _BF16 / _TF32X3 it runs one
  * tensor-core launch per stage over all images' tiles (mixed precision as in
  * tnrd_forward).  The launches are recorded in a CUDA graph at plan creation
  * and replayed by tnrd_batch_forward. */
@@ -179,7 +185,8 @@ typedef struct tnrd_plan tnrd_plan;
 
 /* Creates a plan for `nimg` images (host array, copied) and `nsets` parameter
  * sets (host array of tnrd_params with device arrays, copied; all sets must
- * share T, ksize, nfilt, nrbf).  algo: TNRD_ALGO_FUSED, _TC_TF32 or _TC_BF16
+ * share T, ksize, nfilt, nrbf).  algo: TNRD_ALGO_FUSED, _TC_TF32, _TC_BF16 or
+ * _TC_TF32X3
  * (TNRD_ALGO_UNFUSED is not batched).  This is the one
  * call that allocates device memory (work lists, per-tile stage counters, the
  * inter-stage images, a status word).  With autotune != 0 it times each

@@ -18,7 +18,7 @@ TNRD_OK = 0
 STATUS_NAMES = {0: "TNRD_OK", 1: "TNRD_ERR_INVALID_ARG", 2: "TNRD_ERR_UNSUPPORTED",
                 3: "TNRD_ERR_CUDA", 4: "TNRD_ERR_TIMEOUT", 5: "TNRD_ERR_WORKSPACE"}
 
-ALGO = {"fused": 0, "unfused": 1, "tf32": 2, "bf16": 3}
+ALGO = {"fused": 0, "unfused": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
 OP_FORWARD, OP_BACKWARD = 0, 1
 
 # Every symbol include/tnrd.h declares (checked by the tests).

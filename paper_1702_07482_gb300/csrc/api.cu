@@ -303,10 +303,28 @@ FusedChoice pick_fused(int ks, int nk, int N, int H, int W)
 
 // Row blocks of 16 z rows per tensor-core tile: 3 for BF16 (its smaller
 // operands leave room for three warpgroups with the taller tile), 2 for TF32
-// (three warpgroups fit only with the shorter one).  TNRD_TC_NB=2|3 overrides.
+// (three warpgroups fit only with the shorter one) and for split TF32 (built
+// with two only).  TNRD_TC_NB=2|3 overrides for TF32 and BF16.
+bool is_tc(tnrd_algo algo)
+{
+    return algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16 || algo == TNRD_ALGO_TC_TF32X3;
+}
+
+int tc_prec(tnrd_algo algo)
+{
+    return algo == TNRD_ALGO_TC_BF16 ? tnrd::TC_BF16 : algo == TNRD_ALGO_TC_TF32X3 ? tnrd::TC_TF32X3
+                                                                                    : tnrd::TC_TF32;
+}
+
+const char* tc_name(tnrd_algo algo)
+{
+    return algo == TNRD_ALGO_TC_BF16 ? "bf16" : algo == TNRD_ALGO_TC_TF32X3 ? "tf32x3" : "tf32";
+}
+
 int pick_tc_nb(tnrd_algo algo)
 {
     int nb = (algo == TNRD_ALGO_TC_BF16) ? 3 : 2;
+    if (algo == TNRD_ALGO_TC_TF32X3) return 2;
     if (const char* env = std::getenv("TNRD_TC_NB")) {
         const int v = std::atoi(env);
         if (v == 2 || v == 3) nb = v;
@@ -457,10 +475,10 @@ tnrd_status tnrd_forward_kernel(const tnrd_params* p, int N, int H, int W, tnrd_
         }
     } else if (algo == TNRD_ALGO_UNFUSED) {
         std::snprintf(buf, len, "unf_bank_phi + unf_adjoint + unf_prox <%d,%d>", ks, nk);
-    } else if (algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16) {
+    } else if (is_tc(algo)) {
         const int nb = pick_tc_nb(algo);
-        std::snprintf(buf, len, "tc_stage_fwd<%d,%d,%d,%s> tiles %dx%d", ks, nk, nb,
-                      algo == TNRD_ALGO_TC_BF16 ? "bf16" : "tf32", tnrd::tc_tile_h(ks, nb), 32 - 2 * R);
+        std::snprintf(buf, len, "tc_stage_fwd<%d,%d,%d,%s> tiles %dx%d", ks, nk, nb, tc_name(algo),
+                      tnrd::tc_tile_h(ks, nb), 32 - 2 * R);
     } else {
         return fail(TNRD_ERR_INVALID_ARG, "unknown algo");
     }
@@ -475,8 +493,7 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
     if (st != TNRD_OK) return st;
     st = check_images(N, H, W, pitch, p->ksize);
     if (st != TNRD_OK) return st;
-    if (algo != TNRD_ALGO_FUSED && algo != TNRD_ALGO_UNFUSED && algo != TNRD_ALGO_TC_TF32 &&
-        algo != TNRD_ALGO_TC_BF16)
+    if (algo != TNRD_ALGO_FUSED && algo != TNRD_ALGO_UNFUSED && !is_tc(algo))
         return fail(TNRD_ERR_UNSUPPORTED, "algo %d not available in tnrd_forward", (int)algo);
     if (N == 0) return TNRD_OK;
     if (!f || !u) return fail(TNRD_ERR_INVALID_ARG, "null image pointer");
@@ -578,7 +595,7 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             e = (fc.pair && fc.nsplit > 2) ? tnrd::launch_pair_cluster_fwd(ks, nk, fc.kth, fc.nsplit, a, N, stream)
               : fc.pair ? tnrd::launch_pair_fwd(ks, nk, fc.kth, fc.nsplit, a, N, stream)
                         : tnrd::launch_fused_fwd(ks, nk, fc.kth, a, N, stream);
-        } else if (algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16) {
+        } else if (is_tc(algo)) {
             tnrd::StageArgs a{};
             const int tw = 32 - 2 * (ks / 2), tth = tnrd::tc_tile_h(ks, tc_nb);
             a.u_in = in;
@@ -597,7 +614,7 @@ tnrd_status tnrd_forward(const tnrd_params* p, int N, int H, int W, int pitch,
             a.dterm = p->data_term;
             a.proj_c = p->proj_c;
             a.rc = rc;
-            e = tnrd::launch_tc_fwd(ks, nk, tc_nb, algo == TNRD_ALGO_TC_BF16, a, N, stream);
+            e = tnrd::launch_tc_fwd(ks, nk, tc_nb, tc_prec(algo), a, N, stream);
         } else {
             tnrd::UnfArgs a{};
             a.u_in = in;
@@ -885,9 +902,8 @@ cudaError_t plan_enqueue(const tnrd_plan* P, cudaStream_t s)
         return P->stages == 2 ? tnrd::launch_batch_pairs(P->ks, P->nk, P->th, P->args, s)
              : P->stages ? tnrd::launch_batch_stages(P->ks, P->nk, P->th, P->args, s)
                          : tnrd::launch_batch_fwd(P->ks, P->nk, P->th, P->args, P->grid, s);
-    const bool bf16 = P->algo == TNRD_ALGO_TC_BF16;
     for (int t = 0; t < P->T && e == cudaSuccess; ++t)
-        e = tnrd::launch_tc_batch(P->ks, P->nk, P->tc_nb, bf16, P->args, t, P->ntiles, s);
+        e = tnrd::launch_tc_batch(P->ks, P->nk, P->tc_nb, tc_prec(P->algo), P->args, t, P->ntiles, s);
     return e;
 }
 
@@ -903,7 +919,7 @@ tnrd_status tnrd_plan_create(tnrd_plan** out, const tnrd_image* images, int nimg
     *out = nullptr;
     if (!images || nimg < 1 || !sets || nsets < 1)
         return fail(TNRD_ERR_INVALID_ARG, "need at least one image and one parameter set");
-    if (algo != TNRD_ALGO_FUSED && algo != TNRD_ALGO_TC_TF32 && algo != TNRD_ALGO_TC_BF16)
+    if (algo != TNRD_ALGO_FUSED && !is_tc(algo))
         return fail(TNRD_ERR_UNSUPPORTED, "batched forward supports the fused and tensor-core stages");
     for (int s = 0; s < nsets; ++s) {
         tnrd_status st = check_params(&sets[s]);

@@ -360,14 +360,17 @@ struct BatchArgs {
 };
 
 // ---------------------------------------------------------------------------
-// Tensor-core stage (TNRD_ALGO_TC_TF32 / _BF16): filter bank and adjoint as
-// implicit GEMMs on tcgen05, phi and the prox on the CUDA cores.  One
-// persistent CTA per SM of NWG independent warpgroups; each warpgroup works
+// Tensor-core stage (TNRD_ALGO_TC_TF32 / _BF16 / _TF32X3): filter bank and
+// adjoint as implicit GEMMs on tcgen05, phi and the prox on the CUDA cores.
+// One persistent CTA per SM of NWG independent warpgroups; each warpgroup works
 // through its own tiles, the GEMMs' filter operands and the RBF weights are
-// staged once per CTA (per parameter set) and shared.
+// staged once per CTA (per parameter set) and shared.  X3: every operand is
+// kept as its TF32 high part and the TF32 rounding of the remainder, and each
+// product is taken as lo*hi + hi*lo + hi*hi (three TF32 MMAs).
 // ---------------------------------------------------------------------------
-template <int KS, int NK, int NB, bool BF>
+template <int KS, int NK, int NB, bool BF, bool X3 = false>
 struct TcCfg {
+    static_assert(!(BF && X3), "split operands are TF32 only");
     static constexpr int R = KS / 2;
     static constexpr int TW = 32 - 2 * R;        // output columns per tile
     static constexpr int ZR = 16 * NB;           // z rows per tile (NB blocks of 16)
@@ -375,6 +378,7 @@ struct TcCfg {
     static constexpr int ESZ = BF ? 2 : 4;       // bytes per operand element
     static constexpr int KMMA = BF ? 16 : 8;     // K of one MMA (32 bytes)
     static constexpr int KCORE = BF ? 8 : 4;     // K elements of one core matrix row (16 bytes)
+    static constexpr int NSPL = X3 ? 2 : 1;      // copies of each operand (X3: high, low part)
     static constexpr int NPAD = (NK + 15) / 16 * 16;                 // N of the filter-bank GEMM
     static constexpr int NKP = (NK + KMMA - 1) / KMMA * KMMA;        // K of the adjoint GEMM
     static constexpr int NT = (KS * KS + 15) / 16 * 16;  // N of the adjoint GEMM (taps)
@@ -396,25 +400,36 @@ struct TcCfg {
     static constexpr int WPADN = MAX_NRBF + 2 * RBF_WPAD;
     static constexpr size_t al(size_t x) { return (x + 127) / 128 * 128; }
     static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
-    // shared by the CTA's warpgroups
+    // shared by the CTA's warpgroups (X3: the low parts right after the high parts)
+    static constexpr size_t BZ_BYTES = (size_t)ESZ * KS * NPAD * KMMA;
+    static constexpr size_t KM_BYTES = (size_t)ESZ * NT * NKP;
     static constexpr size_t OFF_BZ = 0;
-    static constexpr size_t OFF_KM = al(OFF_BZ + (size_t)ESZ * KS * NPAD * KMMA);
-    static constexpr size_t OFF_W = al(OFF_KM + (size_t)ESZ * NT * NKP);
+    static constexpr size_t OFF_KM = al(OFF_BZ + NSPL * BZ_BYTES);
+    static constexpr size_t OFF_W = al(OFF_KM + NSPL * KM_BYTES);
     static constexpr int NR = (NK + 15) / 16;    // rounds of 16 filters (RBF weight table)
     static constexpr size_t OFF_WG = al(OFF_W + 8ull * NR * TC_ROWS * 16);
-    // per warpgroup: u operands, V (the raw u rows before the first group), h, barriers
+    // per warpgroup: u operands, V (the raw u rows before the first group), h, barriers.
+    // V holds all NKP filters of a group, or (X3) one round of 16 filters, high and
+    // low parts: the round's adjoint MMAs run while phi works on the next round.
+    static constexpr size_t U_BYTES = 4ull * UROWS * UROWB;
+    static constexpr int VF = X3 ? 16 : NKP;     // filters of V held at once
+    static constexpr size_t VLO = (size_t)ESZ * 128 * VF;   // byte offset of V's low parts
     static constexpr size_t WG_U = 0;
-    static constexpr size_t WG_V = al(WG_U + 4ull * UROWS * UROWB);
-    static constexpr size_t WG_H = al(WG_V + mx((size_t)ESZ * 128 * NKP, 4ull * UROWS * RAWP));
+    static constexpr size_t WG_V = al(WG_U + NSPL * U_BYTES);
+    static constexpr size_t WG_H = al(WG_V + mx(NSPL * VLO, 4ull * UROWS * RAWP));
     static constexpr size_t WG_MISC = al(WG_H + 4ull * HROWS * HPITCH);
     static constexpr size_t WG_BYTES = al(WG_MISC + 32);
     static constexpr size_t SMEM_MAX = 227 * 1024;
     static constexpr int fit_wg(int n) { return (n > 1 && OFF_WG + (size_t)n * WG_BYTES + 16 > SMEM_MAX) ? fit_wg(n - 1) : n; }
-    static constexpr int NWG = fit_wg(4);        // warpgroups per CTA (TMEM: 128 columns each)
+    // warpgroups per CTA; TMEM columns of one: z buffers 0..63, 64..127, and
+    // (X3) the adjoint's Y at 128..191 (z and Y share a buffer otherwise)
+    static constexpr int NWG = fit_wg(X3 ? 2 : 4);
+    static constexpr int TMEM_WG = X3 ? 256 : 128;
     static constexpr int NTHREADS = 128 * NWG;
     static constexpr size_t OFF_TMEM = OFF_WG + (size_t)NWG * WG_BYTES;
     static constexpr size_t SMEM_BYTES = OFF_TMEM + 16;
-    static constexpr uint32_t TMEM_COLS = NWG <= 2 ? 256 : 512;
+    static constexpr uint32_t TMEM_COLS = NWG * TMEM_WG <= 256 ? 256 : 512;
+    static_assert(NWG * TMEM_WG <= 512, "TMEM");
     static_assert(SMEM_BYTES <= SMEM_MAX, "shared memory");
 };
 

@@ -54,7 +54,10 @@ cudaError_t launch_unfused_fwd(int ks, const UnfArgs& a, int N, cudaStream_t s);
 // Tensor-core forward stage: tile height for NB row blocks, launcher, and the
 // device error word (read and cleared).
 int tc_tile_h(int ks, int nb);
-cudaError_t launch_tc_fwd(int ks, int nk, int nb, bool bf16, const StageArgs& a, int N,
+// Operand precision of the tensor-core stage: TF32, BF16, or TF32 with split
+// (high + low) operands.
+enum TcPrec { TC_TF32 = 0, TC_BF16 = 1, TC_TF32X3 = 2 };
+cudaError_t launch_tc_fwd(int ks, int nk, int nb, int prec, const StageArgs& a, int N,
                           cudaStream_t s);
 cudaError_t tc_take_error(int* out);
 // Address of that word on the current device (null if it cannot be had); the
@@ -81,7 +84,7 @@ long long stage_wait_limit();
 // Staged tile (columns x rows) of the fused forward kernel of tile height th.
 bool fused_fwd_box(int ks, int nk, int th, int* box_w, int* box_h);
 // One stage t of a batched plan on the tensor cores (all images' tiles in one launch).
-cudaError_t launch_tc_batch(int ks, int nk, int nb, bool bf16, const BatchArgs& a, int t,
+cudaError_t launch_tc_batch(int ks, int nk, int nb, int prec, const BatchArgs& a, int t,
                             int ntiles, cudaStream_t s);
 
 // Column-pair fused forward (two z-columns per lane, TW = 64 - 2R); nsplit 2

@@ -18,64 +18,79 @@ int sm_count()
 
 // Persistent grid: at most one CTA per SM, and no more CTAs than there are
 // tiles for their warpgroups.
-template <int KS, int NK, int NB, bool BF>
+template <int KS, int NK, int NB, bool BF, bool X3>
 int tc_grid(long long ntiles)
 {
-    using C = TcCfg<KS, NK, NB, BF>;
+    using C = TcCfg<KS, NK, NB, BF, X3>;
     const long long need = (ntiles + C::NWG - 1) / C::NWG;
     return (int)std::max(1LL, std::min((long long)sm_count(), need));
 }
 
-template <int KS, int NK, int NB, bool BF>
+template <int KS, int NK, int NB, bool BF, bool X3>
 cudaError_t launch_one(const StageArgs& a, int N, cudaStream_t s)
 {
-    using C = TcCfg<KS, NK, NB, BF>;
-    cudaError_t e = cudaFuncSetAttribute(tc_stage_fwd<KS, NK, NB, BF>,
+    using C = TcCfg<KS, NK, NB, BF, X3>;
+    cudaError_t e = cudaFuncSetAttribute(tc_stage_fwd<KS, NK, NB, BF, X3>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const int grid = tc_grid<KS, NK, NB, BF>((long long)N * a.tiles_x * a.tiles_y);
-    return launch_pdl(tc_stage_fwd<KS, NK, NB, BF>, dim3(grid), dim3(C::NTHREADS), C::SMEM_BYTES, s, a, N);
+    const int grid = tc_grid<KS, NK, NB, BF, X3>((long long)N * a.tiles_x * a.tiles_y);
+    return launch_pdl(tc_stage_fwd<KS, NK, NB, BF, X3>, dim3(grid), dim3(C::NTHREADS), C::SMEM_BYTES,
+                      s, a, N);
 }
 
-template <int KS, int NK, int NB, bool BF>
+template <int KS, int NK, int NB, bool BF, bool X3>
 cudaError_t launch_batch_one(const BatchArgs& a, int t, int ntiles, cudaStream_t s)
 {
-    using C = TcCfg<KS, NK, NB, BF>;
-    cudaError_t e = cudaFuncSetAttribute(tc_batch_fwd<KS, NK, NB, BF>,
+    using C = TcCfg<KS, NK, NB, BF, X3>;
+    cudaError_t e = cudaFuncSetAttribute(tc_batch_fwd<KS, NK, NB, BF, X3>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    tc_batch_fwd<KS, NK, NB, BF><<<tc_grid<KS, NK, NB, BF>(ntiles), C::NTHREADS, C::SMEM_BYTES, s>>>(a, t);
+    tc_batch_fwd<KS, NK, NB, BF, X3><<<tc_grid<KS, NK, NB, BF, X3>(ntiles), C::NTHREADS,
+                                       C::SMEM_BYTES, s>>>(a, t);
     return cudaGetLastError();
 }
 
 #define TNRD_TC_CASES(X) \
     X(3, 4, 2) X(3, 4, 3) X(5, 24, 2) X(5, 24, 3) X(7, 48, 2) X(7, 48, 3)
+// split-operand TF32 (two row blocks: the operand copies leave room for no more)
+#define TNRD_TC_X3_CASES(X) X(3, 4, 2) X(5, 24, 2) X(7, 48, 2)
 
 }  // namespace
 
 int tc_tile_h(int ks, int nb) { return 16 * nb - 2 * (ks / 2); }
 
-cudaError_t launch_tc_fwd(int ks, int nk, int nb, bool bf16, const StageArgs& a, int N,
+cudaError_t launch_tc_fwd(int ks, int nk, int nb, int prec, const StageArgs& a, int N,
                           cudaStream_t s)
 {
 #define X(K, NN, B)                                                                  \
-    if (ks == K && nk == NN && nb == B)                                              \
-        return bf16 ? launch_one<K, NN, B, true>(a, N, s) : launch_one<K, NN, B, false>(a, N, s);
+    if (ks == K && nk == NN && nb == B && prec != TC_TF32X3)                         \
+        return prec == TC_BF16 ? launch_one<K, NN, B, true, false>(a, N, s)          \
+                               : launch_one<K, NN, B, false, false>(a, N, s);
     TNRD_TC_CASES(X)
+#undef X
+#define X(K, NN, B)                                                                  \
+    if (ks == K && nk == NN && nb == B && prec == TC_TF32X3)                         \
+        return launch_one<K, NN, B, false, true>(a, N, s);
+    TNRD_TC_X3_CASES(X)
 #undef X
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tc_batch(int ks, int nk, int nb, bool bf16, const BatchArgs& a, int t,
+cudaError_t launch_tc_batch(int ks, int nk, int nb, int prec, const BatchArgs& a, int t,
                             int ntiles, cudaStream_t s)
 {
 #define X(K, NN, B)                                                                     \
-    if (ks == K && nk == NN && nb == B)                                                 \
-        return bf16 ? launch_batch_one<K, NN, B, true>(a, t, ntiles, s)                 \
-                    : launch_batch_one<K, NN, B, false>(a, t, ntiles, s);
+    if (ks == K && nk == NN && nb == B && prec != TC_TF32X3)                            \
+        return prec == TC_BF16 ? launch_batch_one<K, NN, B, true, false>(a, t, ntiles, s) \
+                               : launch_batch_one<K, NN, B, false, false>(a, t, ntiles, s);
     TNRD_TC_CASES(X)
+#undef X
+#define X(K, NN, B)                                                                     \
+    if (ks == K && nk == NN && nb == B && prec == TC_TF32X3)                            \
+        return launch_batch_one<K, NN, B, false, true>(a, t, ntiles, s);
+    TNRD_TC_X3_CASES(X)
 #undef X
     return cudaErrorInvalidValue;
 }

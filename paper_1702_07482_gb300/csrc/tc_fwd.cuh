@@ -36,6 +36,15 @@
 // 32 bytes on.  V and the adjoint's filter matrix are BF16 too; phi, the
 // scatter, the fold and the prox stay FP32.
 //
+// X3 (TNRD_ALGO_TC_TF32X3) keeps FP32 accuracy on the TF32 tensor cores: every
+// operand x is held as hi = tf32(x) and lo = tf32(x - hi) (x - hi is exact in
+// FP32), and each GEMM is taken as lo*hi + hi*lo + hi*hi, three TF32 MMAs into
+// the same FP32 accumulator; the dropped lo*lo term is below 2^-22 of the
+// product.  The extra operand copies leave room for two warpgroups per CTA, so
+// V holds one round of 16 filters (high and low parts) at a time: the adjoint
+// MMAs of round rr accumulate Y in its own TMEM buffer while phi works on round
+// rr + 1, and the next round's V is written once they have read the slot.
+//
 // TMEM: each warpgroup owns 128 columns, two buffers of 64.  Group g's z lands
 // in buffer g & 1; once phi has read it, the same buffer receives group g's Y,
 // and once Y has been read, group g + 2's z.  So the filter bank of the next
@@ -157,10 +166,10 @@ struct TcBatchSrc {
 
 // Filter operands of both GEMMs and the padded RBF weights of one parameter
 // set, by all threads of the CTA.
-template <int KS, int NK, int NB, bool BF>
+template <int KS, int NK, int NB, bool BF, bool X3>
 __device__ __forceinline__ void tc_stage_consts(const TcSet& ps, unsigned char* smem, int tid)
 {
-    using C = TcCfg<KS, NK, NB, BF>;
+    using C = TcCfg<KS, NK, NB, BF, X3>;
     constexpr int NTH = C::NTHREADS;
     if constexpr (!BF) {
         float* sBz = reinterpret_cast<float*>(smem + C::OFF_BZ);
@@ -171,13 +180,19 @@ __device__ __forceinline__ void tc_stage_consts(const TcSet& ps, unsigned char* 
             const int ka = e / (C::NPAD * 8), rem = e - ka * (C::NPAD * 8);
             const int nn = rem / 8, k = rem - nn * 8;
             const float v = (nn < NK && k < KS) ? __ldg(ps.k + (nn * KS + ka) * KS + (KS - 1 - k)) : 0.0f;
-            sBz[ka * C::NPAD * 8 + ((nn / 8) * 2 + k / 4) * 32 + (nn % 8) * 4 + (k % 4)] = tc::to_tf32(v);
+            const int o = ka * C::NPAD * 8 + ((nn / 8) * 2 + k / 4) * 32 + (nn % 8) * 4 + (k % 4);
+            const float hi = tc::to_tf32(v);
+            sBz[o] = hi;
+            if constexpr (X3) sBz[C::BZ_BYTES / 4 + o] = tc::to_tf32(v - hi);
         }
         // B of the adjoint GEMM: B[tap][i] = k_i[tap], core matrices [i/4][tap/8][tap%8][i%4]
         for (int e = tid; e < C::NT * C::NKP; e += NTH) {
             const int tap = e / C::NKP, i = e - tap * C::NKP;
             const float v = (tap < KS * KS && i < NK) ? __ldg(ps.k + i * KS * KS + tap) : 0.0f;
-            sKm[((i / 4) * (C::NT / 8) + tap / 8) * 32 + (tap % 8) * 4 + (i % 4)] = tc::to_tf32(v);
+            const int o = ((i / 4) * (C::NT / 8) + tap / 8) * 32 + (tap % 8) * 4 + (i % 4);
+            const float hi = tc::to_tf32(v);
+            sKm[o] = hi;
+            if constexpr (X3) sKm[C::KM_BYTES / 4 + o] = tc::to_tf32(v - hi);
         }
     } else {
         // B of the filter bank, per kernel row ka: B[nn][b'] = k_nn[ka][KS-1-b'] (b' < 16),
@@ -223,12 +238,12 @@ struct TcPipe {
 // One stage on one tile, by one warpgroup (bar: its named barrier).  Returns
 // 0 if a wait on the tensor core gave up (the tile's output is then not
 // written); uniform over the warpgroup.
-template <int KS, int NK, int NB, bool BF>
+template <int KS, int NK, int NB, bool BF, bool X3>
 __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsigned char* smem,
                                        unsigned char* wgs, uint32_t tmem, uint64_t* mb, TcPipe& pp,
                                        int wt, int bar)
 {
-    using C = TcCfg<KS, NK, NB, BF>;
+    using C = TcCfg<KS, NK, NB, BF, X3>;
     constexpr int R = C::R, TW = C::TW, TH = C::TH;
     constexpr long long WAIT_LIMIT = 1ll << 31;   // SM cycles, about one second
     float* sU = reinterpret_cast<float*>(wgs + C::WG_U);
@@ -279,7 +294,10 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
             for (int idx = wt; idx < 4 * UCOPY; idx += 128) {
                 const int r = idx / UCOPY, rem = idx - r * UCOPY;
                 const int i = rem / C::UPITCH, j = rem - i * C::UPITCH;
-                sU[idx] = tc::to_tf32(raw[i * C::RAWP + j + r]);
+                const float v = raw[i * C::RAWP + j + r];
+                const float hi = tc::to_tf32(v);
+                sU[idx] = hi;
+                if constexpr (X3) sU[4 * UCOPY + idx] = tc::to_tf32(v - hi);
             }
         } else {
             // u chunks, two values per 32-bit store: [r][row][chunk][8]
@@ -312,11 +330,22 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
         const uint32_t ur = tc::smem_u32(sU) + (uint32_t)(r * C::UROWS * C::UROWB);
 #pragma unroll
         for (int ka = 0; ka < KS; ++ka) {
-            const uint64_t da = tc::sdesc(ur + (uint32_t)((16 * nb + 2 * R - ka) * C::UROWB),
-                                          BF ? 32 : 16, C::UROWB);
-            const uint64_t db = tc::sdesc(sBz + (uint32_t)(ka * C::NPAD * 32), 128, 256);
-            if constexpr (BF) tc::mma_f16(tmem + 64u * zb, da, db, ID_Z, ka > 0);
-            else tc::mma_tf32(tmem + 64u * zb, da, db, ID_Z, ka > 0);
+            const uint32_t ua = ur + (uint32_t)((16 * nb + 2 * R - ka) * C::UROWB);
+            const uint32_t ba = sBz + (uint32_t)(ka * C::NPAD * 32);
+            const uint64_t da = tc::sdesc(ua, BF ? 32 : 16, C::UROWB);
+            const uint64_t db = tc::sdesc(ba, 128, 256);
+            if constexpr (BF) {
+                tc::mma_f16(tmem + 64u * zb, da, db, ID_Z, ka > 0);
+            } else if constexpr (X3) {
+                // u_lo k_hi + u_hi k_lo + u_hi k_hi
+                tc::mma_tf32(tmem + 64u * zb, tc::sdesc(ua + (uint32_t)C::U_BYTES, 16, C::UROWB), db,
+                             ID_Z, ka > 0);
+                tc::mma_tf32(tmem + 64u * zb, da, tc::sdesc(ba + (uint32_t)C::BZ_BYTES, 128, 256),
+                             ID_Z, 1);
+                tc::mma_tf32(tmem + 64u * zb, da, db, ID_Z, 1);
+            } else {
+                tc::mma_tf32(tmem + 64u * zb, da, db, ID_Z, ka > 0);
+            }
         }
         tc::commit(mb + zb);
     };
@@ -327,57 +356,157 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
     pp.pend |= 3u;
     int ok = 1;
 
+    // phi of round rr (filters 16 rr .. 16 rr + 15) of the group in TMEM buffer
+    // tbuf: x[4q + t] = v of filter 16 rr + 4((q + a) mod 4) + t, a = (wt >> 2) & 3.
+    // Lane j = 4a + b of each half-warp takes the round's filter
+    // 4((q + a) mod 4) + ((t + b) mod 4) at step s = 4q + t: at every step the
+    // half-warp's 16 lanes evaluate 16 different filters, so their weight loads
+    // fall in 16 distinct bank pairs.  Filters beyond NK have zero weights (v = 0).
+    const int ja = (wt >> 2) & 3, jb = wt & 3;
+    auto phi_round = [&](int rr, uint32_t tbuf, bool inside, float (&x)[16]) {
+        const float2* sW2 = reinterpret_cast<const float2*>(smem + C::OFF_W);
+        {
+            uint32_t zr0[8], zr1[8];
+            tc::tmem_ld8_nowait(tbuf + lane_base + 16 * rr, zr0);
+            tc::tmem_ld8_nowait(tbuf + lane_base + 16 * rr + 8, zr1);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                x[k] = __uint_as_float(zr0[k]);
+                x[k + 8] = __uint_as_float(zr1[k]);
+            }
+        }
+        rotl16(x, 4 * ja);                   // groups of four rotated by a
+        rotl4x4(x, jb);                      // within the group by b
+        const float2* tab_r = sW2 + rr * TC_ROWS * 16;
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const int col = (4 * ((s >> 2) + ja) & 12) | (((s & 3) + jb) & 3);
+            x[s] = rbf_phi_col(x[s], tab_r, col, rc);
+        }
+        rotl4x4(x, (4 - jb) & 3);            // x[4q + t] = v of filter 4((q + a) mod 4) + t
+        if (!zin) {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) x[m] = inside ? x[m] : 0.0f;
+        }
+    };
+    // scatter h(p - off(tap)) += Y[p][tap] of group (nb, r), one kernel row per phase
+    constexpr int NY8 = (KS * KS + 7) / 8;
+    auto scatter = [&](int nb, int r, const uint32_t (&yr)[NY8][8]) {
+        const int base = (16 * nb + g + 2 * R) * C::HPITCH + (r + 4 * mp + 2 * R);
+#pragma unroll
+        for (int ka = 0; ka < KS; ++ka) {
+            if (ka > 0) tc::wg_sync(bar);
+#pragma unroll
+            for (int b = 0; b < KS; ++b) {
+                if (b % 4 == 0) __syncwarp();
+                const int t = ka * KS + b;
+                sH[base - ka * C::HPITCH - b] += __uint_as_float(yr[t / 8][t % 8]);
+            }
+        }
+        __syncwarp();
+    };
+    // wait on mbarrier b (z buffers 0, 1; Y 2), uniform over the warpgroup
+    auto wait_mb = [&](int b) {
+        const bool got = ok && tc::mbar_wait(mb + b, (pp.ph >> b) & 1u, WAIT_LIMIT);
+        if (got) {
+            pp.ph ^= 1u << b;
+            pp.pend &= ~(1u << b);
+        }
+        ok = tc::wg_and(bar, got);
+    };
+
+    if constexpr (X3) {
+        const uint32_t ybuf = tmem + 128u;
+#pragma unroll 1
+        for (int gi = 0; gi < NG; ++gi) {
+            const int nb = gi >> 2, r = gi & 3, zb = gi & 1;
+            const uint32_t tbuf = tmem + 64u * zb;
+            wait_mb(zb);
+            tc::fence_after();
+            const int yy = y0 - R + 16 * nb + g, xx = x0 - R + r + 4 * mp;
+            const bool inside = (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
+#pragma unroll 1
+            for (int rr = 0; rr < C::NR; ++rr) {
+                float x[16];
+                if (ok) phi_round(rr, tbuf, inside, x);
+                // the previous round's adjoint MMAs have read the V slot
+                if (rr > 0) wait_mb(2);
+                if (ok) {
+                    // A layout [filter/4][g][mp][filter%4] of the round's 16 filters,
+                    // high parts, then low parts VLO bytes on
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const int f0 = 4 * ((q4 + ja) & 3);
+                        if (16 * rr + f0 < C::NKP) {
+                            float hi[4], lo[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                hi[k] = tc::to_tf32(x[4 * q4 + k]);
+                                lo[k] = tc::to_tf32(x[4 * q4 + k] - hi[k]);
+                            }
+                            float* dst = sV + ((f0 / 4) * 16 + g) * 32 + mp * 4;
+                            *reinterpret_cast<float4*>(dst) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                            *reinterpret_cast<float4*>(dst + C::VLO / 4) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                        }
+                    }
+                }
+                tc::fence_async_smem();
+                tc::fence_before();
+                tc::wg_sync(bar);
+                tc::fence_after();
+                const bool last = rr == C::NR - 1;
+                if (ok && wt == 0) {
+                    // Y += V_rr Kmat_rr: per 8 filters v_lo k_hi + v_hi k_lo + v_hi k_hi
+                    const int nks = min(2, (C::NKP - 16 * rr) / 8);
+                    for (int s = 0; s < nks; ++s) {
+                        const uint32_t va = tc::smem_u32(sV) + (uint32_t)(s * 4096);
+                        const uint32_t kh = sKm + (uint32_t)((2 * rr + s) * 2 * LBO_KM);
+                        const uint64_t dvh = tc::sdesc(va, 16 * 128, 128);
+                        const uint64_t dkh = tc::sdesc(kh, LBO_KM, 128);
+                        tc::mma_tf32(ybuf, tc::sdesc(va + (uint32_t)C::VLO, 16 * 128, 128), dkh, ID_Y,
+                                     rr > 0 || s > 0);
+                        tc::mma_tf32(ybuf, dvh, tc::sdesc(kh + (uint32_t)C::KM_BYTES, LBO_KM, 128),
+                                     ID_Y, 1);
+                        tc::mma_tf32(ybuf, dvh, dkh, ID_Y, 1);
+                    }
+                    tc::commit(mb + 2);
+                    // every lane has read this group's z: the buffer takes group gi + 2's
+                    if (last && gi + 2 < NG) issue_z(gi + 2);
+                }
+                if (ok) {
+                    pp.pend |= 4u;
+                    if (last && gi + 2 < NG) pp.pend |= 1u << zb;
+                }
+            }
+            wait_mb(2);
+            tc::fence_after();
+            uint32_t yr[NY8][8];
+            if (ok) {
+#pragma unroll
+                for (int c = 0; c < NY8; ++c) tc::tmem_ld8_nowait(ybuf + lane_base + 8 * c, yr[c]);
+                tc::tmem_wait_ld();
+            }
+            tc::fence_before();
+            tc::wg_sync(bar);
+            tc::fence_after();
+            if (ok) scatter(nb, r, yr);
+        }
+    } else {
 #pragma unroll 1
     for (int gi = 0; gi < NG; ++gi) {
         const int nb = gi >> 2, r = gi & 3, zb = gi & 1;
         const uint32_t tbuf = tmem + 64u * zb;
-        {
-            const bool got = ok && tc::mbar_wait(mb + zb, (pp.ph >> zb) & 1u, WAIT_LIMIT);
-            if (got) {
-                pp.ph ^= 1u << zb;
-                pp.pend &= ~(1u << zb);
-            }
-            ok = tc::wg_and(bar, got);
-        }
+        wait_mb(zb);
         tc::fence_after();
         // ---- v = phi(z) into the A operand of the adjoint GEMM -------------------
         const int yy = y0 - R + 16 * nb + g, xx = x0 - R + r + 4 * mp;
         const bool inside = (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
         if (ok) {
-            // Rounds of 16 filters.  Lane j = 4a + b of each half-warp takes
-            // the round's filter 4((q + a) mod 4) + ((t + b) mod 4) at step
-            // s = 4q + t: at every step the half-warp's 16 lanes evaluate 16
-            // different filters, so their weight loads fall in 16 distinct
-            // bank pairs.  Filters beyond NK have zero weights (v = 0).
-            const int ja = (wt >> 2) & 3, jb = wt & 3;
-            const float2* sW2 = reinterpret_cast<const float2*>(smem + C::OFF_W);
 #pragma unroll 1
             for (int rr = 0; rr < C::NR; ++rr) {
                 float x[16];
-                {
-                    uint32_t zr0[8], zr1[8];
-                    tc::tmem_ld8_nowait(tbuf + lane_base + 16 * rr, zr0);
-                    tc::tmem_ld8_nowait(tbuf + lane_base + 16 * rr + 8, zr1);
-                    tc::tmem_wait_ld();
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        x[k] = __uint_as_float(zr0[k]);
-                        x[k + 8] = __uint_as_float(zr1[k]);
-                    }
-                }
-                rotl16(x, 4 * ja);                   // groups of four rotated by a
-                rotl4x4(x, jb);                      // within the group by b
-                const float2* tab_r = sW2 + rr * TC_ROWS * 16;
-#pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    const int col = (4 * ((s >> 2) + ja) & 12) | (((s & 3) + jb) & 3);
-                    x[s] = rbf_phi_col(x[s], tab_r, col, rc);
-                }
-                rotl4x4(x, (4 - jb) & 3);            // x[4q + t] = v of filter 4((q + a) mod 4) + t
-                if (!zin) {
-#pragma unroll
-                    for (int m = 0; m < 16; ++m) x[m] = inside ? x[m] : 0.0f;
-                }
+                phi_round(rr, tbuf, inside, x);
                 if constexpr (!BF) {
                     // A layout [filter/4][g][mp][filter%4]: core matrices of 8 positions x 4
                     // filters; group q of this lane is the round's filter group (q + a) mod 4
@@ -426,19 +555,11 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
             tc::commit(mb + 2);
         }
         if (ok) pp.pend |= 4u;
-        {
-            const bool got = ok && tc::mbar_wait(mb + 2, (pp.ph >> 2) & 1u, WAIT_LIMIT);
-            if (got) {
-                pp.ph ^= 4u;
-                pp.pend &= ~4u;
-            }
-            ok = tc::wg_and(bar, got);
-        }
+        wait_mb(2);
         tc::fence_after();
         // ---- this pixel's Y row, then the buffer takes group gi + 2's z ----------
         // (tcgen05.ld is warp-collective: every lane loads; lanes outside the
         // image have v = 0, hence Y = 0, and add zeros at in-range indices)
-        constexpr int NY8 = (KS * KS + 7) / 8;
         uint32_t yr[NY8][8];
         if (ok) {
 #pragma unroll
@@ -453,20 +574,8 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
             pp.pend |= 1u << zb;
         }
         // ---- scatter h(p - off(tap)) += Y[p][tap], one kernel row per phase ------
-        if (ok) {
-            const int base = (16 * nb + g + 2 * R) * C::HPITCH + (r + 4 * mp + 2 * R);
-#pragma unroll
-            for (int ka = 0; ka < KS; ++ka) {
-                if (ka > 0) tc::wg_sync(bar);
-#pragma unroll
-                for (int b = 0; b < KS; ++b) {
-                    if (b % 4 == 0) __syncwarp();
-                    const int t = ka * KS + b;
-                    sH[base - ka * C::HPITCH - b] += __uint_as_float(yr[t / 8][t % 8]);
-                }
-            }
-            __syncwarp();
-        }
+        if (ok) scatter(nb, r, yr);
+    }
     }
 
     // ---- epilogue: g = fold(h), u_t = prox(u_{t-1} - g) ---------------------------
@@ -506,10 +615,10 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
 // when a warpgroup gave up waiting for its MMAs (it then skips its remaining
 // tiles, waits a bounded time for the MMAs still in flight, and the CTA frees
 // its TMEM as usual).
-template <int KS, int NK, int NB, bool BF, class Src>
+template <int KS, int NK, int NB, bool BF, bool X3, class Src>
 __device__ __forceinline__ void tc_run(const Src& src, unsigned char* smem, int* err)
 {
-    using C = TcCfg<KS, NK, NB, BF>;
+    using C = TcCfg<KS, NK, NB, BF, X3>;
     constexpr long long WAIT_LIMIT = 1ll << 31;
     const int tid = threadIdx.x, wg = tid >> 7, wt = tid & 127;
     const int bar = 1 + wg;   // named barrier of this warpgroup (0 is the CTA's)
@@ -526,7 +635,7 @@ __device__ __forceinline__ void tc_run(const Src& src, unsigned char* smem, int*
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t tmem = tbase + (uint32_t)(128 * wg);
+    const uint32_t tmem = tbase + (uint32_t)(C::TMEM_WG * wg);
 
     TcPipe pp;
     int ok = 1;
@@ -539,7 +648,7 @@ __device__ __forceinline__ void tc_run(const Src& src, unsigned char* smem, int*
         const int s1 = src.seg_end(s0, c1);
         const TcSet ps = src.params(set);
         __syncthreads();   // every warpgroup's MMAs of the previous set have completed
-        tc_stage_consts<KS, NK, NB, BF>(ps, smem, tid);
+        tc_stage_consts<KS, NK, NB, BF, X3>(ps, smem, tid);
         tc::fence_async_smem();
         __syncthreads();
         // the tiles read u_{t-1} (the previous stage's output) and overwrite the
@@ -548,7 +657,7 @@ __device__ __forceinline__ void tc_run(const Src& src, unsigned char* smem, int*
         const RbfConst rc = *ps.rc;
 #pragma unroll 1
         for (int s = s0 + wg; s < s1 && ok; s += C::NWG)
-            ok = tc_tile<KS, NK, NB, BF>(src.tile(s), rc, smem, wgs, tmem, mb, pp, wt, bar);
+            ok = tc_tile<KS, NK, NB, BF, X3>(src.tile(s), rc, smem, wgs, tmem, mb, pp, wt, bar);
         s0 = s1;
     }
     if (!ok) {
@@ -564,24 +673,24 @@ __device__ __forceinline__ void tc_run(const Src& src, unsigned char* smem, int*
 
 // Per-call stage: a persistent grid of at most one CTA per SM over the N
 // images' tiles.
-template <int KS, int NK, int NB, bool BF>
-__global__ void __launch_bounds__(TcCfg<KS, NK, NB, BF>::NTHREADS, 1)
+template <int KS, int NK, int NB, bool BF, bool X3>
+__global__ void __launch_bounds__(TcCfg<KS, NK, NB, BF, X3>::NTHREADS, 1)
 tc_stage_fwd(const __grid_constant__ StageArgs a, int n_img)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     tc::pdl_launch_dependents();   // the next stage may launch; it waits before touching u
     const TcCallSrc src{&a, n_img};
-    tc_run<KS, NK, NB, BF>(src, smem, &g_tc_error);
+    tc_run<KS, NK, NB, BF, X3>(src, smem, &g_tc_error);
 }
 
 // Stage t of a batched plan over every image's tiles.
-template <int KS, int NK, int NB, bool BF>
-__global__ void __launch_bounds__(TcCfg<KS, NK, NB, BF>::NTHREADS, 1)
+template <int KS, int NK, int NB, bool BF, bool X3>
+__global__ void __launch_bounds__(TcCfg<KS, NK, NB, BF, X3>::NTHREADS, 1)
 tc_batch_fwd(const __grid_constant__ BatchArgs a, int t)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcBatchSrc<KS, NK> src{&a, t};
-    tc_run<KS, NK, NB, BF>(src, smem, a.status);
+    tc_run<KS, NK, NB, BF, X3>(src, smem, a.status);
 }
 
 }  // namespace tnrd

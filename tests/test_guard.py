@@ -39,7 +39,7 @@ def _images(region, N, H, P):
 
 
 @pytest.mark.parametrize("algo", ["fused", "lane", "pair", "pair2", "pair4", "pair8", "unfused", "tf32",
-                                  "bf16"])
+                                  "bf16", "tf32x3"])
 @pytest.mark.parametrize("keep", [0, 1])
 def test_forward_writes_only_its_output(algo, keep, monkeypatch):
     if algo in ("lane", "pair", "pair2", "pair4", "pair8"):
