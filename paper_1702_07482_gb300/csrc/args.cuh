@@ -409,22 +409,27 @@ struct TcCfg {
     static constexpr int NR = (NK + 15) / 16;    // rounds of 16 filters (RBF weight table)
     static constexpr size_t OFF_WG = al(OFF_W + 8ull * NR * TC_ROWS * 16);
     // per warpgroup: u operands, V (the raw u rows before the first group), h, barriers.
+    // U holds the four residue copies of u, or (X3) a ring of two residues, each
+    // as high and low parts, built from the raw rows that stay for the whole tile.
     // V holds all NKP filters of a group, or (X3) one round of 16 filters, high and
     // low parts: the round's adjoint MMAs run while phi works on the next round.
-    static constexpr size_t U_BYTES = 4ull * UROWS * UROWB;
+    static constexpr size_t U_SLOT = (size_t)UROWS * UROWB;     // one residue copy
+    static constexpr size_t U_BYTES = 4 * U_SLOT;
+    static constexpr size_t RAW_BYTES = 4ull * UROWS * RAWP;
     static constexpr int VF = X3 ? 16 : NKP;     // filters of V held at once
     static constexpr size_t VLO = (size_t)ESZ * 128 * VF;   // byte offset of V's low parts
     static constexpr size_t WG_U = 0;
-    static constexpr size_t WG_V = al(WG_U + NSPL * U_BYTES);
-    static constexpr size_t WG_H = al(WG_V + mx(NSPL * VLO, 4ull * UROWS * RAWP));
+    static constexpr size_t WG_RAW = al(WG_U + U_BYTES);    // X3 only
+    static constexpr size_t WG_V = X3 ? al(WG_RAW + RAW_BYTES) : WG_RAW;
+    static constexpr size_t WG_H = al(WG_V + (X3 ? 2 * VLO : mx(VLO, RAW_BYTES)));
     static constexpr size_t WG_MISC = al(WG_H + 4ull * HROWS * HPITCH);
     static constexpr size_t WG_BYTES = al(WG_MISC + 32);
     static constexpr size_t SMEM_MAX = 227 * 1024;
     static constexpr int fit_wg(int n) { return (n > 1 && OFF_WG + (size_t)n * WG_BYTES + 16 > SMEM_MAX) ? fit_wg(n - 1) : n; }
-    // warpgroups per CTA; TMEM columns of one: z buffers 0..63, 64..127, and
-    // (X3) the adjoint's Y at 128..191 (z and Y share a buffer otherwise)
-    static constexpr int NWG = fit_wg(X3 ? 2 : 4);
-    static constexpr int TMEM_WG = X3 ? 256 : 128;
+    // warpgroups per CTA; TMEM columns of one (128): two z buffers that also
+    // take Y, or (X3) one z buffer at 0..63 and the adjoint's Y at 64..127
+    static constexpr int NWG = fit_wg(4);
+    static constexpr int TMEM_WG = 128;
     static constexpr int NTHREADS = 128 * NWG;
     static constexpr size_t OFF_TMEM = OFF_WG + (size_t)NWG * WG_BYTES;
     static constexpr size_t SMEM_BYTES = OFF_TMEM + 16;

@@ -40,10 +40,14 @@
 // operand x is held as hi = tf32(x) and lo = tf32(x - hi) (x - hi is exact in
 // FP32), and each GEMM is taken as lo*hi + hi*lo + hi*hi, three TF32 MMAs into
 // the same FP32 accumulator; the dropped lo*lo term is below 2^-22 of the
-// product.  The extra operand copies leave room for two warpgroups per CTA, so
-// V holds one round of 16 filters (high and low parts) at a time: the adjoint
-// MMAs of round rr accumulate Y in its own TMEM buffer while phi works on round
-// rr + 1, and the next round's V is written once they have read the slot.
+// product.  To keep three warpgroups per CTA with the doubled operands, a
+// warpgroup holds the u copies of two residues only (a ring; the groups run
+// residue-major and the next residue is built from the tile's raw rows while
+// the current one is in use), V holds one round of 16 filters (high and low
+// parts) at a time -- the adjoint MMAs of round rr accumulate Y in its own TMEM
+// buffer while phi works on round rr + 1, and the next round's V is written
+// once they have read the slot -- and z has one TMEM buffer: z(gi + 1) is
+// issued once phi has read z(gi), and runs under gi's adjoint and scatter.
 //
 // TMEM: each warpgroup owns 128 columns, two buffers of 64.  Group g's z lands
 // in buffer g & 1; once phi has read it, the same buffer receives group g's Y,
@@ -261,10 +265,25 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
     const bool zin = y0 - R >= 0 && y0 - R + C::ZR <= H && x0 - R >= 0 && x0 - R + 32 <= W;
     const float* uin = a.u_in;
 
-    // ---- stage u: raw rows (in the V area), then the residue operands --------
+    // ---- stage u: raw rows (in the V area; X3: their own area, kept for the
+    // tile), then the residue operands (X3: residue 0; the others as the groups
+    // reach them) --------
+    float* const sRaw = X3 ? reinterpret_cast<float*>(wgs + C::WG_RAW) : sV;
+    // X3: residue rres of u as high and low parts into ring slot rres & 1
+    auto build_res = [&](int rres) {
+        constexpr int UCOPY = C::UROWS * C::UPITCH;
+        float* dst = sU + (rres & 1) * 2 * (C::U_SLOT / 4);
+        for (int idx = wt; idx < UCOPY; idx += 128) {
+            const int i = idx / C::UPITCH, j = idx - i * C::UPITCH;
+            const float v = sRaw[i * C::RAWP + j + rres];
+            const float hi = tc::to_tf32(v);
+            dst[idx] = hi;
+            dst[C::U_SLOT / 4 + idx] = tc::to_tf32(v - hi);
+        }
+    };
     tc::wg_sync(bar);   // the previous tile's epilogue has read h
     {
-        float* raw = sV;
+        float* raw = sRaw;
         const int ry = y0 - 2 * R, rx = x0 - 2 * R;
         const bool inner = ry >= 0 && ry + C::UROWS <= H && rx >= 0 && rx + C::RAWC <= W;
         constexpr int NRAW = C::UROWS * C::RAWC;
@@ -289,15 +308,14 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
         }
         for (int e = wt; e < C::HROWS * C::HPITCH; e += 128) sH[e] = 0.0f;
         tc::wg_sync(bar);
-        if constexpr (!BF) {
+        if constexpr (X3) {
+            build_res(0);
+        } else if constexpr (!BF) {
             constexpr int UCOPY = C::UROWS * C::UPITCH;
             for (int idx = wt; idx < 4 * UCOPY; idx += 128) {
                 const int r = idx / UCOPY, rem = idx - r * UCOPY;
                 const int i = rem / C::UPITCH, j = rem - i * C::UPITCH;
-                const float v = raw[i * C::RAWP + j + r];
-                const float hi = tc::to_tf32(v);
-                sU[idx] = hi;
-                if constexpr (X3) sU[4 * UCOPY + idx] = tc::to_tf32(v - hi);
+                sU[idx] = tc::to_tf32(raw[i * C::RAWP + j + r]);
             }
         } else {
             // u chunks, two values per 32-bit store: [r][row][chunk][8]
@@ -312,7 +330,7 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
         }
         tc::fence_async_smem();
         tc::fence_before();
-        tc::wg_sync(bar);   // operands complete; the raw rows are no longer needed
+        tc::wg_sync(bar);   // operands complete; the raw rows are no longer needed (but X3's)
         tc::fence_after();
     }
 
@@ -324,10 +342,13 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
     constexpr int NG = 4 * NB;                  // groups (row block, residue) per tile
     const int g = wt >> 3, mp = wt & 7;         // this thread's pixel in every group
 
-    // z = K u of group gi into TMEM buffer gi & 1: one MMA (K = 32 bytes) per kernel row
+    // z = K u of group gi into TMEM buffer gi & 1: one MMA (K = 32 bytes) per kernel
+    // row.  X3: groups residue-major (gi = NB r + nb), residue r in ring slot r & 1,
+    // one z buffer (0), three MMAs per kernel row.
     auto issue_z = [&](int gi) {
-        const int nb = gi >> 2, r = gi & 3, zb = gi & 1;
-        const uint32_t ur = tc::smem_u32(sU) + (uint32_t)(r * C::UROWS * C::UROWB);
+        const int nb = X3 ? gi % NB : gi >> 2, r = X3 ? gi / NB : gi & 3, zb = X3 ? 0 : gi & 1;
+        const uint32_t ur = tc::smem_u32(sU) +
+                            (uint32_t)(X3 ? (r & 1) * 2 * C::U_SLOT : r * C::UROWS * C::UROWB);
 #pragma unroll
         for (int ka = 0; ka < KS; ++ka) {
             const uint32_t ua = ur + (uint32_t)((16 * nb + 2 * R - ka) * C::UROWB);
@@ -338,7 +359,7 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
                 tc::mma_f16(tmem + 64u * zb, da, db, ID_Z, ka > 0);
             } else if constexpr (X3) {
                 // u_lo k_hi + u_hi k_lo + u_hi k_hi
-                tc::mma_tf32(tmem + 64u * zb, tc::sdesc(ua + (uint32_t)C::U_BYTES, 16, C::UROWB), db,
+                tc::mma_tf32(tmem + 64u * zb, tc::sdesc(ua + (uint32_t)C::U_SLOT, 16, C::UROWB), db,
                              ID_Z, ka > 0);
                 tc::mma_tf32(tmem + 64u * zb, da, tc::sdesc(ba + (uint32_t)C::BZ_BYTES, 128, 256),
                              ID_Z, 1);
@@ -351,9 +372,9 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
     };
     if (wt == 0) {
         issue_z(0);
-        issue_z(1);
+        if constexpr (!X3) issue_z(1);
     }
-    pp.pend |= 3u;
+    pp.pend |= X3 ? 1u : 3u;
     int ok = 1;
 
     // phi of round rr (filters 16 rr .. 16 rr + 15) of the group in TMEM buffer
@@ -417,13 +438,16 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
     };
 
     if constexpr (X3) {
-        const uint32_t ybuf = tmem + 128u;
+        // one z buffer (columns 0..63) and Y (64..127); z(gi + 1) is issued once
+        // phi has read z(gi) and runs under the adjoint and the scatter of gi
+        const uint32_t tbuf = tmem, ybuf = tmem + 64u;
 #pragma unroll 1
         for (int gi = 0; gi < NG; ++gi) {
-            const int nb = gi >> 2, r = gi & 3, zb = gi & 1;
-            const uint32_t tbuf = tmem + 64u * zb;
-            wait_mb(zb);
+            const int nb = gi % NB, r = gi / NB;
+            wait_mb(0);
             tc::fence_after();
+            // the next residue into the slot of residue r - 1, whose z are all done
+            if ((gi + 1) % NB == 0 && gi + 1 < NG) build_res((gi + 1) / NB);
             const int yy = y0 - R + 16 * nb + g, xx = x0 - R + r + 4 * mp;
             const bool inside = (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
 #pragma unroll 1
@@ -471,12 +495,12 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
                         tc::mma_tf32(ybuf, dvh, dkh, ID_Y, 1);
                     }
                     tc::commit(mb + 2);
-                    // every lane has read this group's z: the buffer takes group gi + 2's
-                    if (last && gi + 2 < NG) issue_z(gi + 2);
+                    // every lane has read z(gi) and written the next residue: z(gi + 1)
+                    if (last && gi + 1 < NG) issue_z(gi + 1);
                 }
                 if (ok) {
                     pp.pend |= 4u;
-                    if (last && gi + 2 < NG) pp.pend |= 1u << zb;
+                    if (last && gi + 1 < NG) pp.pend |= 1u;
                 }
             }
             wait_mb(2);
