@@ -554,14 +554,14 @@ class Train(Workload):
     kernels, or the TF32 / BF16 tensor-core stage with algo), then the FP32
     backward of every stage."""
 
-    def __init__(self, dev, n=32, S=180, T_=T, cfg=4, algo="fused"):
+    def __init__(self, dev, n=32, S=180, T_=T, cfg=4, algo="fused", bwd_algo="fused"):
         super().__init__(dev)
         import numpy as np
         import torch
         import synth
         from paper_1702_07482_gb300 import binding as B
         from paper_1702_07482_gb300 import ops
-        self.T, self.n, self.S, self.algo = T_, n, S, algo
+        self.T, self.n, self.S, self.algo, self.bwd_algo = T_, n, S, algo, bwd_algo
         self.p = _p32(synth.params(T_, KS, NK, seed=synth.seed_for(cfg, 0, "params")))
         rank = int(os.environ.get("RANK", "0"))      # each rank its own crops (weak scaling)
         pairs = [synth.single_image(S, S, 1, cfg, index=rank * n + i) for i in range(n)]
@@ -574,7 +574,8 @@ class Train(Workload):
         self.f_host = self.f_dev.cpu().pin_memory()
         self.c_host = self.c_dev.cpu().pin_memory()
         self.u_all = torch.empty((T_ + 1,) + tuple(self.f_dev.shape), device=dev)
-        self.ws_bytes = ops.workspace_size(self.m, n, S, S, self.P, 1, op=B.OP_BACKWARD)
+        self.ws_bytes = ops.workspace_size(self.m, n, S, S, self.P, 1, op=B.OP_BACKWARD,
+                                           algo=bwd_algo)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.g_host = torch.empty(self.m.filters.numel() + self.m.rbf_w.numel() + T_,
                                   dtype=torch.float32).pin_memory()
@@ -583,8 +584,9 @@ class Train(Workload):
         self.launches = T_ + T_ * 5   # forward stages; prep, zb, adj, dk, reduce per stage
         self.flops = float(self.px) * T_ * (FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE)
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE
+        adj = "bwd_adj" if bwd_algo == "fused" else f"tc_bwd_adj[{bwd_algo}]"
         self.kernel = (B.tnrd_forward_kernel(self.m.params(), n, S, S, B.ALGO[algo]) +
-                       " + bwd_prep/bwd_zb/bwd_adj/bwd_dk/bwd_reduce <7,48>")
+                       f" + bwd_prep/bwd_zb/{adj}/bwd_dk/bwd_reduce <7,48>")
         if algo != "fused":
             # the forward's filter bank and adjoint on the tensor cores, the rest FP32
             self.tensor_dtype = algo
@@ -594,9 +596,12 @@ class Train(Workload):
             self.alu_flops_per_px_stage = ALU_FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE
         self.h2d = int((self.f_host.numel() + self.c_host.numel()) * 4)
         self.d2h = int(self.g_host.numel() * 4)
-        fwd = {"fused": "", "tf32": ", TF32 tensor-core forward, FP32 backward",
-               "bf16": ", BF16 tensor-core forward, FP32 backward",
-               "tf32x3": ", split-TF32 tensor-core forward, FP32 backward"}[algo]
+        fwd = {"fused": "", "tf32": ", TF32 tensor-core forward",
+               "bf16": ", BF16 tensor-core forward",
+               "tf32x3": ", split-TF32 tensor-core forward"}[algo]
+        fwd += {"fused": (", FP32 backward" if algo != "fused" else ""),
+                "tf32x3": ", backward adjoint on split-TF32 tensor cores",
+                "tf32": ", backward adjoint on TF32 tensor cores"}[bwd_algo]
         self.config = {"workload": f"TRDMD training step (forward + backward), {n} crops of "
                                    f"{S}x{S}, L=1, 7x7x48, 63 RBF, T={T_}, loss 1/2|u_T - clean|^2, "
                                    "gradients of all filters, RBF weights and lambda" + fwd,
@@ -610,7 +615,7 @@ class Train(Workload):
                         W=self.S)
         e = u[-1] - self.c_dev
         self.grads = ops.backward(self.m, self.f_dev, u, e, want_grad_u0=False, W=self.S,
-                                  workspace=self.ws)
+                                  workspace=self.ws, algo=self.bwd_algo)
 
     def e2e(self):
         import torch
@@ -632,7 +637,7 @@ class Train(Workload):
         f0 = self.f_dev[:1]
         u = ops.forward(self.m, f0, keep_stages=True, algo=self.algo, W=self.S)
         _, gk, gw, gl = ops.backward(self.m, f0, u, (u[-1] - self.c_dev[:1]).contiguous(),
-                                     want_grad_u0=False, W=self.S)
+                                     want_grad_u0=False, W=self.S, algo=self.bwd_algo)
         torch.cuda.synchronize()
         oracle.build()
         fo = self.f[0].astype(np.float64)
@@ -784,7 +789,7 @@ class Mixed(Workload):
         import synth
         from paper_1702_07482_gb300 import binding as B
         from paper_1702_07482_gb300 import ops
-        self.T, self.n, self.S, self.algo = T_, n, S, algo
+        self.T, self.n, self.S, self.algo, self.bwd_algo = T_, n, S, algo, bwd_algo
         self.tensor_dtype = algo if algo in TENSOR_RATIO else None
         self.dtype = {"tf32": "tf32 operands, f32 accumulate",
                       "bf16": "bf16 operands, f32 accumulate",
@@ -884,7 +889,9 @@ def make_workload(name, dev):
     if name == "train_tf32":
         return Train(dev, algo="tf32")
     if name == "train_tf32x3":
-        return Train(dev, algo="tf32x3")
+        return Train(dev, algo="tf32x3", bwd_algo="tf32x3")
+    if name == "train_tc":
+        return Train(dev, algo="tf32", bwd_algo="tf32")
     if name == "fwd512_tf32x3":
         return Fwd(dev, algo="tf32x3")
     if name == "mixed_tf32x3":
@@ -1136,7 +1143,7 @@ def main():
     ap.add_argument("--workload", default="fwd512",
                     choices=["fwd512", "fwd512_unfused", "small128", "batched", "batched_tf32",
                              "batched_bf16", "train", "train_tf32", "train_bf16", "train_tf32x3",
-                             "fwd512_tf32x3", "mixed_tf32x3",
+                             "train_tc", "fwd512_tf32x3", "mixed_tf32x3",
                              "fit", "fit_tf32", "fwd512_gauss", "fwd512_proj", "quality", "mixed_tf32",
                              "mixed_bf16", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -651,8 +651,8 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
     if (st != TNRD_OK) return st;
     st = check_images(N, H, W, pitch, p->ksize);
     if (st != TNRD_OK) return st;
-    if (algo != TNRD_ALGO_FUSED)
-        return fail(TNRD_ERR_UNSUPPORTED, "tnrd_backward supports TNRD_ALGO_FUSED only");
+    if (algo != TNRD_ALGO_FUSED && algo != TNRD_ALGO_TC_TF32 && algo != TNRD_ALGO_TC_TF32X3)
+        return fail(TNRD_ERR_UNSUPPORTED, "tnrd_backward supports TNRD_ALGO_FUSED, _TC_TF32 and _TC_TF32X3");
     if (!grad_filters || !grad_rbf_w || !grad_lambda)
         return fail(TNRD_ERR_INVALID_ARG, "null gradient output");
     const int T = p->T, ks = p->ksize, nk = p->nfilt, nrbf = p->nrbf;
@@ -700,6 +700,11 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
     a.dterm = p->data_term;
     a.proj_c = p->proj_c;
     a.rc = make_rbf(p);
+    // the adjoint on the tensor cores (TF32 or split TF32), the rest as FUSED
+    const int adj_prec = algo == TNRD_ALGO_FUSED ? -1 : tc_prec(algo);
+    int* err = nullptr;
+    if (adj_prec >= 0 && !(err = tnrd::device_status_word()))
+        return fail(TNRD_ERR_CUDA, "device status word unavailable");
 
     for (int t = T - 1; t >= 0; --t) {
         a.u_prev = u_stages + (size_t)t * batch;
@@ -709,7 +714,7 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
         a.k = p->filters + (size_t)t * nk * ks * ks;
         a.w = p->rbf_w + (size_t)t * nk * nrbf;
         a.lam = p->lambda + t;
-        cudaError_t e = tnrd::launch_bwd_stage(ks, nk, a, N, stream);
+        cudaError_t e = tnrd::launch_bwd_stage(ks, nk, a, N, stream, adj_prec, err);
         if (e != cudaSuccess) return cuda_fail(e, "backward stage launch");
         tnrd::RedArgs r{};
         r.s[0] = {a.part_k, N * L.dk_tiles_x * L.dk_tiles_y, nk * ks * ks,

@@ -43,7 +43,7 @@ int sm_count()
 }
 
 template <int KS, int NK, int TH>
-cudaError_t launch_stage(const BwdArgs& a, int N, cudaStream_t s)
+cudaError_t launch_stage(const BwdArgs& a, int N, cudaStream_t s, int adj_prec, int* err)
 {
     using Z = ZbCfg<KS, NK, TH>;
     using A = AdjCfg<KS, NK, TH>;
@@ -81,8 +81,12 @@ cudaError_t launch_stage(const BwdArgs& a, int N, cudaStream_t s)
     bwd_zb<KS, NK, TH><<<dim3(a.zb_tiles_x * a.zb_tiles_y, N, zs), Z::NTHREADS, Z::SMEM_BYTES, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    bwd_adj<KS, NK, TH><<<dim3(a.tiles_x * a.tiles_y, N), A::NTHREADS, A::SMEM_BYTES, s>>>(a);
-    e = cudaGetLastError();
+    if (adj_prec >= 0) {
+        e = launch_tc_bwd_adj(KS, NK, adj_prec, a, N, err, s);
+    } else {
+        bwd_adj<KS, NK, TH><<<dim3(a.tiles_x * a.tiles_y, N), A::NTHREADS, A::SMEM_BYTES, s>>>(a);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     bwd_dk<KS, NK, TH><<<dim3(a.dk_tiles_x * a.dk_tiles_y, N, ds), 128, 0, s>>>(a);
     return cudaGetLastError();
@@ -90,14 +94,15 @@ cudaError_t launch_stage(const BwdArgs& a, int N, cudaStream_t s)
 
 }  // namespace
 
-cudaError_t launch_bwd_stage(int ks, int nk, const BwdArgs& a, int N, cudaStream_t s)
+cudaError_t launch_bwd_stage(int ks, int nk, const BwdArgs& a, int N, cudaStream_t s,
+                             int adj_prec, int* err)
 {
     bwd_prep<<<dim3(a.prep_blocks, N), 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (ks == 3 && nk == 4) return launch_stage<3, 4, 34>(a, N, s);
-    if (ks == 5 && nk == 24) return launch_stage<5, 24, 36>(a, N, s);
-    if (ks == 7 && nk == 48) return launch_stage<7, 48, 36>(a, N, s);
+    if (ks == 3 && nk == 4) return launch_stage<3, 4, 34>(a, N, s, adj_prec, err);
+    if (ks == 5 && nk == 24) return launch_stage<5, 24, 36>(a, N, s, adj_prec, err);
+    if (ks == 7 && nk == 48) return launch_stage<7, 48, 36>(a, N, s, adj_prec, err);
     return cudaErrorInvalidValue;
 }
 

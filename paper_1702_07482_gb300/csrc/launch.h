@@ -116,7 +116,13 @@ bool pair_fwd_box(int ks, int nk, int th, int* box_w, int* box_h);
 // Backward: tile height of bwd_zb / bwd_adj, one stage's prep + zb + adj +
 // filter-gradient launches, and the fixed-order partial reduce (three sets).
 int bwd_tile_h(int ks);
-cudaError_t launch_bwd_stage(int ks, int nk, const BwdArgs& a, int N, cudaStream_t s);
+// One backward stage (prep, zb, adjoint, dk).  adj_prec < 0: the adjoint on the
+// CUDA cores (bwd_adj); TC_TF32 / TC_TF32X3: on the tensor cores (tc_bwd_adj),
+// recording a wait that gave up in the status word err.
+cudaError_t launch_bwd_stage(int ks, int nk, const BwdArgs& a, int N, cudaStream_t s,
+                             int adj_prec = -1, int* err = nullptr);
+cudaError_t launch_tc_bwd_adj(int ks, int nk, int prec, const BwdArgs& a, int N, int* err,
+                              cudaStream_t s);
 cudaError_t launch_bwd_reduce(const RedArgs& r, cudaStream_t s);
 
 // Quality indexes: tiles per image, and the partials + finish launches.

@@ -1,0 +1,308 @@
+// Tensor-core adjoint of the backward stage (Sec. 3.2, Eq. derv1-1):
+//   dL/du_{t-1} = d + fold(sum_i K_i^T c_i)
+// as the forward stage's adjoint: Y[p][tap] = sum_i c_i(p) k_i[tap] is one
+// tcgen05 GEMM per group of 128 positions (M = 128, N = 64 taps, K = the
+// filters), h(q) = sum_tap Y[q + off(tap)][tap] is scattered on the CUDA cores
+// into the warpgroup's h buffer in kernel-row phases, and the epilogue folds the
+// border (the exact transpose of the symmetric-padded convolution) and adds d.
+//
+// The c planes come from bwd_zb in HBM; each thread loads its position's c
+// values, 16 filters per round, one round ahead, and writes them as the A
+// operand (TF32, or X3: TF32 high part and TF32 remainder, three MMAs per
+// product -- lo*hi + hi*lo + hi*hi -- for FP32 accuracy).  Tiles are those of
+// the forward's tensor-core stage, (16 NB - 2R) x (32 - 2R) outputs over a
+// region of 16 NB x 32 positions; a group is 4 rows x 32 columns of it, warp w
+// one row, lane l one column, so a warp's loads are 128 contiguous bytes.  The
+// scatter sums each kernel row within the warp first: lane l adds
+// Y[row][l - R + b][tap (a, b)] over b (shuffles), the one h element of column
+// l + R the row feeds through kernel row a, then one read-modify-write per
+// kernel row (the warps' h rows are disjoint within a phase; a warpgroup barrier
+// between phases).  One persistent CTA per SM of NWG warpgroups; the filter
+// matrix is staged once per CTA.  Every wait on the tensor core is bounded; a
+// timeout sets the status word and the CTA still frees its TMEM.
+#include <algorithm>
+
+#include "args.cuh"
+#include "launch.h"
+#include "tc_ptx.cuh"
+
+namespace tnrd {
+
+template <int KS, int NK, int NB, bool X3>
+struct TcAdjCfg {
+    static constexpr int R = KS / 2;
+    static constexpr int TW = 32 - 2 * R;
+    static constexpr int ZR = 16 * NB;                   // position rows per tile
+    static constexpr int TH = ZR - 2 * R;
+    static constexpr int NKP = (NK + 7) / 8 * 8;         // K of the GEMM (TF32: 8 per MMA)
+    static constexpr int NT = (KS * KS + 15) / 16 * 16;  // N (taps)
+    static constexpr int NR = (NK + 15) / 16;            // rounds of 16 filters
+    static constexpr int NSPL = X3 ? 2 : 1;
+    static constexpr int HROWS = ZR + 2 * R;
+    static constexpr int HPITCH = 41;
+    static constexpr size_t al(size_t x) { return (x + 127) / 128 * 128; }
+    static constexpr size_t KM_BYTES = 4ull * NT * NKP;
+    static constexpr size_t OFF_KM = 0;
+    static constexpr size_t OFF_WG = al(OFF_KM + NSPL * KM_BYTES);
+    static constexpr size_t VLO = 4ull * 128 * 16;       // one round, high parts; low parts after
+    static constexpr size_t WG_V = 0;
+    static constexpr size_t WG_H = al(WG_V + NSPL * VLO);
+    static constexpr size_t WG_MISC = al(WG_H + 4ull * HROWS * HPITCH);
+    static constexpr size_t WG_BYTES = al(WG_MISC + 32);
+    static constexpr int NWG = 4;
+    static constexpr int NTHREADS = 128 * NWG;
+    static constexpr size_t OFF_TMEM = OFF_WG + (size_t)NWG * WG_BYTES;
+    static constexpr size_t SMEM_BYTES = OFF_TMEM + 16;
+    static constexpr uint32_t TMEM_COLS = 512;           // 128 per warpgroup, Y in the first 64
+    static_assert(NT <= 64, "Y fits one 64-column buffer");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
+
+template <int KS, int NK, int NB, bool X3>
+__global__ void __launch_bounds__(TcAdjCfg<KS, NK, NB, X3>::NTHREADS, 1)
+tc_bwd_adj(const __grid_constant__ BwdArgs a, int n_img, int tiles_x, int tiles_y, int* err)
+{
+    using C = TcAdjCfg<KS, NK, NB, X3>;
+    constexpr int R = C::R, TW = C::TW, TH = C::TH;
+    constexpr long long WAIT_LIMIT = 1ll << 31;          // SM cycles, about one second
+    constexpr uint32_t ID_Y = tc::idesc(tc::FMT_TF32, 128, C::NT);
+    constexpr uint32_t LBO_KM = (C::NT / 8) * 128;
+    constexpr int NG = C::ZR / 4;                        // groups of 4 position rows
+    constexpr int NY8 = (KS * KS + 7) / 8;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, wg = tid >> 7, wt = tid & 127, warp = wt >> 5, lane = wt & 31;
+    const int bar = 1 + wg;
+    unsigned char* wgs = smem + C::OFF_WG + (size_t)wg * C::WG_BYTES;
+    float* sV = reinterpret_cast<float*>(wgs + C::WG_V);
+    float* sH = reinterpret_cast<float*>(wgs + C::WG_H);
+    uint64_t* mb = reinterpret_cast<uint64_t*>(wgs + C::WG_MISC);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_TMEM);
+
+    // filter matrix B[tap][i] = k_i[tap], core matrices [i/4][tap/8][tap%8][i%4]
+    // (X3: the TF32 remainders KM_BYTES on)
+    {
+        float* sKm = reinterpret_cast<float*>(smem + C::OFF_KM);
+        for (int e = tid; e < C::NT * C::NKP; e += C::NTHREADS) {
+            const int tap = e / C::NKP, i = e - tap * C::NKP;
+            const float v = (tap < KS * KS && i < NK) ? __ldg(a.k + i * KS * KS + tap) : 0.0f;
+            const int o = ((i / 4) * (C::NT / 8) + tap / 8) * 32 + (tap % 8) * 4 + (i % 4);
+            const float hi = tc::to_tf32(v);
+            sKm[o] = hi;
+            if constexpr (X3) sKm[C::KM_BYTES / 4 + o] = tc::to_tf32(v - hi);
+        }
+    }
+    if (wt == 0) tc::mbar_init(mb, 1);
+    tc::fence_async_smem();
+    if (tid < 32) tc::tmem_alloc(tslot, C::TMEM_COLS);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t ybuf = tbase + (uint32_t)(128 * wg);
+    const uint32_t sKm = tc::smem_u32(smem + C::OFF_KM);
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const int g = wt >> 3, mp = wt & 7;
+
+    uint32_t ph = 0;       // parity of the next phase of mb
+    bool pend = false;     // a commit on mb not yet waited for
+    int ok = 1;
+    auto wait_mma = [&]() {
+        const bool got = ok && tc::mbar_wait(mb, ph, WAIT_LIMIT);
+        if (got) {
+            ph ^= 1u;
+            pend = false;
+        }
+        ok = tc::wg_and(bar, got);
+    };
+
+    const int H = a.H, W = a.W, P = a.pitch;
+    const long long plane = a.img_stride;
+    const int tpi = tiles_x * tiles_y, nt = n_img * tpi;
+    const int per = (nt + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int c0 = min(nt, (int)blockIdx.x * per), c1 = min(nt, c0 + per);
+#pragma unroll 1
+    for (int s = c0 + wg; s < c1 && ok; s += C::NWG) {
+        const int n = s / tpi, ti = s - n * tpi, ty = ti / tiles_x, tx = ti - ty * tiles_x;
+        const int y0 = tile_origin(ty, TH, H), x0 = tile_origin(tx, TW, W);
+        const bool border = (ty == 0) || (ty == tiles_y - 1) || (tx == 0) || (tx == tiles_x - 1);
+        const float* cimg = a.cpl + (size_t)n * plane * a.nfilt;
+        tc::wg_sync(bar);   // the previous tile's epilogue has read h
+        for (int e = wt; e < C::HROWS * C::HPITCH; e += 128) sH[e] = 0.0f;
+
+        // c values of round rr of group gi at this thread's position (0 outside
+        // the image and for filters beyond NK)
+        auto load_round = [&](int gi, int rr, float (&c)[16]) {
+            const int yy = y0 - R + 4 * gi + warp, xx = x0 - R + lane;
+            const bool in = (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
+            const float* p = cimg + (in ? (size_t)yy * P + xx : 0);
+#pragma unroll
+            for (int f = 0; f < 16; ++f) {
+                const int i = 16 * rr + f;
+                c[f] = (in && i < NK) ? __ldcg(p + (size_t)i * plane) : 0.0f;
+            }
+        };
+        float cur[16];
+        load_round(0, 0, cur);
+#pragma unroll 1
+        for (int gi = 0; gi < NG; ++gi) {
+#pragma unroll 1
+            for (int rr = 0; rr < C::NR; ++rr) {
+                float nxt[16];
+                if (rr + 1 < C::NR) load_round(gi, rr + 1, nxt);
+                else if (gi + 1 < NG) load_round(gi + 1, 0, nxt);
+                // the previous round's MMAs have read the V slot
+                if (rr > 0) wait_mma();
+                if (ok) {
+                    // A layout [filter/4][g][mp][filter%4], high parts then low parts
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        if (16 * rr + 4 * q4 >= C::NKP) continue;
+                        float hi[4], lo[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            hi[k] = tc::to_tf32(cur[4 * q4 + k]);
+                            lo[k] = tc::to_tf32(cur[4 * q4 + k] - hi[k]);
+                        }
+                        float* dst = sV + (q4 * 16 + g) * 32 + mp * 4;
+                        *reinterpret_cast<float4*>(dst) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                        if constexpr (X3)
+                            *reinterpret_cast<float4*>(dst + C::VLO / 4) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                    }
+                }
+                tc::fence_async_smem();
+                tc::fence_before();
+                tc::wg_sync(bar);
+                tc::fence_after();
+                if (ok && wt == 0) {
+                    // Y += C_rr Kmat_rr, per 8 filters (X3: c_lo k_hi + c_hi k_lo + c_hi k_hi)
+                    const int nks = min(2, (C::NKP - 16 * rr) / 8);
+                    for (int s8 = 0; s8 < nks; ++s8) {
+                        const uint32_t va = tc::smem_u32(sV) + (uint32_t)(s8 * 4096);
+                        const uint32_t kh = sKm + (uint32_t)((2 * rr + s8) * 2 * LBO_KM);
+                        const uint64_t dvh = tc::sdesc(va, 16 * 128, 128);
+                        const uint64_t dkh = tc::sdesc(kh, LBO_KM, 128);
+                        const uint32_t acc0 = (rr > 0 || s8 > 0) ? 1u : 0u;
+                        if constexpr (X3) {
+                            tc::mma_tf32(ybuf, tc::sdesc(va + (uint32_t)C::VLO, 16 * 128, 128), dkh, ID_Y, acc0);
+                            tc::mma_tf32(ybuf, dvh, tc::sdesc(kh + (uint32_t)C::KM_BYTES, LBO_KM, 128), ID_Y, 1);
+                            tc::mma_tf32(ybuf, dvh, dkh, ID_Y, 1);
+                        } else {
+                            tc::mma_tf32(ybuf, dvh, dkh, ID_Y, acc0);
+                        }
+                    }
+                    tc::commit(mb);
+                }
+                if (ok) pend = true;
+#pragma unroll
+                for (int f = 0; f < 16; ++f) cur[f] = nxt[f];
+            }
+            wait_mma();
+            tc::fence_after();
+            uint32_t yr[NY8][8];
+            if (ok) {
+#pragma unroll
+                for (int c = 0; c < NY8; ++c) tc::tmem_ld8_nowait(ybuf + lane_base + 8 * c, yr[c]);
+                tc::tmem_wait_ld();
+            }
+            tc::fence_before();
+            tc::wg_sync(bar);
+            tc::fence_after();
+            // h(p - off(tap)) += Y[p][tap]: h index (prow + 2R - a, pcol + 2R - b) for
+            // the position (prow, pcol) of the region; lane l owns h column l + R,
+            // fed by the positions l - R + b of its warp's row (outside the 32
+            // columns: outside the image, or h columns no output reads)
+            if (ok) {
+                const int hrow0 = 4 * gi + warp + 2 * R;
+#pragma unroll
+                for (int ka = 0; ka < KS; ++ka) {
+                    if (ka > 0) tc::wg_sync(bar);
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < KS; ++b) {
+                        const int t = ka * KS + b;
+                        const int src = lane - R + b;
+                        const float v = __shfl_sync(0xffffffffu, __uint_as_float(yr[t / 8][t % 8]), src & 31);
+                        acc += (src >= 0 && src < 32) ? v : 0.0f;
+                    }
+                    sH[(hrow0 - ka) * C::HPITCH + lane + R] += acc;
+                }
+            }
+        }
+
+        // ---- e_{t-1} = d + fold(h) over the pixels this tile owns ----
+        tc::wg_sync(bar);
+        if (ok) {
+            const int wy0 = tile_split(ty, TH, H, tiles_y, R), wy1 = tile_split(ty + 1, TH, H, tiles_y, R);
+            const int wx0 = tile_split(tx, TW, W, tiles_x, R), wx1 = tile_split(tx + 1, TW, W, tiles_x, R);
+            const size_t ioff = (size_t)n * plane;
+            for (int idx = wt; idx < TH * TW; idx += 128) {
+                const int qy = y0 + idx / TW, qx = x0 + idx % TW;
+                if (qy < wy0 || qy >= wy1 || qx < wx0 || qx >= wx1) continue;
+                int sy[2], sx[2];
+                int nsy = 1, nsx = 1;
+                sy[0] = qy;
+                sx[0] = qx;
+                if (border) {
+                    if (qy < R) sy[nsy++] = -1 - qy;
+                    else if (qy >= H - R) sy[nsy++] = 2 * H - 1 - qy;
+                    if (qx < R) sx[nsx++] = -1 - qx;
+                    else if (qx >= W - R) sx[nsx++] = 2 * W - 1 - qx;
+                }
+                float gsum = 0.0f;
+                for (int pp = 0; pp < nsy; ++pp)
+                    for (int q = 0; q < nsx; ++q)
+                        gsum += sH[(sy[pp] - (y0 - 2 * R)) * C::HPITCH + sx[q] - (x0 - 2 * R)];
+                const size_t o = ioff + (size_t)qy * P + qx;
+                a.e_prev[o] = a.d_id[o] + gsum;
+            }
+        }
+    }
+    if (!ok) {
+        if (pend) tc::mbar_wait(mb, ph, WAIT_LIMIT);
+        if (wt == 0) atomicExch(err, 4);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (tid < 32) tc::tmem_dealloc(tbase, C::TMEM_COLS);
+}
+
+namespace {
+
+int sm_count()
+{
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return nsm > 0 ? nsm : 1;
+}
+
+template <int KS, int NK, bool X3>
+cudaError_t launch_adj(const BwdArgs& a, int N, int* err, cudaStream_t s)
+{
+    using C = TcAdjCfg<KS, NK, 2, X3>;
+    cudaError_t e = cudaFuncSetAttribute(tc_bwd_adj<KS, NK, 2, X3>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    const int tx = (a.W + C::TW - 1) / C::TW, ty = (a.H + C::TH - 1) / C::TH;
+    const long long tiles = (long long)N * tx * ty;
+    const int grid = (int)std::max(1LL, std::min((long long)sm_count(), (tiles + C::NWG - 1) / C::NWG));
+    tc_bwd_adj<KS, NK, 2, X3><<<grid, C::NTHREADS, C::SMEM_BYTES, s>>>(a, N, tx, ty, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc_bwd_adj(int ks, int nk, int prec, const BwdArgs& a, int N, int* err,
+                              cudaStream_t s)
+{
+    const bool x3 = prec == TC_TF32X3;
+    if (prec != TC_TF32 && !x3) return cudaErrorInvalidValue;
+#define X(K, NN)                                                                          \
+    if (ks == K && nk == NN) return x3 ? launch_adj<K, NN, true>(a, N, err, s)            \
+                                       : launch_adj<K, NN, false>(a, N, err, s);
+    X(3, 4) X(5, 24) X(7, 48)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace tnrd

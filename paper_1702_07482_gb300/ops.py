@@ -125,10 +125,14 @@ def forward_band(model: Model, f: torch.Tensor, world: int, rank: int, algo: str
 
 
 def backward(model: Model, f: torch.Tensor, u_stages: torch.Tensor, grad_uT: torch.Tensor,
-             want_grad_u0: bool = True, W: int | None = None, workspace=None):
+             want_grad_u0: bool = True, W: int | None = None, workspace=None,
+             algo: str = "fused"):
     """Gradients (grad_u0, grad_filters, grad_rbf_w, grad_lambda) given dL/du_T.
 
-    f [N][H][pitch], u_stages [T+1][N][H][pitch], grad_uT [N][H][pitch].
+    f [N][H][pitch], u_stages [T+1][N][H][pitch], grad_uT [N][H][pitch].  algo
+    "fused": every kernel on the CUDA cores; "tf32x3" / "tf32": the adjoint
+    dL/du_{t-1} = d + sum_i K_i^T c_i on the tensor cores (split TF32 for FP32
+    accuracy, or TF32).
     """
     N, H, P = f.shape
     if W is None:
@@ -139,12 +143,12 @@ def backward(model: Model, f: torch.Tensor, u_stages: torch.Tensor, grad_uT: tor
     g_k = torch.empty_like(model.filters)
     g_w = torch.empty_like(model.rbf_w)
     g_l = torch.empty_like(model.lam)
-    ws_bytes = B.tnrd_workspace_size(B.OP_BACKWARD, p, N, H, W, P, 1, B.ALGO["fused"])
+    ws_bytes = B.tnrd_workspace_size(B.OP_BACKWARD, p, N, H, W, P, 1, B.ALGO[algo])
     if workspace is None and ws_bytes:
         workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
     B.tnrd_backward(p, N, H, W, P, f, u_stages, grad_uT, g_u0, g_k, g_w, g_l,
-                    B.ALGO["fused"], workspace, ws_bytes, stream)
+                    B.ALGO[algo], workspace, ws_bytes, stream)
     return g_u0, g_k, g_w, g_l
 
 

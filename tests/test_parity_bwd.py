@@ -28,7 +28,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-def _gpu_grads(p, f, clean, algo="fused"):
+def _gpu_grads(p, f, clean, algo="fused", bwd_algo="fused"):
     from paper_1702_07482_gb300 import ops
     m = ops.Model.create(p.filters, p.rbf_w, p.lam, p.mu0, p.delta, p.gamma)
     W = f.shape[-1]
@@ -36,7 +36,7 @@ def _gpu_grads(p, f, clean, algo="fused"):
     u_all = ops.forward(m, fp, keep_stages=True, algo=algo, W=W)
     ct = ops.to_pitched(torch.tensor(clean, dtype=torch.float32, device="cuda"))
     eT = (u_all[-1] - ct).contiguous()
-    g0, gk, gw, gl = ops.backward(m, fp, u_all, eT, want_grad_u0=True, W=W)
+    g0, gk, gw, gl = ops.backward(m, fp, u_all, eT, want_grad_u0=True, W=W, algo=bwd_algo)
     torch.cuda.synchronize()
     c = lambda t: t.double().cpu().numpy()
     return c(u_all[..., :W]), c(g0[..., :W]), c(gk), c(gw), c(gl)
@@ -58,8 +58,8 @@ def _oracle_grads(p, f, clean, u_gpu=None):
     return np.stack(g0), gk, gw, gl
 
 
-def _check(p, f, clean, algo="fused", tol=TOL_GRAD):
-    _, g0, gk, gw, gl = _gpu_grads(p, f, clean, algo)
+def _check(p, f, clean, algo="fused", tol=TOL_GRAD, bwd_algo="fused"):
+    _, g0, gk, gw, gl = _gpu_grads(p, f, clean, algo, bwd_algo)
     r0, rk, rw, rl = _oracle_grads(p, f, clean)
     errs = {"u0": _rel(g0, r0), "lam": _rel(gl, rl)}
     for t in range(p.T):
@@ -182,3 +182,38 @@ def test_autograd_tensor_core_forward():
     np.testing.assert_array_equal(k.grad.double().cpu().numpy(), gk)
     np.testing.assert_array_equal(w.grad.double().cpu().numpy(), gw)
     np.testing.assert_array_equal(lam.grad.double().cpu().numpy(), gl)
+
+
+# The backward's adjoint on the tensor cores (tc_bwd_adj): split TF32 keeps the
+# FP32 bound with every other kernel FP32 (and with the split-TF32 forward);
+# TF32 operands in both directions stay within 1e-3 too.
+@pytest.mark.parametrize("H,W,ks,nk,T,N", [
+    (40, 53, 7, 48, 2, 2),
+    (37, 29, 5, 24, 3, 1),
+    (70, 33, 7, 48, 1, 1),
+    (45, 61, 3, 4, 2, 1),
+])
+def test_tensor_core_adjoint_gradients(H, W, ks, nk, T, N):
+    p, f = case(H, W, ks, nk, T, N=N, cfg=170 + H)
+    clean = np.stack([_clean(H, W, 170 + H, n) for n in range(N)])
+    _check(p, f, clean, "fused", TOL_GRAD, "tf32x3")
+
+
+@pytest.mark.parametrize("algo", ["tf32x3", "tf32"])
+def test_tensor_core_training_step_180_crop_T5(algo):
+    p, f = case(180, 180, 7, 48, 5, cfg=4)
+    clean = np.stack([_clean(180, 180, 4)])
+    _check(p, f, clean, algo, TOL_GRAD, algo)
+
+
+def test_tensor_core_adjoint_repeatable_and_close_to_cuda_core():
+    """tc_bwd_adj gives the same bits on repeated calls, and with split TF32
+    the gradients of the CUDA-core adjoint within FP32 rounding."""
+    p, f = case(90, 77, 7, 48, 2, N=2, cfg=175)
+    clean = np.stack([_clean(90, 77, 175, n) for n in range(2)])
+    a = _gpu_grads(p, f, clean, "fused", "tf32x3")
+    b = _gpu_grads(p, f, clean, "fused", "tf32x3")
+    c = _gpu_grads(p, f, clean, "fused", "fused")
+    for x, y, z in zip(a[1:], b[1:], c[1:]):
+        np.testing.assert_array_equal(x, y)
+        assert _rel(x, z) <= 1e-5
