@@ -9,8 +9,9 @@ collective on the data path): weak scaling.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload fwd512|fwd512_unfused|fwd512_tf32x3|small128|batched|
-                              batched_tf32|batched_bf16|train|train_tf32|train_bf16|
-                              train_tf32x3|fit|fit_tf32|fwd512_gauss|fwd512_proj|
+                              batched_tf32|batched_bf16|batched_tf32x3|train|train_tf32|
+                              train_bf16|train_tf32x3|train_tc|fit|fit_tf32|fwd512_gauss|
+                              fwd512_proj|
                               quality|mixed_tf32|mixed_bf16|mixed_fp32|mixed_tf32x3]
                   [--no-cpu-baseline] [--no-accuracy] [--no-alt]
 
@@ -497,7 +498,8 @@ class Batched(Workload):
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE
         self.algo = algo
         if algo != "fused":
-            self.dtype = f"{algo} operands, f32 accumulate"
+            self.dtype = ("f32 (split TF32 tensor-core products)" if algo == "tf32x3"
+                          else f"{algo} operands, f32 accumulate")
             self.tensor_dtype = algo
         sched = ("batch_persistent_fwd" if self.launches == 1 else
                  "batch_pair2_fwd" if self.plan.tile_width == 64 - 2 * (KS // 2) else "batch_stage_fwd")
@@ -884,6 +886,8 @@ def make_workload(name, dev):
         return Batched(dev, algo="tf32")
     if name == "batched_bf16":
         return Batched(dev, algo="bf16")
+    if name == "batched_tf32x3":
+        return Batched(dev, algo="tf32x3")
     if name == "train":
         return Train(dev)
     if name == "train_tf32":
@@ -1142,7 +1146,8 @@ def main():
                     help="fwd512: skip the split-TF32 measurement reported beside the headline")
     ap.add_argument("--workload", default="fwd512",
                     choices=["fwd512", "fwd512_unfused", "small128", "batched", "batched_tf32",
-                             "batched_bf16", "train", "train_tf32", "train_bf16", "train_tf32x3",
+                             "batched_bf16", "batched_tf32x3", "train", "train_tf32", "train_bf16",
+                             "train_tf32x3",
                              "train_tc", "fwd512_tf32x3", "mixed_tf32x3",
                              "fit", "fit_tf32", "fwd512_gauss", "fwd512_proj", "quality", "mixed_tf32",
                              "mixed_bf16", "mixed_fp32"])
