@@ -151,7 +151,8 @@ TNRD_API tnrd_status tnrd_forward_kernel(const tnrd_params* params, int N, int H
  * Requires lam_t > 0.  algo: TNRD_ALGO_FUSED (every kernel on the CUDA cores,
  * FP32), TNRD_ALGO_TC_TF32X3 (the adjoint dL/du_{t-1} = d + sum_i K_i^T c_i
  * of Eq. derv1-1 as a tensor-core GEMM on split TF32 operands, FP32 accuracy;
- * the rest as FUSED) or TNRD_ALGO_TC_TF32 (the same adjoint with TF32 operands;
+ * the rest as FUSED) or TNRD_ALGO_TC_TF32 (the same adjoint, and the filter
+ * gradient dL/dk as a tensor-core GEMM over the pixels, with TF32 operands;
  * error larger, see the tests); others are TNRD_ERR_UNSUPPORTED.  A tensor-core
  * wait that gave up sets the word tnrd_device_status reads.  The parameter
  * gradients are reduced in a fixed order: repeated calls give identical bits. */

@@ -408,7 +408,9 @@ BwdLayout bwd_layout(const tnrd_params* p, int N, int H, int W, int pitch)
     L.c = take(batch * (size_t)p->nfilt);
     L.v = take(batch * (size_t)p->nfilt);
     L.pw = take(sizeof(float) * (size_t)N * L.zb_tiles_x * L.zb_tiles_y * p->nfilt * p->nrbf);
-    L.pk = take(sizeof(float) * (size_t)N * L.dk_tiles_x * L.dk_tiles_y * p->nfilt * ks * ks);
+    // dL/dk partials: the CUDA-core kernel's tiles or the tensor-core kernel's
+    const size_t dk_rows = std::max((size_t)L.dk_tiles_x * L.dk_tiles_y, (size_t)tnrd::tc_dk_tiles(H, W));
+    L.pk = take(sizeof(float) * (size_t)N * dk_rows * p->nfilt * ks * ks);
     L.pl = take(sizeof(float) * (size_t)N * L.prep_blocks);
     L.total = off;
     return L;
@@ -717,7 +719,9 @@ tnrd_status tnrd_backward(const tnrd_params* p, int N, int H, int W, int pitch,
         cudaError_t e = tnrd::launch_bwd_stage(ks, nk, a, N, stream, adj_prec, err);
         if (e != cudaSuccess) return cuda_fail(e, "backward stage launch");
         tnrd::RedArgs r{};
-        r.s[0] = {a.part_k, N * L.dk_tiles_x * L.dk_tiles_y, nk * ks * ks,
+        r.s[0] = {a.part_k, N * (adj_prec == tnrd::TC_TF32 ? tnrd::tc_dk_tiles(H, W)
+                                                          : L.dk_tiles_x * L.dk_tiles_y),
+                  nk * ks * ks,
                   grad_filters + (size_t)t * nk * ks * ks};
         r.s[1] = {a.part_w, N * L.zb_tiles_x * L.zb_tiles_y, nk * nrbf,
                   grad_rbf_w + (size_t)t * nk * nrbf};

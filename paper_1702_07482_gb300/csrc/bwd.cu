@@ -88,6 +88,10 @@ cudaError_t launch_stage(const BwdArgs& a, int N, cudaStream_t s, int adj_prec, 
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
+    // the filter gradient on the tensor cores with TF32 operands; with split TF32
+    // the CUDA-core kernel is faster (the doubled operands leave one or two CTAs
+    // per SM for a kernel that hides its loads with CTAs)
+    if (adj_prec == TC_TF32) return launch_tc_bwd_dk(KS, NK, adj_prec, a, N, err, s);
     bwd_dk<KS, NK, TH><<<dim3(a.dk_tiles_x * a.dk_tiles_y, N, ds), 128, 0, s>>>(a);
     return cudaGetLastError();
 }

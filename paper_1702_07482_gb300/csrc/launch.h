@@ -116,13 +116,20 @@ bool pair_fwd_box(int ks, int nk, int th, int* box_w, int* box_h);
 // Backward: tile height of bwd_zb / bwd_adj, one stage's prep + zb + adj +
 // filter-gradient launches, and the fixed-order partial reduce (three sets).
 int bwd_tile_h(int ks);
-// One backward stage (prep, zb, adjoint, dk).  adj_prec < 0: the adjoint on the
-// CUDA cores (bwd_adj); TC_TF32 / TC_TF32X3: on the tensor cores (tc_bwd_adj),
-// recording a wait that gave up in the status word err.
+// One backward stage (prep, zb, adjoint, dk).  adj_prec < 0: the adjoint and the
+// filter gradient on the CUDA cores (bwd_adj, bwd_dk); TC_TF32X3: the adjoint on
+// the tensor cores (tc_bwd_adj); TC_TF32: the adjoint and the filter gradient
+// (tc_bwd_dk) on the tensor cores.  A tensor-core wait that gave up is recorded
+// in the status word err.
 cudaError_t launch_bwd_stage(int ks, int nk, const BwdArgs& a, int N, cudaStream_t s,
                              int adj_prec = -1, int* err = nullptr);
 cudaError_t launch_tc_bwd_adj(int ks, int nk, int prec, const BwdArgs& a, int N, int* err,
                               cudaStream_t s);
+// dL/dk partials on the tensor cores (tc_bwd_dk): one row of part_k per tile of
+// 32 x 16 pixels, tc_dk_tiles(H, W) tiles per image.
+cudaError_t launch_tc_bwd_dk(int ks, int nk, int prec, const BwdArgs& a, int N, int* err,
+                             cudaStream_t s);
+int tc_dk_tiles(int H, int W);
 cudaError_t launch_bwd_reduce(const RedArgs& r, cudaStream_t s);
 
 // Quality indexes: tiles per image, and the partials + finish launches.
