@@ -73,8 +73,9 @@ def test_forward_writes_only_its_output(algo, keep, monkeypatch):
     assert np.all(fi[..., W:] == np.float32(CANARY)), "input padding modified"
 
 
-@pytest.mark.parametrize("dterm", [0, 1, 2])
-def test_backward_writes_only_its_outputs(dterm):
+@pytest.mark.parametrize("dterm,algo", [(0, "fused"), (1, "fused"), (2, "fused"), (0, "tf32x3"),
+                                        (0, "tf32"), (2, "tf32")])
+def test_backward_writes_only_its_outputs(dterm, algo):
     from paper_1702_07482_gb300 import binding as B
     from paper_1702_07482_gb300 import ops
     H, W, P, N, T = 40, 33, 36, 2, 2
@@ -89,11 +90,12 @@ def test_backward_writes_only_its_outputs(dterm):
     gwbuf, gw = _guarded(m.rbf_w.numel())
     glbuf, gl = _guarded(m.lam.numel())
     prm = m.params()
-    wsb = B.tnrd_workspace_size(B.OP_BACKWARD, prm, N, H, W, P, 1, 0)
+    wsb = B.tnrd_workspace_size(B.OP_BACKWARD, prm, N, H, W, P, 1, B.ALGO[algo])
     wbuf, wreg = _guarded((wsb + 3) // 4)
-    B.tnrd_backward(prm, N, H, W, P, fp, u_all, eT, g0, gk, gw, gl, 0, wreg, wsb,
+    B.tnrd_backward(prm, N, H, W, P, fp, u_all, eT, g0, gk, gw, gl, B.ALGO[algo], wreg, wsb,
                     torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
+    assert B.tnrd_device_status() == 0
     for buf, n in ((g0buf, N * H * P), (gkbuf, m.filters.numel()), (gwbuf, m.rbf_w.numel()),
                    (glbuf, m.lam.numel()), (wbuf, (wsb + 3) // 4)):
         _check_slabs(buf, n)
