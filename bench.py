@@ -791,7 +791,7 @@ class Mixed(Workload):
         import synth
         from paper_1702_07482_gb300 import binding as B
         from paper_1702_07482_gb300 import ops
-        self.T, self.n, self.S, self.algo, self.bwd_algo = T_, n, S, algo, bwd_algo
+        self.T, self.n, self.S, self.algo = T_, n, S, algo
         self.tensor_dtype = algo if algo in TENSOR_RATIO else None
         self.dtype = {"tf32": "tf32 operands, f32 accumulate",
                       "bf16": "bf16 operands, f32 accumulate",
