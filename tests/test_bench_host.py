@@ -3,9 +3,12 @@ algorithmic counts per pixel that `achieved` divides by, the FP32 ALU peak
 derived from unit counts and clock, and the DRAM-traffic pin, which must
 follow the kernel it was captured on."""
 import importlib
+import os
 import sys
 
 import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -90,3 +93,28 @@ def test_reference_arm_config_equals_the_default_workload_config(bench):
     # the driver compares the two arms' config: the reference line must name
     # the same workload keys as the GPU arm's default line
     assert bench.CONFIG["data_term"] == "idiv" and bench.CONFIG["H"] == bench.H == 512
+
+
+def test_bench_names_resolve():
+    """Every name a bench.py function reads from outside its scopes is a module
+    global or a builtin (a workload constructor that names an undefined variable
+    fails only when that workload runs on a GPU)."""
+    import builtins
+    import symtable
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    top = symtable.symtable(src, "bench.py", "exec")
+    module_names = {s.get_name() for s in top.get_symbols() if s.is_assigned() or s.is_imported()}
+    known = module_names | set(dir(builtins))
+    bad = []
+
+    def walk(t, path):
+        for child in t.get_children():
+            p = f"{path}.{child.get_name()}"
+            if child.get_type() == "function":
+                for sym in child.get_symbols():
+                    if sym.is_global() and sym.is_referenced() and sym.get_name() not in known:
+                        bad.append((p, sym.get_name()))
+            walk(child, p)
+
+    walk(top, "bench")
+    assert not bad, bad
