@@ -587,8 +587,9 @@ class Train(Workload):
         self.flops = float(self.px) * T_ * (FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE)
         self.flops_per_px_stage = FLOPS_PER_PX_STAGE + BWD_FLOPS_PER_PX_STAGE
         adj = "bwd_adj" if bwd_algo == "fused" else f"tc_bwd_adj[{bwd_algo}]"
+        dk = f"tc_bwd_dk[{bwd_algo}]" if bwd_algo == "tf32" else "bwd_dk"
         self.kernel = (B.tnrd_forward_kernel(self.m.params(), n, S, S, B.ALGO[algo]) +
-                       f" + bwd_prep/bwd_zb/{adj}/bwd_dk/bwd_reduce <7,48>")
+                       f" + bwd_prep/bwd_zb/{adj}/{dk}/bwd_reduce <7,48>")
         if algo != "fused":
             # the forward's filter bank and adjoint on the tensor cores, the rest FP32
             self.tensor_dtype = algo
@@ -603,7 +604,7 @@ class Train(Workload):
                "tf32x3": ", split-TF32 tensor-core forward"}[algo]
         fwd += {"fused": (", FP32 backward" if algo != "fused" else ""),
                 "tf32x3": ", backward adjoint on split-TF32 tensor cores",
-                "tf32": ", backward adjoint on TF32 tensor cores"}[bwd_algo]
+                "tf32": ", backward adjoint and filter gradient on TF32 tensor cores"}[bwd_algo]
         self.config = {"workload": f"TRDMD training step (forward + backward), {n} crops of "
                                    f"{S}x{S}, L=1, 7x7x48, 63 RBF, T={T_}, loss 1/2|u_T - clean|^2, "
                                    "gradients of all filters, RBF weights and lambda" + fwd,
