@@ -303,8 +303,9 @@ FusedChoice pick_fused(int ks, int nk, int N, int H, int W)
 
 // Row blocks of 16 z rows per tensor-core tile: 3 for BF16 (its smaller
 // operands leave room for three warpgroups with the taller tile), 2 for TF32
-// (three warpgroups fit only with the shorter one) and for split TF32 (built
-// with two only).  TNRD_TC_NB=2|3 overrides for TF32 and BF16.
+// (with three it runs the ring layout on three warpgroups, measured 3 % slower)
+// and for split TF32 (built with two only).  TNRD_TC_NB=2|3 overrides for TF32
+// and BF16.
 bool is_tc(tnrd_algo algo)
 {
     return algo == TNRD_ALGO_TC_TF32 || algo == TNRD_ALGO_TC_BF16 || algo == TNRD_ALGO_TC_TF32X3;

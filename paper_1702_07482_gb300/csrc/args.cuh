@@ -379,6 +379,10 @@ struct TcCfg {
     static constexpr int KMMA = BF ? 16 : 8;     // K of one MMA (32 bytes)
     static constexpr int KCORE = BF ? 8 : 4;     // K elements of one core matrix row (16 bytes)
     static constexpr int NSPL = X3 ? 2 : 1;      // copies of each operand (X3: high, low part)
+    // ring layout (a two-residue ring of u copies, one z buffer, V one round of
+    // 16 filters): split TF32, and TF32 with three row blocks, whose taller tiles
+    // fit three warpgroups only so
+    static constexpr bool RING = X3 || (!BF && NB == 3);
     static constexpr int NPAD = (NK + 15) / 16 * 16;                 // N of the filter-bank GEMM
     static constexpr int NKP = (NK + KMMA - 1) / KMMA * KMMA;        // K of the adjoint GEMM
     static constexpr int NT = (KS * KS + 15) / 16 * 16;  // N of the adjoint GEMM (taps)
@@ -414,21 +418,21 @@ struct TcCfg {
     // V holds all NKP filters of a group, or (X3) one round of 16 filters, high and
     // low parts: the round's adjoint MMAs run while phi works on the next round.
     static constexpr size_t U_SLOT = (size_t)UROWS * UROWB;     // one residue copy
-    static constexpr size_t U_BYTES = 4 * U_SLOT;
+    static constexpr size_t U_BYTES = (RING ? 2 * NSPL : 4) * U_SLOT;
     static constexpr size_t RAW_BYTES = 4ull * UROWS * RAWP;
-    static constexpr int VF = X3 ? 16 : NKP;     // filters of V held at once
+    static constexpr int VF = RING ? 16 : NKP;   // filters of V held at once
     static constexpr size_t VLO = (size_t)ESZ * 128 * VF;   // byte offset of V's low parts
     static constexpr size_t WG_U = 0;
-    static constexpr size_t WG_RAW = al(WG_U + U_BYTES);    // X3 only
-    static constexpr size_t WG_V = X3 ? al(WG_RAW + RAW_BYTES) : WG_RAW;
-    static constexpr size_t WG_H = al(WG_V + (X3 ? 2 * VLO : mx(VLO, RAW_BYTES)));
+    static constexpr size_t WG_RAW = al(WG_U + U_BYTES);    // ring layout only
+    static constexpr size_t WG_V = RING ? al(WG_RAW + RAW_BYTES) : WG_RAW;
+    static constexpr size_t WG_H = al(WG_V + (RING ? NSPL * VLO : mx(VLO, RAW_BYTES)));
     static constexpr size_t WG_MISC = al(WG_H + 4ull * HROWS * HPITCH);
     static constexpr size_t WG_BYTES = al(WG_MISC + 32);
     static constexpr size_t SMEM_MAX = 227 * 1024;
     static constexpr int fit_wg(int n) { return (n > 1 && OFF_WG + (size_t)n * WG_BYTES + 16 > SMEM_MAX) ? fit_wg(n - 1) : n; }
     // warpgroups per CTA; TMEM columns of one (128): two z buffers that also
-    // take Y, or (X3) one z buffer at 0..63 and the adjoint's Y at 64..127
-    static constexpr int NWG = fit_wg(4);
+    // take Y, or (ring) one z buffer at 0..63 and the adjoint's Y at 64..127
+    static constexpr int NWG = fit_wg(RING ? 3 : 4);   // ring: at most three (registers)
     static constexpr int TMEM_WG = 128;
     static constexpr int NTHREADS = 128 * NWG;
     static constexpr size_t OFF_TMEM = OFF_WG + (size_t)NWG * WG_BYTES;

@@ -268,17 +268,17 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
     // ---- stage u: raw rows (in the V area; X3: their own area, kept for the
     // tile), then the residue operands (X3: residue 0; the others as the groups
     // reach them) --------
-    float* const sRaw = X3 ? reinterpret_cast<float*>(wgs + C::WG_RAW) : sV;
-    // X3: residue rres of u as high and low parts into ring slot rres & 1
+    float* const sRaw = C::RING ? reinterpret_cast<float*>(wgs + C::WG_RAW) : sV;
+    // ring layout: residue rres of u (X3: high and low parts) into ring slot rres & 1
     auto build_res = [&](int rres) {
         constexpr int UCOPY = C::UROWS * C::UPITCH;
-        float* dst = sU + (rres & 1) * 2 * (C::U_SLOT / 4);
+        float* dst = sU + (rres & 1) * C::NSPL * (C::U_SLOT / 4);
         for (int idx = wt; idx < UCOPY; idx += 128) {
             const int i = idx / C::UPITCH, j = idx - i * C::UPITCH;
             const float v = sRaw[i * C::RAWP + j + rres];
             const float hi = tc::to_tf32(v);
             dst[idx] = hi;
-            dst[C::U_SLOT / 4 + idx] = tc::to_tf32(v - hi);
+            if constexpr (X3) dst[C::U_SLOT / 4 + idx] = tc::to_tf32(v - hi);
         }
     };
     tc::wg_sync(bar);   // the previous tile's epilogue has read h
@@ -308,7 +308,7 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
         }
         for (int e = wt; e < C::HROWS * C::HPITCH; e += 128) sH[e] = 0.0f;
         tc::wg_sync(bar);
-        if constexpr (X3) {
+        if constexpr (C::RING) {
             build_res(0);
         } else if constexpr (!BF) {
             constexpr int UCOPY = C::UROWS * C::UPITCH;
@@ -343,12 +343,13 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
     const int g = wt >> 3, mp = wt & 7;         // this thread's pixel in every group
 
     // z = K u of group gi into TMEM buffer gi & 1: one MMA (K = 32 bytes) per kernel
-    // row.  X3: groups residue-major (gi = NB r + nb), residue r in ring slot r & 1,
-    // one z buffer (0), three MMAs per kernel row.
+    // row.  Ring layout: groups residue-major (gi = NB r + nb), residue r in ring slot
+    // r & 1, one z buffer (0); X3: three MMAs per kernel row.
+    constexpr bool RING = C::RING;
     auto issue_z = [&](int gi) {
-        const int nb = X3 ? gi % NB : gi >> 2, r = X3 ? gi / NB : gi & 3, zb = X3 ? 0 : gi & 1;
+        const int nb = RING ? gi % NB : gi >> 2, r = RING ? gi / NB : gi & 3, zb = RING ? 0 : gi & 1;
         const uint32_t ur = tc::smem_u32(sU) +
-                            (uint32_t)(X3 ? (r & 1) * 2 * C::U_SLOT : r * C::UROWS * C::UROWB);
+                            (uint32_t)(RING ? (r & 1) * C::NSPL * C::U_SLOT : r * C::UROWS * C::UROWB);
 #pragma unroll
         for (int ka = 0; ka < KS; ++ka) {
             const uint32_t ua = ur + (uint32_t)((16 * nb + 2 * R - ka) * C::UROWB);
@@ -372,9 +373,9 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
     };
     if (wt == 0) {
         issue_z(0);
-        if constexpr (!X3) issue_z(1);
+        if constexpr (!RING) issue_z(1);
     }
-    pp.pend |= X3 ? 1u : 3u;
+    pp.pend |= RING ? 1u : 3u;
     int ok = 1;
 
     // phi of round rr (filters 16 rr .. 16 rr + 15) of the group in TMEM buffer
@@ -437,7 +438,7 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
         ok = tc::wg_and(bar, got);
     };
 
-    if constexpr (X3) {
+    if constexpr (RING) {
         // one z buffer (columns 0..63) and Y (64..127); z(gi + 1) is issued once
         // phi has read z(gi) and runs under the adjoint and the scatter of gi
         const uint32_t tbuf = tmem, ybuf = tmem + 64u;
@@ -471,7 +472,8 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
                             }
                             float* dst = sV + ((f0 / 4) * 16 + g) * 32 + mp * 4;
                             *reinterpret_cast<float4*>(dst) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-                            *reinterpret_cast<float4*>(dst + C::VLO / 4) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                            if constexpr (X3)
+                                *reinterpret_cast<float4*>(dst + C::VLO / 4) = make_float4(lo[0], lo[1], lo[2], lo[3]);
                         }
                     }
                 }
@@ -488,11 +490,15 @@ __device__ __forceinline__ int tc_tile(const TcTile& a, const RbfConst& rc, unsi
                         const uint32_t kh = sKm + (uint32_t)((2 * rr + s) * 2 * LBO_KM);
                         const uint64_t dvh = tc::sdesc(va, 16 * 128, 128);
                         const uint64_t dkh = tc::sdesc(kh, LBO_KM, 128);
-                        tc::mma_tf32(ybuf, tc::sdesc(va + (uint32_t)C::VLO, 16 * 128, 128), dkh, ID_Y,
-                                     rr > 0 || s > 0);
-                        tc::mma_tf32(ybuf, dvh, tc::sdesc(kh + (uint32_t)C::KM_BYTES, LBO_KM, 128),
-                                     ID_Y, 1);
-                        tc::mma_tf32(ybuf, dvh, dkh, ID_Y, 1);
+                        if constexpr (X3) {
+                            tc::mma_tf32(ybuf, tc::sdesc(va + (uint32_t)C::VLO, 16 * 128, 128), dkh, ID_Y,
+                                         rr > 0 || s > 0);
+                            tc::mma_tf32(ybuf, dvh, tc::sdesc(kh + (uint32_t)C::KM_BYTES, LBO_KM, 128),
+                                         ID_Y, 1);
+                            tc::mma_tf32(ybuf, dvh, dkh, ID_Y, 1);
+                        } else {
+                            tc::mma_tf32(ybuf, dvh, dkh, ID_Y, rr > 0 || s > 0);
+                        }
                     }
                     tc::commit(mb + 2);
                     // every lane has read z(gi) and written the next residue: z(gi + 1)
