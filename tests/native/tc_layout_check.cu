@@ -14,9 +14,15 @@
 //     or +32 B), the raw rows the copies are built from, V (the adjoint's A: 16
 //     M groups 128 B apart, two K cores 2 KB apart per MMA), h, the mbarriers;
 //   - TMEM: the z buffer(s) and Y inside the warpgroup's columns.
+// The backward's kernels (tc_bwd_cfg.cuh) likewise: tc_bwd_adj's filter matrix,
+// V rounds, h buffers and TMEM; tc_bwd_dk's interleaved residue rows as its A
+// descriptors read them (16 kernel-row groups one row apart from pixel row pr,
+// core rows 16 B apart, second K core at +64 B) and its staged B rows (core
+// matrices of 8 filters 128 B apart, second K core one quad on).
 // Prints "ok <configs>" and exits 0, or prints the first violation and exits 1.
 #include <cstdio>
 #include "args.cuh"
+#include "tc_bwd_cfg.cuh"
 
 static int fails = 0;
 #define CHECK(cond, ...)                                                   \
@@ -121,6 +127,69 @@ void check_cfg()
     }
 }
 
+#define CHECKB(cond, ...)                                                  \
+    do {                                                                   \
+        if (!(cond)) {                                                     \
+            std::printf("%s KS %d NK %d X3 %d: ", what, KS, NK, X3);      \
+            std::printf(__VA_ARGS__);                                      \
+            std::printf("\n");                                             \
+            ++fails;                                                       \
+            return;                                                        \
+        }                                                                  \
+    } while (0)
+
+template <int KS, int NK, bool X3>
+void check_adj()
+{
+    const char* what = "tc_bwd_adj";
+    using C = tnrd::TcAdjCfg<KS, NK, 2, X3>;
+    CHECKB(C::SMEM_BYTES <= 227 * 1024, "shared memory %zu", C::SMEM_BYTES);
+    CHECKB(C::NWG * 128 <= (int)C::TMEM_COLS && C::TMEM_COLS <= 512, "TMEM");
+    CHECKB(C::OFF_KM + C::NSPL * C::KM_BYTES <= C::OFF_WG, "filter matrix overlaps the warpgroups");
+    CHECKB(C::WG_V + C::NSPL * C::VLO <= C::WG_H, "V overlaps h");
+    CHECKB(C::WG_H + 4ull * C::HROWS * C::HPITCH <= C::WG_MISC, "h overlaps the mbarrier");
+    CHECKB(C::WG_MISC + 8 <= C::WG_BYTES, "mbarrier leaves the warpgroup");
+    CHECKB(C::OFF_WG + (size_t)C::NWG * C::WG_BYTES <= C::OFF_TMEM, "warpgroups overlap the TMEM slot");
+    // B: k-step (2 rr + s) at (2 rr + s) 2 LBO; two K cores LBO apart, NT / 8 core
+    // matrices 128 B apart
+    const size_t lbo = (C::NT / 8) * 128;
+    const size_t endb = (size_t)(C::NKP / 8 - 1) * 2 * lbo + lbo + (size_t)(C::NT / 8 - 1) * 128 + 128;
+    CHECKB(endb <= C::KM_BYTES, "filter matrix read to %zu of %zu", endb, C::KM_BYTES);
+    // A (V, one round): two k-steps of 4096 B, 16 M groups 128 B apart, two K cores 2048 B apart
+    const size_t enda = 4096 + 2048 + 15 * 128 + 128;
+    CHECKB(enda <= C::VLO, "V read to %zu of %zu", enda, C::VLO);
+    CHECKB(C::NT <= 64, "Y columns");
+}
+
+template <int KS, int NK, bool X3>
+void check_dk()
+{
+    const char* what = "tc_bwd_dk";
+    using C = tnrd::TcDkCfg<KS, NK, X3>;
+    CHECKB(C::SMEM_BYTES <= 227 * 1024, "shared memory %zu", C::SMEM_BYTES);
+    CHECKB(C::NP <= (int)C::TMEM_COLS, "TMEM columns");
+    CHECKB(C::OFF_ILD == C::OFF_ILU + C::NSPL * C::IL_BYTES && C::OFF_ST == C::OFF_ILD + C::NSPL * C::IL_BYTES &&
+               C::OFF_MISC == C::OFF_ST + C::NBUF * C::BUF_BYTES && C::OFF_MISC + 16 + 4 <= C::SMEM_BYTES,
+           "regions out of order");
+    CHECKB(C::NBUF <= 2, "mbarriers: two slots");
+    // A: pixel row pr, 8-pixel chunk kc: start pr ILP + 2 kc 64; 16 groups ILP
+    // apart; 8 core rows 16 B apart; the second K core at +64
+    for (int pr = 0; pr < C::TPR; ++pr)
+        for (int kc = 0; kc < 4; ++kc) {
+            const size_t end = (size_t)(pr + 15) * C::ILP + 2 * kc * 64 + 64 + 7 * 16 + 16;
+            CHECKB(end <= C::IL_BYTES, "A of row %d chunk %d reads to %zu of %zu", pr, kc, end, C::IL_BYTES);
+            // within one IL row: quads up to 2 kc + 1 + 1 (taps b'' < 8)
+            CHECKB(2 * kc * 64 + 64 + 7 * 16 + 16 <= C::ILP, "A leaves its IL row");
+        }
+    CHECKB(C::ILR_REAL <= C::ILR, "built IL rows");
+    // the IL rows real taps read (kernel-row slots a'' < KS) are the built ones
+    CHECKB(C::TPR - 1 + KS - 1 < C::ILR_REAL, "real taps read unbuilt IL rows");
+    // B: chunk kc at 2 kc QB; NP / 8 core matrices 128 B apart; second K core at +QB
+    const size_t endb = (size_t)(2 * 3 + 1) * C::QB + (size_t)(C::NP / 8 - 1) * 128 + 128;
+    CHECKB(endb <= C::STG_BYTES, "B reads to %zu of %zu", endb, C::STG_BYTES);
+    CHECKB(C::QB % 16 == 0 && (C::QB / 4) % 32 == 4, "staging quad pitch (banks)");
+}
+
 int main()
 {
     int n = 0;
@@ -134,6 +203,14 @@ int main()
     check_cfg<5, 24, 2, false, true>();
     check_cfg<7, 48, 2, false, true>();
     n += 3;
+#define Y(K, NN)                 \
+    check_adj<K, NN, false>();   \
+    check_adj<K, NN, true>();    \
+    check_dk<K, NN, false>();    \
+    check_dk<K, NN, true>();     \
+    n += 4;
+    Y(3, 4) Y(5, 24) Y(7, 48)
+#undef Y
     if (fails) return 1;
     std::printf("ok %d\n", n);
     return 0;

@@ -1,5 +1,6 @@
-"""Host-only: the tensor-core stage's shared-memory and TMEM layout (TcCfg in
-csrc/args.cuh) for every instantiated configuration, checked by a small native
+"""Host-only: the shared-memory and TMEM layouts of the tensor-core kernels (TcCfg
+in csrc/args.cuh, TcAdjCfg and TcDkCfg in csrc/tc_bwd_cfg.cuh) for every
+instantiated configuration, checked by a small native
 program built with nvcc for the host (tests/native/tc_layout_check.cu): every
 byte range an MMA descriptor or a staging loop addresses lies inside its own
 region, the regions are disjoint, and shared memory and TMEM fit.  No GPU."""
@@ -25,4 +26,4 @@ def test_tensor_core_layouts(tmp_path):
     assert r.returncode == 0, r.stderr[-3000:]
     r = subprocess.run([exe], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert r.stdout.startswith("ok 15")
+    assert r.stdout.startswith("ok 27")
